@@ -1,0 +1,385 @@
+"""CPU oracle for the column-row partitioned sparse product (CRoP).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this module.  It is a
+plain, slow, single-threaded restatement of what the product computes, written
+from the paper (Campagna, Kutzkov, Pagh, "On Parallelizing Matrix
+Multiplication by the Column-Row Method"), and it shares no code with the CUDA
+path: the hash, the enumeration, the accumulation and the summaries are all
+written out again here.  Floating point is fp64.
+
+Sections of the paper each function follows:
+
+* Preliminaries, Notation: ``C = A B = sum_k a_k b_k``; the weight of entry
+  (i, j) is ``sum_k a_k(i) b_k(j)``; ``[n] = {0..n-1}``
+  -> :func:`outer_product_terms`, :func:`exact_product_loop`,
+  :func:`exact_product`, :func:`entry`.
+* Section 4, Lemma 1 (proof): ``h(i,j) = (h_a(i) + h_b(j)) mod P`` with
+  pairwise independent ``h_a, h_b``; the set ``E_L^{ab}`` of entries of the
+  outer product ``ab`` hashing into an interval ``L = [q, r)``
+  -> :func:`hash_params`, :func:`side_hash`, :func:`partition_of`,
+  :func:`interval_terms` (tests every pair; it does not use the two-pointer
+  scan, so that scan is checked against the definition).
+* Preliminaries, Space-Saving, with weighted positive updates
+  -> :func:`space_saving`.
+* Section 6 (case study): support of a pair = number of transactions holding
+  it, i.e. the entries above the diagonal of ``T^T T``; heaviest entries
+  -> :func:`topk`.
+
+Readings where the paper is silent (each also listed in the design doc):
+
+* Hash family: the paper requires pairwise independence only.  ``(a, b)`` are
+  the first two SplitMix64 outputs (Steele, Lea, Flood 2014) from the seed, and
+  ``h(x) = ((a x + b) mod 2^64) >> (64 - log2 P)`` (Dietzfelbinger's
+  multiply-add-shift); ``P`` is a power of two; ``P = 1`` maps everything to 0.
+* Space-Saving ties: the slot evicted is the one of minimum count, ties broken
+  by the smallest key (i, j); a weighted insert of weight w into a full summary
+  takes ``(key, min + w, min)``.
+* Top-k order: weight descending, then i ascending, then j ascending.
+"""
+from __future__ import annotations
+
+import heapq
+from dataclasses import dataclass
+
+import numpy as np
+
+MASK64 = (1 << 64) - 1
+FULL = 0   # every entry (i, j)
+UPPER = 1  # only entries above the diagonal, i < j (pair mining, Section 6)
+
+
+# ---------------------------------------------------------------------------
+# Hashing (Lemma 1 proof; Preliminaries: k-wise independence)
+# ---------------------------------------------------------------------------
+
+def splitmix64(seed: int, count: int) -> list[int]:
+    """The first ``count`` outputs of SplitMix64 started from state ``seed``
+    (Steele, Lea, Flood, "Fast splittable pseudorandom number generators",
+    OOPSLA 2014): the state advances by the golden-gamma constant and each
+    output is the state passed through the variant-13 mixer."""
+    out = []
+    x = seed & MASK64
+    for _ in range(count):
+        x = (x + 0x9E3779B97F4A7C15) & MASK64
+        z = x
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        out.append(z ^ (z >> 31))
+    return out
+
+
+def hash_params(seed: int) -> tuple[int, int]:
+    """Multiplier and addend of one side hash, drawn from ``seed``."""
+    a, b = splitmix64(seed, 2)
+    return a, b
+
+
+def mas_hash_scalar(x: int, a: int, b: int, out_bits: int, word_bits: int = 64) -> int:
+    """Multiply-add-shift: ``((a x + b) mod 2^w) >> (w - l)`` with ``l =
+    out_bits`` (0 bits -> 0).  ``word_bits`` is a parameter only so tests can
+    check the construction exhaustively at small widths."""
+    if out_bits == 0:
+        return 0
+    m = (1 << word_bits) - 1
+    return (((a * x) + b) & m) >> (word_bits - out_bits)
+
+
+def side_hash(x: np.ndarray, seed: int, out_bits: int) -> np.ndarray:
+    """``h(x)`` for an array of nonnegative indices, 64-bit words (numpy
+    uint64 arithmetic wraps modulo 2^64)."""
+    x = np.asarray(x, dtype=np.int64).astype(np.uint64)
+    if out_bits == 0:
+        return np.zeros(x.shape, dtype=np.int64)
+    a, b = hash_params(seed)
+    with np.errstate(over="ignore"):
+        v = x * np.uint64(a) + np.uint64(b)
+    return (v >> np.uint64(64 - out_bits)).astype(np.int64)
+
+
+def log2_exact(P: int) -> int:
+    if P < 1 or (P & (P - 1)):
+        raise ValueError("P must be a power of two >= 1")
+    return P.bit_length() - 1
+
+
+def partition_of(i, j, P: int, seed_a: int, seed_b: int) -> np.ndarray:
+    """``h(i,j) = (h_a(i) + h_b(j)) mod P`` (Lemma 1 proof)."""
+    lg = log2_exact(P)
+    return (side_hash(i, seed_a, lg) + side_hash(j, seed_b, lg)) % P
+
+
+# ---------------------------------------------------------------------------
+# Sparse inputs
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Compressed:
+    """Compressed sparse vectors: vector k holds indices idx[ptr[k]:ptr[k+1]]
+    with values val[...] (None = all ones, a {0,1} matrix)."""
+    ptr: np.ndarray
+    idx: np.ndarray
+    val: np.ndarray | None
+    n_minor: int
+
+    @staticmethod
+    def of(obj) -> "Compressed":
+        return Compressed(np.asarray(obj.ptr, dtype=np.int64), np.asarray(obj.idx, np.int32),
+                          None if obj.val is None else np.asarray(obj.val, np.float32),
+                          int(obj.n_minor))
+
+    @property
+    def n_major(self) -> int:
+        return len(self.ptr) - 1
+
+    def vector(self, k: int):
+        s, e = int(self.ptr[k]), int(self.ptr[k + 1])
+        v = np.ones(e - s) if self.val is None else self.val[s:e].astype(np.float64)
+        return self.idx[s:e].astype(np.int64), v
+
+
+def total_terms(A: Compressed, B: Compressed) -> int:
+    """``sum_k |a_k| |b_k|``: the number of nonzero terms over all outer
+    products (Section 6, Table 2 counts these as "# of pairs")."""
+    la = np.diff(A.ptr)
+    lb = np.diff(B.ptr)
+    return int(np.dot(la.astype(np.int64), lb.astype(np.int64)))
+
+
+def dense(X: Compressed, n_major: int | None = None) -> np.ndarray:
+    """Dense (n_major x n_minor) fp64 array of a compressed matrix."""
+    n_major = X.n_major if n_major is None else n_major
+    D = np.zeros((n_major, X.n_minor))
+    for k in range(X.n_major):
+        ii, vv = X.vector(k)
+        D[k, ii] += vv
+    return D
+
+
+# ---------------------------------------------------------------------------
+# Column-row product (Preliminaries, Notation)
+# ---------------------------------------------------------------------------
+
+def outer_product_terms(A: Compressed, B: Compressed, k0: int, k1: int, mode: int = FULL):
+    """All nonzero terms ``a_k(i) b_k(j)`` of the outer products k in [k0, k1),
+    in stream order: k ascending, then the order of a_k, then the order of b_k
+    (i ascending, j ascending for sorted inputs).
+
+    A holds the columns a_k (compressed by k, indices i), B the rows b_k
+    (compressed by k, indices j).  Returns (k, i, j, w) arrays; w is the fp64
+    product of the two fp32 values (exact: 24+24 mantissa bits fit in 53)."""
+    la = np.diff(A.ptr[k0:k1 + 1])
+    lb = np.diff(B.ptr[k0:k1 + 1])
+    nt = la * lb
+    T = int(nt.sum())
+    ks = np.repeat(np.arange(k0, k1, dtype=np.int64), nt)
+    start = np.cumsum(nt) - nt
+    t = np.arange(T, dtype=np.int64) - np.repeat(start, nt)
+    lbk = np.repeat(lb, nt)
+    ia = A.ptr[ks] + t // np.maximum(lbk, 1)
+    jb = B.ptr[ks] + t % np.maximum(lbk, 1)
+    i = A.idx[ia].astype(np.int64)
+    j = B.idx[jb].astype(np.int64)
+    if A.val is None and B.val is None:
+        w = np.ones(T)
+    else:
+        wa = np.ones(T) if A.val is None else A.val[ia].astype(np.float64)
+        wb = np.ones(T) if B.val is None else B.val[jb].astype(np.float64)
+        w = wa * wb
+    if mode == UPPER:
+        keep = i < j
+        ks, i, j, w = ks[keep], i[keep], j[keep], w[keep]
+    return ks, i, j, w
+
+
+def exact_product_loop(A: Compressed, B: Compressed, mode: int = FULL) -> dict:
+    """The definition written as loops: for each k, for each i in a_k, for
+    each j in b_k, ``C[(i, j)] += a_k(i) b_k(j)``.  For tiny inputs only."""
+    C: dict = {}
+    for k in range(A.n_major):
+        ii, va = A.vector(k)
+        jj, vb = B.vector(k)
+        for x in range(len(ii)):
+            for y in range(len(jj)):
+                i, j = int(ii[x]), int(jj[y])
+                if mode == UPPER and not i < j:
+                    continue
+                C[(i, j)] = C.get((i, j), 0.0) + float(va[x]) * float(vb[y])
+    return C
+
+
+@dataclass
+class Product:
+    """Nonzero entries of C sorted by (i, j): arrays i, j, w (fp64; counts are
+    exact integers in fp64 up to 2^53) and the number of terms processed."""
+    i: np.ndarray
+    j: np.ndarray
+    w: np.ndarray
+    terms: int
+    n_cols: int
+
+    def keys(self) -> np.ndarray:
+        return self.i * self.n_cols + self.j
+
+    def as_dict(self) -> dict:
+        return {(int(a), int(b)): float(c) for a, b, c in zip(self.i, self.j, self.w)}
+
+
+def _reduce(keys: np.ndarray, w: np.ndarray):
+    uk, inv = np.unique(keys, return_inverse=True)
+    return uk, np.bincount(inv, weights=w, minlength=len(uk))
+
+
+def exact_product(A: Compressed, B: Compressed, mode: int = FULL,
+                  chunk_terms: int = 20_000_000) -> Product:
+    """C = sum_k a_k b_k exactly: every term of every outer product is added
+    into its entry.  Terms are generated a range of k at a time; equal keys
+    are summed with a sort (np.unique) and a bincount."""
+    n_cols = B.n_minor
+    la = np.diff(A.ptr)
+    lb = np.diff(B.ptr)
+    nt = np.cumsum(la.astype(np.int64) * lb.astype(np.int64))
+    K = A.n_major
+    parts_k, parts_w = [], []
+    terms = 0
+    k0 = 0
+    while k0 < K:
+        base = nt[k0 - 1] if k0 else 0
+        k1 = int(np.searchsorted(nt, base + chunk_terms, side="right"))
+        k1 = max(k1, k0 + 1)
+        k1 = min(k1, K)
+        _, i, j, w = outer_product_terms(A, B, k0, k1, mode)
+        terms += len(i)
+        uk, uw = _reduce(i * n_cols + j, w)
+        parts_k.append(uk)
+        parts_w.append(uw)
+        k0 = k1
+    if parts_k:
+        uk, uw = _reduce(np.concatenate(parts_k), np.concatenate(parts_w))
+    else:
+        uk, uw = np.zeros(0, np.int64), np.zeros(0)
+    return Product(uk // n_cols, uk % n_cols, uw, terms, n_cols)
+
+
+def split_by_partition(prod: Product, P: int, seed_a: int, seed_b: int) -> list[Product]:
+    """Per-partition tables: entry (i, j) goes to partition h(i, j) and to no
+    other (Lemma 1; Section 4 "Our approach")."""
+    p = partition_of(prod.i, prod.j, P, seed_a, seed_b)
+    out = []
+    for q in range(P):
+        m = p == q
+        out.append(Product(prod.i[m], prod.j[m], prod.w[m], -1, prod.n_cols))
+    return out
+
+
+def partition_term_counts(A: Compressed, B: Compressed, P: int, seed_a: int, seed_b: int,
+                          mode: int = FULL, chunk_terms: int = 20_000_000) -> np.ndarray:
+    """Number of terms (not entries) of all outer products landing in each
+    partition: the per-processor work of Theorem 1 / Table 4."""
+    la = np.diff(A.ptr)
+    lb = np.diff(B.ptr)
+    nt = np.cumsum(la.astype(np.int64) * lb.astype(np.int64))
+    out = np.zeros(P, dtype=np.int64)
+    K = A.n_major
+    k0 = 0
+    while k0 < K:
+        base = nt[k0 - 1] if k0 else 0
+        k1 = min(max(int(np.searchsorted(nt, base + chunk_terms, side="right")), k0 + 1), K)
+        _, i, j, _ = outer_product_terms(A, B, k0, k1, mode)
+        out += np.bincount(partition_of(i, j, P, seed_a, seed_b), minlength=P)
+        k0 = k1
+    return out
+
+
+def interval_terms(a_idx, a_val, b_idx, b_val, q: int, r: int, P: int, seed_a: int,
+                   seed_b: int):
+    """``E_L^{ab}`` for ``L = [q, r)`` (Lemma 1): the entries of the single
+    outer product ``ab`` whose hash lies in [q, r), found by testing every
+    pair.  Returns a list of (i, j, w) in (a order, b order)."""
+    out = []
+    for x in range(len(a_idx)):
+        for y in range(len(b_idx)):
+            i, j = int(a_idx[x]), int(b_idx[y])
+            h = int(partition_of(np.array([i]), np.array([j]), P, seed_a, seed_b)[0])
+            if q <= h < r:
+                out.append((i, j, float(a_val[x]) * float(b_val[y])))
+    return out
+
+
+def entry(A_rows: Compressed, B_cols: Compressed, i: int, j: int) -> float:
+    """One entry by its definition as an inner product: row i of A (compressed
+    by i, indices k) times column j of B (compressed by j, indices k)."""
+    ka, va = A_rows.vector(i)
+    kb, vb = B_cols.vector(j)
+    common, xa, xb = np.intersect1d(ka, kb, assume_unique=True, return_indices=True)
+    return float(np.dot(va[xa], vb[xb]))
+
+
+# ---------------------------------------------------------------------------
+# Heaviest entries (Section 6)
+# ---------------------------------------------------------------------------
+
+def topk(i: np.ndarray, j: np.ndarray, w: np.ndarray, k: int, upper_only: bool = False):
+    """The k heaviest entries ordered by weight descending, then i, then j
+    ascending.  ``upper_only`` keeps pairs i < j only."""
+    i = np.asarray(i, np.int64)
+    j = np.asarray(j, np.int64)
+    w = np.asarray(w, np.float64)
+    if upper_only:
+        m = i < j
+        i, j, w = i[m], j[m], w[m]
+    order = np.lexsort((j, i, -np.abs(w)))[:k]
+    return i[order], j[order], w[order]
+
+
+# ---------------------------------------------------------------------------
+# Space-Saving (Preliminaries)
+# ---------------------------------------------------------------------------
+
+def space_saving(stream, ell: int) -> dict:
+    """Weighted Space-Saving over a stream of (key, w), w > 0, with ``ell``
+    counters.  Returns {key: (count, overestimation)}; the upper bound on the
+    key's weight is ``count`` and the lower bound ``count - overestimation``.
+
+    * key already recorded: count += w;
+    * a free counter: record (key, w, 0);
+    * otherwise the counter of minimum count (ties: smallest key) is given to
+      the key as (key, min + w, min).
+    A lazy heap of (count, key) finds the minimum."""
+    summ: dict = {}
+    heap: list = []
+    for key, w in stream:
+        if key in summ:
+            c, o = summ[key]
+            summ[key] = (c + w, o)
+            heapq.heappush(heap, (c + w, key))
+        elif len(summ) < ell:
+            summ[key] = (w, 0)
+            heapq.heappush(heap, (w, key))
+        else:
+            while True:
+                c, victim = heapq.heappop(heap)
+                if victim in summ and summ[victim][0] == c:
+                    break
+            del summ[victim]
+            summ[key] = (c + w, c)
+            heapq.heappush(heap, (c + w, key))
+    return summ
+
+
+def partition_streams(A: Compressed, B: Compressed, P: int, seed_a: int, seed_b: int,
+                      mode: int = FULL):
+    """Per-partition term streams in stream order (k ascending, then i, then
+    j): the input each Space-Saving summary of the CRoP algorithm sees
+    (Figure 1: entries of each outer product go to the summary of their
+    bucket)."""
+    ks, i, j, w = outer_product_terms(A, B, 0, A.n_major, mode)
+    order = np.lexsort((j, i, ks))
+    ks, i, j, w = ks[order], i[order], j[order], w[order]
+    p = partition_of(i, j, P, seed_a, seed_b)
+    n_cols = B.n_minor
+    out = []
+    for q in range(P):
+        m = p == q
+        out.append(list(zip((i[m] * n_cols + j[m]).tolist(), w[m].tolist())))
+    return out
