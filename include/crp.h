@@ -1,0 +1,203 @@
+/*
+ * crp.h -- C ABI of the column-row partitioned sparse product on GB300.
+ *
+ * The library computes C = A B as the sum of outer products of the columns
+ * of A and the rows of B (the column-row method; paper "On Parallelizing
+ * Matrix Multiplication by the Column-Row Method", Campagna, Kutzkov, Pagh:
+ * Preliminaries, Notation: the weight of entry (i,j) is sum_k a_k(i) b_k(j)).
+ * Every output entry (i,j) belongs to exactly one of P hash partitions,
+ *     h(i,j) = (h_a(i) + h_b(j)) mod P                      (Section 4, Lemma 1)
+ * whatever the structure of the outer product it appears in, so partitions
+ * are accumulated independently (Section 4, "Our approach": CRoP).  Each
+ * partition holds either an exact table of its entries or a counter summary
+ * with Space-Saving guarantees (Preliminaries; Figure 1).
+ *
+ * Conventions for every call below:
+ *  - Indices are 0-based ([n] = {0..n-1}, Preliminaries).
+ *  - "device" pointers are CUDA device (or managed) memory of the device that
+ *    was current at crp_plan_create; "host or device" pointers are detected
+ *    with cudaPointerGetAttributes.
+ *  - The caller owns every buffer it passes; the plan owns its tables,
+ *    summaries and scratch, which crp_plan_destroy frees.
+ *  - Work is enqueued on the plan's stream and is asynchronous; errors the
+ *    host can see are returned at once, errors the device records (a full
+ *    table, an index out of range) are returned by crp_sync.
+ *  - No call throws, traps or aborts.  A plan is not thread-safe.
+ *  - crp_last_error() returns a message for the calling thread's last error.
+ *
+ * Hash family (a reading: the paper only requires pairwise independent
+ * h_a, h_b, Lemma 1).  With s = seed_a (resp. seed_b), (a, b) are the first
+ * two outputs of SplitMix64 started from state s, and for a 32-bit index x
+ *     h(x) = ((a*x + b) mod 2^64) >> (64 - log2 P)     (multiply-add-shift)
+ * P must be a power of two; P = 1 puts everything in partition 0.
+ */
+#ifndef CRP_H
+#define CRP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CRP_OK = 0,
+    CRP_EINVAL = 1,          /* bad argument or descriptor */
+    CRP_ENOMEM = 2,          /* device allocation failed */
+    CRP_ETABLE_FULL = 3,     /* a partition table ran out of slots and the
+                                entries could not be kept */
+    CRP_ETIMEOUT = 4,        /* a bounded device wait gave up */
+    CRP_ECUDA = 5,           /* CUDA runtime error (message in last_error) */
+    CRP_EUNSUPPORTED = 6     /* valid but outside what this build handles */
+} crp_status;
+
+/* value_type */
+enum { CRP_I32 = 0,          /* {0,1} inputs (val == NULL), exact int32 counts */
+       CRP_F32_COMP = 1 };   /* fp32 inputs, exact fp32 products, compensated
+                                fp32 (TwoSum) on chip, fp64 per-entry result */
+/* mode */
+enum { CRP_FULL = 0,         /* every entry (i,j) */
+       CRP_UPPER = 1 };      /* only i < j: pairs above the diagonal, the
+                                frequent-pair view of T^T T (Section 6) */
+/* crp_topk flags */
+enum { CRP_TOPK_UPPER = 1 }; /* report only i < j */
+/* crp_plan_desc.flags */
+enum { CRP_PLAN_NO_WARP_MATCH = 1,  /* skip __match_any_sync pre-combining */
+       CRP_PLAN_DEBUG_CHECKS = 2 }; /* bounds-check every index on device */
+
+/* A compressed sparse matrix viewed as K vectors: vector k holds indices
+ * idx[ptr[k] .. ptr[k+1]) (each < n_minor, distinct within a vector) with
+ * values val[...] (val == NULL: all ones).  A is passed compressed by column
+ * (CSC: vector k = column a_k, indices i) and B compressed by row (CSR:
+ * vector k = row b_k, indices j); the paper stores A as column-major and B
+ * as row-major triples (Section 4, "The algorithm").  For co-occurrence
+ * counts T^T T of a transaction matrix T (CSR, rows = transactions) pass the
+ * same CSR of T as both A and B (Section 6).  ptr, idx, val: device. */
+typedef struct {
+    int64_t n_major;        /* K, the number of vectors */
+    int32_t n_minor;        /* index range */
+    int32_t _pad;
+    int64_t nnz;            /* ptr[n_major] */
+    const int64_t *ptr;     /* device, n_major + 1 entries, ptr[0] == 0 */
+    const int32_t *idx;     /* device, nnz entries */
+    const float *val;       /* device, nnz entries, or NULL */
+} crp_sparse;
+
+typedef struct {
+    int32_t n_rows, n_cols;       /* C is n_rows x n_cols */
+    uint32_t P;                   /* partitions (power of two, >= 1) */
+    uint32_t _pad0;
+    uint64_t seed_a, seed_b;      /* hash seeds of h_a and h_b */
+    int32_t value_type;           /* CRP_I32 | CRP_F32_COMP */
+    int32_t mode;                 /* CRP_FULL | CRP_UPPER */
+    uint32_t summary_counters;    /* 0: exact tables; else counters per
+                                     partition of a Space-Saving summary */
+    uint32_t reserved_counters;   /* summary mode: exact counters for keys
+                                     registered with crp_reserve (0 = none) */
+    uint64_t table_capacity_hint; /* total exact-table slots wanted (0: the
+                                     library sizes from the input of the first
+                                     crp_outer_accumulate) */
+    int32_t auto_grow;            /* exact mode: on a full partition keep the
+                                     overflow in a spill list and grow that
+                                     partition at crp_sync */
+    uint32_t groups;              /* partition groups G (passes over the input;
+                                     one CTA work item covers P/G partitions);
+                                     0 = default */
+    uint32_t tile_vectors;        /* outer products per work item; 0 = default */
+    uint32_t smem_slots;          /* on-chip combining table slots per CTA
+                                     (power of two); 0 = default */
+    uint32_t flags;               /* CRP_PLAN_* */
+    uint32_t _pad1;
+} crp_plan_desc;
+
+typedef struct crp_plan crp_plan;
+
+typedef struct {
+    uint64_t terms;               /* outer-product terms enumerated */
+    uint64_t flushed_updates;     /* on-chip entries flushed to partition
+                                     tables (terms / this = combining ratio) */
+    uint64_t entries;             /* live entries in all partitions */
+    uint64_t table_slots;         /* allocated exact-table slots */
+    uint64_t spilled;             /* updates held in the spill list */
+    uint32_t full_partitions;     /* partitions that ran out of slots */
+    uint32_t P;
+    double max_over_mean_terms;   /* largest / mean per-partition terms (int
+                                     mode; Theorem 1, Table 4) */
+    double last_accumulate_ms;    /* device time of the last enumeration /
+                                     combining kernel (CUDA events on the
+                                     plan's stream) */
+    uint64_t launches;            /* kernels this plan has launched */
+} crp_stats_t;
+
+/* Create a plan: validates desc, derives the hash parameters and allocates
+ * the partition tables (exact mode) or summaries (summary mode) on the
+ * current device.  stream: a cudaStream_t (NULL = legacy default stream).
+ * Returns CRP_EINVAL for a P that is not a power of two, n_rows/n_cols <= 0,
+ * an unknown value_type/mode, or smem_slots not a power of two. */
+crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc, void *stream);
+
+/* Free everything the plan owns (NULL is accepted). */
+void crp_plan_destroy(crp_plan *plan);
+
+/* Zero all partition tables / summaries and statistics (capacity is kept). */
+crp_status crp_reset(crp_plan *plan);
+
+/* Add sum_k a_k b_k over the K outer products of A (CSC) and B (CSR) into
+ * the partition tables (Figure 1, CRoP: for each k hash every entry of a_k
+ * b_k to its partition and update that partition's table or summary).
+ * Additive across calls, so a stream is processed in chunks of k.
+ * A->n_major must equal B->n_major, A->n_minor == n_rows, B->n_minor ==
+ * n_cols.  CRP_I32 requires A->val == B->val == NULL.  In CRP_UPPER mode
+ * only terms with i < j are added.  Asynchronous: a full table or a bad index
+ * is reported by crp_sync. */
+crp_status crp_outer_accumulate(crp_plan *plan, const crp_sparse *A_csc, const crp_sparse *B_csr);
+
+/* Wait for the plan's stream and return the status the device recorded
+ * (CRP_ETABLE_FULL, CRP_EINVAL for an index >= n_minor when
+ * CRP_PLAN_DEBUG_CHECKS is set, CRP_ETIMEOUT).  With auto_grow, full
+ * partitions are grown and their spilled updates re-inserted first. */
+crp_status crp_sync(crp_plan *plan);
+
+/* The k heaviest entries (largest |weight|; ties by i then j ascending),
+ * written in that order to i_out, j_out, w_out (host or device, k entries
+ * each); w_lower (nullable) receives the lower bound in summary mode and the
+ * weight itself in exact mode.  *n_out (host) = entries written (< k when C
+ * has fewer nonzero entries).  flags: CRP_TOPK_UPPER.  1 <= k <= 8192.
+ * Synchronises the plan's stream. */
+crp_status crp_topk(crp_plan *plan, int32_t k, uint32_t flags, int32_t *i_out, int32_t *j_out,
+                    double *w_out, double *w_lower, int32_t *n_out);
+
+/* Partition of entry (i,j): (h_a(i) + h_b(j)) mod P, computed on the host. */
+uint32_t crp_partition_of(const crp_plan *plan, int32_t i, int32_t j);
+
+/* Copy the entries of partitions [p_begin, p_end) to i_out, j_out, w_out
+ * (and w_lower, nullable; host or device; `capacity` entries each), grouped
+ * by partition in ascending order, unordered within a partition.  *n_out =
+ * number of entries in those partitions, even when it exceeds capacity (then
+ * nothing is written and CRP_EINVAL is returned).  Synchronises. */
+crp_status crp_export_partitions(crp_plan *plan, uint32_t p_begin, uint32_t p_end, int32_t *i_out,
+                                 int32_t *j_out, double *w_out, double *w_lower,
+                                 int64_t capacity, int64_t *n_out);
+
+/* Per-partition term counts (int mode: sum of the counts in the partition)
+ * into terms_out (host, P entries, nullable) and aggregate statistics into
+ * *stats.  Synchronises. */
+crp_status crp_stats(crp_plan *plan, crp_stats_t *stats, uint64_t *terms_out);
+
+/* Device time of the last enumeration kernel launched by crp_outer_accumulate
+ * (CUDA events on the plan's stream; waits for that kernel) and the number of
+ * kernels the plan has launched so far.  Either pointer may be NULL.  Cheap:
+ * it does not scan the tables. */
+crp_status crp_timing(crp_plan *plan, double *accumulate_ms, uint64_t *launches);
+
+/* Library version string. */
+const char *crp_version(void);
+
+/* Message for the calling thread's last error ("" if none). */
+const char *crp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRP_H */

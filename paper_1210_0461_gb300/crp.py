@@ -1,0 +1,285 @@
+"""ctypes binding of libcrp (include/crp.h): argument marshalling only.
+
+Every step of the product runs in the CUDA kernels of libcrp.so; this module
+only builds the C structs, passes device pointers taken from torch tensors and
+the current torch stream, and turns status codes into exceptions.  There is no
+CPU path: if the library is missing the import of :func:`lib` fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcrp.so")
+
+CRP_OK, CRP_EINVAL, CRP_ENOMEM, CRP_ETABLE_FULL, CRP_ETIMEOUT, CRP_ECUDA, CRP_EUNSUPPORTED = range(7)
+STATUS_NAMES = {0: "CRP_OK", 1: "CRP_EINVAL", 2: "CRP_ENOMEM", 3: "CRP_ETABLE_FULL",
+                4: "CRP_ETIMEOUT", 5: "CRP_ECUDA", 6: "CRP_EUNSUPPORTED"}
+CRP_I32, CRP_F32_COMP = 0, 1
+CRP_FULL, CRP_UPPER = 0, 1
+CRP_TOPK_UPPER = 1
+CRP_PLAN_NO_WARP_MATCH, CRP_PLAN_DEBUG_CHECKS = 1, 2
+
+
+class CrpError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class crp_sparse(ctypes.Structure):
+    _fields_ = [("n_major", ctypes.c_int64), ("n_minor", ctypes.c_int32),
+                ("_pad", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("ptr", ctypes.c_void_p), ("idx", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class crp_plan_desc(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int32), ("n_cols", ctypes.c_int32),
+                ("P", ctypes.c_uint32), ("_pad0", ctypes.c_uint32),
+                ("seed_a", ctypes.c_uint64), ("seed_b", ctypes.c_uint64),
+                ("value_type", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("summary_counters", ctypes.c_uint32), ("reserved_counters", ctypes.c_uint32),
+                ("table_capacity_hint", ctypes.c_uint64), ("auto_grow", ctypes.c_int32),
+                ("groups", ctypes.c_uint32), ("tile_vectors", ctypes.c_uint32),
+                ("smem_slots", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("_pad1", ctypes.c_uint32)]
+
+
+class crp_stats_t(ctypes.Structure):
+    _fields_ = [("terms", ctypes.c_uint64), ("flushed_updates", ctypes.c_uint64),
+                ("entries", ctypes.c_uint64), ("table_slots", ctypes.c_uint64),
+                ("spilled", ctypes.c_uint64), ("full_partitions", ctypes.c_uint32),
+                ("P", ctypes.c_uint32), ("max_over_mean_terms", ctypes.c_double),
+                ("last_accumulate_ms", ctypes.c_double), ("launches", ctypes.c_uint64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "crp_plan_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(crp_plan_desc), _P]),
+    "crp_plan_destroy": (None, [_P]),
+    "crp_reset": (ctypes.c_int, [_P]),
+    "crp_outer_accumulate": (ctypes.c_int, [_P, ctypes.POINTER(crp_sparse),
+                                            ctypes.POINTER(crp_sparse)]),
+    "crp_sync": (ctypes.c_int, [_P]),
+    "crp_topk": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32, _P, _P, _P, _P,
+                                ctypes.POINTER(ctypes.c_int32)]),
+    "crp_partition_of": (ctypes.c_uint32, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "crp_export_partitions": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint32, _P, _P, _P, _P,
+                                             ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "crp_stats": (ctypes.c_int, [_P, ctypes.POINTER(crp_stats_t), _P]),
+    "crp_timing": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_uint64)]),
+    "crp_version": (ctypes.c_char_p, []),
+    "crp_last_error": (ctypes.c_char_p, []),
+}
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def lib() -> ctypes.CDLL:
+    """Load libcrp.so.  Raises when it has not been built (there is no
+    fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libcrp.so is not built ({LIB_PATH}); run "
+                                  "paper_1210_0461_gb300._build.build() first")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(st: int, where: str):
+    if st != CRP_OK:
+        raise CrpError(st, where, lib().crp_last_error().decode())
+
+
+# ---------------------------------------------------------------------------
+# Device-side inputs
+# ---------------------------------------------------------------------------
+
+@dataclass
+class DeviceSparse:
+    """K compressed vectors held in torch tensors on a CUDA device."""
+    ptr: "object"     # torch.int64 [K+1]
+    idx: "object"     # torch.int32 [nnz]
+    val: "object"     # torch.float32 [nnz] or None
+    n_minor: int
+
+    @property
+    def n_major(self) -> int:
+        return int(self.ptr.shape[0]) - 1
+
+    @property
+    def nnz(self) -> int:
+        return int(self.idx.shape[0])
+
+    def c_struct(self) -> crp_sparse:
+        s = crp_sparse()
+        s.n_major = self.n_major
+        s.n_minor = self.n_minor
+        s.nnz = self.nnz
+        s.ptr = self.ptr.data_ptr()
+        s.idx = self.idx.data_ptr() if self.nnz else 0
+        s.val = self.val.data_ptr() if self.val is not None and self.nnz else None
+        return s
+
+    def nbytes(self) -> int:
+        b = self.ptr.numel() * 8 + self.idx.numel() * 4
+        return b + (self.val.numel() * 4 if self.val is not None else 0)
+
+
+def to_device(sp, device="cuda", pin: bool = False) -> DeviceSparse:
+    """Copy a host compressed matrix (any object with ptr, idx, val, n_minor
+    numpy arrays) to the device."""
+    import torch
+    ptr = torch.from_numpy(np.ascontiguousarray(sp.ptr, dtype=np.int64))
+    idx = torch.from_numpy(np.ascontiguousarray(sp.idx, dtype=np.int32))
+    val = None if sp.val is None else torch.from_numpy(np.ascontiguousarray(sp.val, np.float32))
+    if pin:
+        ptr, idx = ptr.pin_memory(), idx.pin_memory()
+        val = val.pin_memory() if val is not None else None
+    return DeviceSparse(ptr.to(device, non_blocking=pin), idx.to(device, non_blocking=pin),
+                        None if val is None else val.to(device, non_blocking=pin), int(sp.n_minor))
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# Plan
+# ---------------------------------------------------------------------------
+
+class Plan:
+    """An exact column-row product plan: P hash partitions, each with its own
+    open-addressing table in device memory (see include/crp.h)."""
+
+    def __init__(self, n_rows: int, n_cols: int, P: int, seed_a: int, seed_b: int,
+                 value_type: int = CRP_I32, mode: int = CRP_FULL, groups: int = 0,
+                 tile_vectors: int = 0, smem_slots: int = 0, capacity_hint: int = 0,
+                 auto_grow: bool = False, flags: int = 0, stream=None):
+        self._lib = lib()
+        d = crp_plan_desc()
+        d.n_rows, d.n_cols, d.P = n_rows, n_cols, P
+        d.seed_a, d.seed_b = seed_a & (2**64 - 1), seed_b & (2**64 - 1)
+        d.value_type, d.mode = value_type, mode
+        d.table_capacity_hint = capacity_hint
+        d.auto_grow = 1 if auto_grow else 0
+        d.groups, d.tile_vectors, d.smem_slots, d.flags = groups, tile_vectors, smem_slots, flags
+        self.desc = d
+        self.P = P
+        self.value_type = value_type
+        self._stream = stream
+        h = _P()
+        _check(self._lib.crp_plan_create(ctypes.byref(h), ctypes.byref(d), _stream_handle(stream)),
+               "crp_plan_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.crp_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def reset(self):
+        _check(self._lib.crp_reset(self._h), "crp_reset")
+
+    def accumulate(self, A: DeviceSparse, B: DeviceSparse):
+        a, b = A.c_struct(), B.c_struct()
+        _check(self._lib.crp_outer_accumulate(self._h, ctypes.byref(a), ctypes.byref(b)),
+               "crp_outer_accumulate")
+
+    def sync(self):
+        _check(self._lib.crp_sync(self._h), "crp_sync")
+
+    def partition_of(self, i: int, j: int) -> int:
+        return int(self._lib.crp_partition_of(self._h, i, j))
+
+    def topk(self, k: int, upper: bool = False, device_out=None):
+        """(i, j, w, w_lower) of the k heaviest entries, numpy arrays (or torch
+        tensors on ``device_out``)."""
+        n = ctypes.c_int32(0)
+        flags = CRP_TOPK_UPPER if upper else 0
+        if device_out is not None:
+            import torch
+            i = torch.empty(k, dtype=torch.int32, device=device_out)
+            j = torch.empty(k, dtype=torch.int32, device=device_out)
+            w = torch.empty(k, dtype=torch.float64, device=device_out)
+            wl = torch.empty(k, dtype=torch.float64, device=device_out)
+            ptrs = [t.data_ptr() for t in (i, j, w, wl)]
+        else:
+            i = np.zeros(k, np.int32)
+            j = np.zeros(k, np.int32)
+            w = np.zeros(k, np.float64)
+            wl = np.zeros(k, np.float64)
+            ptrs = [t.ctypes.data for t in (i, j, w, wl)]
+        _check(self._lib.crp_topk(self._h, k, flags, *ptrs, ctypes.byref(n)), "crp_topk")
+        m = n.value
+        return i[:m], j[:m], w[:m], wl[:m]
+
+    def export(self, p_begin: int = 0, p_end: int | None = None):
+        """All entries of partitions [p_begin, p_end): (i, j, w, w_lower, counts
+        per partition) as numpy arrays."""
+        p_end = self.P if p_end is None else p_end
+        n = ctypes.c_int64(0)
+        st = self._lib.crp_export_partitions(self._h, p_begin, p_end, None, None, None, None, 0,
+                                             ctypes.byref(n))
+        if st not in (CRP_OK, CRP_EINVAL) or (st == CRP_EINVAL and n.value == 0):
+            _check(st, "crp_export_partitions")
+        cap = n.value
+        i = np.zeros(cap, np.int32)
+        j = np.zeros(cap, np.int32)
+        w = np.zeros(cap, np.float64)
+        wl = np.zeros(cap, np.float64)
+        if cap:
+            _check(self._lib.crp_export_partitions(self._h, p_begin, p_end, i.ctypes.data,
+                                                   j.ctypes.data, w.ctypes.data, wl.ctypes.data,
+                                                   cap, ctypes.byref(n)), "crp_export_partitions")
+        return i, j, w, wl
+
+    def timing(self):
+        """(device ms of the last enumeration kernel, kernels launched so far)."""
+        ms = ctypes.c_double(0)
+        n = ctypes.c_uint64(0)
+        _check(self._lib.crp_timing(self._h, ctypes.byref(ms), ctypes.byref(n)), "crp_timing")
+        return ms.value, n.value
+
+    def stats(self, per_partition: bool = False):
+        s = crp_stats_t()
+        terms = np.zeros(self.P, np.uint64) if per_partition else None
+        _check(self._lib.crp_stats(self._h, ctypes.byref(s),
+                                   terms.ctypes.data if terms is not None else None), "crp_stats")
+        d = {f: getattr(s, f) for f, _ in crp_stats_t._fields_}
+        if per_partition:
+            d["partition_terms"] = terms
+        return d

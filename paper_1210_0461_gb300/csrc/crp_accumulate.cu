@@ -1,0 +1,716 @@
+// Column-row accumulation kernels.
+//
+//  * k_sort_by_hash: for every outer product k, the entries of b_k sorted by
+//    h_b (the array H_b of Lemma 1 / Figure 1 "Hash", first step).
+//  * k_accumulate: the CRoP loop of Figure 1 for a set of partition groups.
+//    A work item is (tile of outer products, partition group g).  For each k
+//    of the tile a warp enumerates exactly the entries of a_k b_k whose hash
+//    lies in group g's interval [q, q + P/G) (Lemma 1: for each i, the j with
+//    h_b(j) in the cyclic window [(q - h_a(i)) mod P, +P/G) form at most two
+//    runs of H_b), spreads those terms over its 32 lanes, combines equal keys
+//    of the warp with __match_any_sync, and adds them into a shared-memory
+//    open-addressing table.  When the table passes its fill threshold the CTA
+//    flushes it into the per-partition exact tables in HBM.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "crp_internal.cuh"
+
+namespace crp {
+
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
+constexpr int kRoundChunks = 4;                       // chunks of 32 terms per warp per round
+constexpr int kMaxNewPerRound = kWarps * kRoundChunks * 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+int accumulate_block_threads() { return kThreads; }
+
+size_t accumulate_smem_bytes(int value_type, uint32_t S) {
+    size_t v = value_type == CRP_I32 ? 4 : 8;
+    return (size_t)S * (8 + v) + 64;
+}
+
+// ---------------------------------------------------------------------------
+// Partition-table update (HBM)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void spill_update(const TableView &tv, unsigned long long key,
+                                             unsigned long long v) {
+    unsigned long long at = atomicAdd(&tv.dc->spill_n, 1ull);
+    if (at < tv.spill_cap) {
+        tv.spill[at].key = key;
+        tv.spill[at].val = v;
+    } else {
+        atomicOr(&tv.dc->status, kStatusSpillFull);
+    }
+}
+
+// Add v (u32 count, or the bits of a double) to entry `key` of partition p.
+__device__ __forceinline__ void table_update(const TableView &tv, uint32_t p,
+                                             unsigned long long key, unsigned long long v) {
+    if (*(volatile unsigned int *)&tv.part_full[p]) {
+        spill_update(tv, key, v);
+        return;
+    }
+    const unsigned long long off = tv.part_off[p];
+    const unsigned long long mask = tv.part_mask[p];
+    unsigned long long h = slot_mix(key) & mask;
+    for (unsigned long long probe = 0; probe <= mask; ++probe) {
+        Slot *s = tv.slots + off + h;
+        unsigned long long k = *(volatile unsigned long long *)&s->key;
+        if (k == kEmptyKey) {
+            k = atomicCAS(&s->key, kEmptyKey, key);
+            if (k == kEmptyKey) k = key;
+        }
+        if (k == key) {
+            if (tv.value_type == CRP_I32)
+                atomicAdd((unsigned int *)&s->val, (unsigned int)v);
+            else
+                atomicAdd((double *)&s->val, __longlong_as_double((long long)v));
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+    atomicOr(&tv.part_full[p], 1u);
+    atomicOr(&tv.dc->status, kStatusTableFull);
+    spill_update(tv, key, v);
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory combining table
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_slot(unsigned long long key, uint32_t mask) {
+    return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 40) & mask;
+}
+
+// Returns true when the key was new to the table.  The caller keeps the fill
+// below 75% so a free slot always exists; the probe bound is a guard only.
+__device__ __forceinline__ bool smem_find(unsigned long long *keys, uint32_t mask,
+                                          unsigned long long key, uint32_t &slot,
+                                          unsigned int *status) {
+    uint32_t h = smem_slot(key, mask);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        unsigned long long k = *(volatile unsigned long long *)&keys[h];
+        if (k == key) { slot = h; return false; }
+        if (k == kEmptyKey) {
+            unsigned long long prev = atomicCAS(&keys[h], kEmptyKey, key);
+            if (prev == kEmptyKey) { slot = h; return true; }
+            if (prev == key) { slot = h; return false; }
+        }
+        h = (h + 1) & mask;
+    }
+    atomicOr(status, kStatusSmemProbe);
+    slot = 0xffffffffu;
+    return false;
+}
+
+// fp32 TwoSum (Knuth): s + t == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &t) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Add the exact product p + e into a packed (sum, compensation) fp32 pair.
+__device__ __forceinline__ void smem_add_comp(unsigned long long *cell, float p, float e) {
+    unsigned long long old = *(volatile unsigned long long *)cell;
+    for (int guard = 0; guard < (1 << 20); ++guard) {
+        float s = __uint_as_float((unsigned int)(old >> 32));
+        float c = __uint_as_float((unsigned int)old);
+        float s1, t1;
+        two_sum(s, p, s1, t1);
+        float c1 = __fadd_rn(c, __fadd_rn(t1, e));
+        unsigned long long nw = ((unsigned long long)__float_as_uint(s1) << 32) | __float_as_uint(c1);
+        unsigned long long prev = atomicCAS(cell, old, nw);
+        if (prev == old) return;
+        old = prev;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-warp enumeration of the terms of a_k b_k that hash into one interval
+// ---------------------------------------------------------------------------
+
+struct WarpEnum {
+    int64_t k, k_hi;
+    int64_t a_cur, a_end;
+    int64_t b_beg;
+    int32_t b_len;
+    // this lane's a entry of the current batch of 32
+    uint32_t my_i;
+    float my_wa;
+    int32_t lo1, n1, lo2, excl;
+    int32_t total, pos;
+    bool has_batch, done;
+};
+
+__device__ __forceinline__ int32_t lower_bound_hash(const uint32_t *hb, int32_t n, uint32_t v) {
+    int32_t lo = 0, hi = n;
+    while (lo < hi) {
+        int32_t mid = (lo + hi) >> 1;
+        if (__ldg(hb + mid) < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void load_batch(WarpEnum &st, const AccumulateArgs &A,
+                                           const uint32_t *b_hash, uint32_t q, uint32_t w,
+                                           int lane) {
+    int64_t idx = st.a_cur + lane;
+    bool va = idx < st.a_end;
+    int32_t c = 0;
+    st.my_i = 0;
+    st.my_wa = 1.0f;
+    st.lo1 = 0; st.n1 = 0; st.lo2 = 0;
+    if (va) {
+        st.my_i = (uint32_t)__ldg(A.a_idx + idx);
+        if (A.a_val) st.my_wa = __ldg(A.a_val + idx);
+        if (A.groups == 1) {
+            st.n1 = st.b_len;
+            c = st.b_len;
+        } else {
+            const uint32_t P = A.hp.ha.mask + 1u;
+            uint32_t x = side_hash(A.hp.ha, st.my_i);
+            uint32_t s = (q - x) & (P - 1u);
+            uint32_t e = s + w;
+            const uint32_t *hb = b_hash + st.b_beg;
+            st.lo1 = lower_bound_hash(hb, st.b_len, s);
+            if (e <= P) {
+                int32_t hi = (e == P) ? st.b_len : lower_bound_hash(hb, st.b_len, e);
+                st.n1 = hi - st.lo1;
+                c = st.n1;
+            } else {
+                st.n1 = st.b_len - st.lo1;
+                int32_t n2 = lower_bound_hash(hb, st.b_len, e - P);
+                c = st.n1 + n2;
+            }
+        }
+    }
+    int32_t incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int32_t y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
+    }
+    st.total = __shfl_sync(kFull, incl, 31);
+    st.excl = incl - c;
+    st.pos = 0;
+    st.has_batch = true;
+}
+
+// Advance to the next batch with work.  Returns false when the tile is done.
+__device__ __forceinline__ bool advance(WarpEnum &st, const AccumulateArgs &A,
+                                        const uint32_t *b_hash, uint32_t q, uint32_t w,
+                                        int lane) {
+    while (true) {
+        if (st.has_batch && st.pos < st.total) return true;
+        if (st.has_batch) {
+            st.a_cur += 32;
+            st.has_batch = false;
+            if (st.a_cur < st.a_end) {
+                load_batch(st, A, b_hash, q, w, lane);
+                continue;
+            }
+        }
+        st.k += kWarps;
+        if (st.k >= st.k_hi) { st.done = true; return false; }
+        int64_t a0 = __ldg(A.a_ptr + st.k), a1 = __ldg(A.a_ptr + st.k + 1);
+        int64_t b0 = __ldg(A.b_ptr + st.k), b1 = __ldg(A.b_ptr + st.k + 1);
+        if (a1 == a0 || b1 == b0) continue;
+        st.a_cur = a0;
+        st.a_end = a1;
+        st.b_beg = b0;
+        st.b_len = (int32_t)(b1 - b0);
+        load_batch(st, A, b_hash, q, w, lane);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The accumulation kernel
+// ---------------------------------------------------------------------------
+
+template <int VT>
+__device__ void flush_table(unsigned long long *keys, void *vals, uint32_t S,
+                            const AccumulateArgs &A, unsigned long long &flushed) {
+    for (uint32_t s = threadIdx.x; s < S; s += kThreads) {
+        unsigned long long key = keys[s];
+        if (key == kEmptyKey) continue;
+        unsigned long long v;
+        if (VT == CRP_I32) {
+            v = ((unsigned int *)vals)[s];
+            ((unsigned int *)vals)[s] = 0u;
+        } else {
+            unsigned long long pk = ((unsigned long long *)vals)[s];
+            double d = (double)__uint_as_float((unsigned int)(pk >> 32)) +
+                       (double)__uint_as_float((unsigned int)pk);
+            v = (unsigned long long)__double_as_longlong(d);
+            ((unsigned long long *)vals)[s] = 0ull;
+        }
+        keys[s] = kEmptyKey;
+        uint32_t i = (uint32_t)(key >> 32), j = (uint32_t)key;
+        table_update(A.tv, partition_hash(A.hp, i, j), key, v);
+        ++flushed;
+    }
+}
+
+template <int VT>
+__global__ void __launch_bounds__(kThreads, 2)
+k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t S = A.smem_slots;
+    const uint32_t smask = S - 1u;
+    unsigned long long *keys = (unsigned long long *)smem_raw;
+    void *vals = (void *)(keys + S);
+    unsigned int *ctrl = (unsigned int *)((unsigned char *)vals + (size_t)S * (VT == CRP_I32 ? 4 : 8));
+    // ctrl[0] = fill, ctrl[1] = current work item
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+
+    for (uint32_t s = threadIdx.x; s < S; s += kThreads) {
+        keys[s] = kEmptyKey;
+        if (VT == CRP_I32) ((unsigned int *)vals)[s] = 0u;
+        else ((unsigned long long *)vals)[s] = 0ull;
+    }
+    if (threadIdx.x == 0) ctrl[0] = 0u;
+    __syncthreads();
+
+    const uint32_t threshold = (3u * S) / 4u - (uint32_t)kMaxNewPerRound;
+    const uint32_t P = A.hp.ha.mask + 1u;
+    const uint32_t w = P / A.groups;
+    const uint32_t n_groups_here = A.group_end - A.group_begin;
+    const unsigned long long total_items = (unsigned long long)A.n_tiles * n_groups_here;
+    unsigned long long my_terms = 0, flushed = 0;
+
+    while (true) {
+        if (threadIdx.x == 0) ctrl[1] = atomicAdd(&A.tv.dc->work_next, 1u);
+        __syncthreads();
+        const unsigned long long item = ctrl[1];
+        __syncthreads();
+        if (item >= total_items) break;
+        const uint32_t g = A.group_begin + (uint32_t)(item / A.n_tiles);
+        const uint64_t tile = item % A.n_tiles;
+        const uint32_t q = g * w;
+
+        WarpEnum st;
+        st.k = (int64_t)tile * A.tile + warp - kWarps;
+        st.k_hi = min((int64_t)A.K, (int64_t)(tile + 1) * A.tile);
+        st.has_batch = false;
+        st.done = false;
+        st.total = 0;
+        st.pos = 0;
+
+        while (true) {
+            for (int r = 0; r < kRoundChunks; ++r) {
+                if (st.done || !advance(st, A, b_hash, q, w, lane)) break;
+                // one chunk: lane takes flattened term pos + lane
+                const int32_t t = st.pos + lane;
+                bool valid = t < st.total;
+                int o = 0;
+#pragma unroll
+                for (int s2 = 16; s2 > 0; s2 >>= 1) {
+                    int32_t e = __shfl_sync(kFull, st.excl, o + s2);
+                    if (e <= t) o += s2;
+                }
+                const uint32_t oi = __shfl_sync(kFull, st.my_i, o);
+                const float owa = __shfl_sync(kFull, st.my_wa, o);
+                const int32_t olo1 = __shfl_sync(kFull, st.lo1, o);
+                const int32_t on1 = __shfl_sync(kFull, st.n1, o);
+                const int32_t olo2 = __shfl_sync(kFull, st.lo2, o);
+                const int32_t oex = __shfl_sync(kFull, st.excl, o);
+                st.pos += 32;
+                uint32_t j = 0;
+                float wb = 1.0f;
+                if (valid) {
+                    const int32_t off = t - oex;
+                    const int32_t m = off < on1 ? olo1 + off : olo2 + (off - on1);
+                    j = (uint32_t)__ldg(A.b_idx + st.b_beg + m);
+                    if (VT != CRP_I32 && A.b_val) wb = __ldg(A.b_val + st.b_beg + m);
+                    if (A.debug_checks && (oi >= (uint32_t)A.n_rows || j >= (uint32_t)A.n_cols)) {
+                        atomicOr(&A.tv.dc->status, kStatusBadIndex);
+                        valid = false;
+                    }
+                    if (A.mode == CRP_UPPER && !(oi < j)) valid = false;
+                }
+                const unsigned long long key = make_key(oi, j);
+                const unsigned act = __ballot_sync(kFull, valid);
+                my_terms += valid ? 1 : 0;
+                bool is_new = false;
+                if (VT == CRP_I32) {
+                    if (valid) {
+                        unsigned cnt = 1;
+                        bool lead = true;
+                        if (A.use_match) {
+                            unsigned peers = __match_any_sync(act, key);
+                            lead = lane == __ffs(peers) - 1;
+                            cnt = __popc(peers);
+                        }
+                        if (lead) {
+                            uint32_t slot;
+                            is_new = smem_find(keys, smask, key, slot, &A.tv.dc->status);
+                            if (slot != 0xffffffffu) atomicAdd(&((unsigned int *)vals)[slot], cnt);
+                        }
+                    }
+                } else {
+                    if (valid) {
+                        const float p = __fmul_rn(owa, wb);
+                        const float e = __fmaf_rn(owa, wb, -p);
+                        uint32_t slot;
+                        is_new = smem_find(keys, smask, key, slot, &A.tv.dc->status);
+                        if (slot != 0xffffffffu)
+                            smem_add_comp(&((unsigned long long *)vals)[slot], p, e);
+                    }
+                }
+                const unsigned nnew = __popc(__ballot_sync(kFull, is_new));
+                if (lane == 0 && nnew) atomicAdd(&ctrl[0], nnew);
+            }
+            const int more = __syncthreads_or(st.done ? 0 : 1);
+            if (ctrl[0] >= threshold) {
+                __syncthreads();
+                flush_table<VT>(keys, vals, S, A, flushed);
+                __syncthreads();
+                if (threadIdx.x == 0) ctrl[0] = 0u;
+                __syncthreads();
+            }
+            if (!more) break;
+        }
+    }
+    __syncthreads();
+    flush_table<VT>(keys, vals, S, A, flushed);
+
+    // aggregate counters: warp reduce then one atomic per warp
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        my_terms += __shfl_down_sync(kFull, my_terms, d);
+        flushed += __shfl_down_sync(kFull, flushed, d);
+    }
+    if (lane == 0) {
+        if (my_terms) atomicAdd(&A.tv.dc->terms, my_terms);
+        if (flushed) atomicAdd(&A.tv.dc->flushed, flushed);
+    }
+}
+
+cudaError_t launch_accumulate(const AccumulateArgs &args, const uint32_t *b_hash, int grid,
+                              cudaStream_t s) {
+    const size_t smem = accumulate_smem_bytes(args.tv.value_type, args.smem_slots);
+    cudaError_t e;
+    if (args.tv.value_type == CRP_I32) {
+        e = cudaFuncSetAttribute(k_accumulate<CRP_I32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        k_accumulate<CRP_I32><<<grid, kThreads, smem, s>>>(args, b_hash);
+    } else {
+        e = cudaFuncSetAttribute(k_accumulate<CRP_F32_COMP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_accumulate<CRP_F32_COMP><<<grid, kThreads, smem, s>>>(args, b_hash);
+    }
+    return cudaGetLastError();
+}
+
+int accumulate_max_blocks_per_sm(int value_type, uint32_t smem_slots) {
+    const size_t smem = accumulate_smem_bytes(value_type, smem_slots);
+    int n = 0;
+    if (value_type == CRP_I32) {
+        if (cudaFuncSetAttribute(k_accumulate<CRP_I32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_accumulate<CRP_I32>, kThreads, smem)
+            != cudaSuccess) return 0;
+    } else {
+        if (cudaFuncSetAttribute(k_accumulate<CRP_F32_COMP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_accumulate<CRP_F32_COMP>, kThreads,
+                                                          smem) != cudaSuccess) return 0;
+    }
+    return n;
+}
+
+// ---------------------------------------------------------------------------
+// H_b: entries of each b_k sorted by h_b (bitonic sort in shared memory)
+// ---------------------------------------------------------------------------
+
+constexpr int kSortWarpMax = 512;    // per-warp segment capacity (8 warps x 4 KB static smem)
+constexpr int kSortThreads = 256;
+constexpr int kSortBlockMax = 16384; // per-CTA capacity for long segments
+
+template <int CAP>
+__device__ __forceinline__ void bitonic_sort_u64(unsigned long long *v, int n_pow2, int tid,
+                                                 int nthreads, bool warp_only) {
+    for (int size = 2; size <= n_pow2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = tid; t < (n_pow2 >> 1); t += nthreads) {
+                int lo = 2 * t - (t & (stride - 1));
+                int hi = lo + stride;
+                bool up = (lo & size) == 0;
+                unsigned long long x = v[lo], y = v[hi];
+                if ((x > y) == up) { v[lo] = y; v[hi] = x; }
+            }
+            if (warp_only) __syncwarp(); else __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_sort_by_hash_warp(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                    const float *__restrict__ val, int64_t K, SideHash h,
+                    int32_t *__restrict__ out_idx, float *__restrict__ out_val,
+                    uint32_t *__restrict__ out_hash, DevCounters *dc, unsigned int *long_list) {
+    __shared__ unsigned long long buf[kSortThreads / 32][kSortWarpMax];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long *v = buf[warp];
+    const int64_t stride = (int64_t)gridDim.x * (kSortThreads / 32);
+    for (int64_t k = (int64_t)blockIdx.x * (kSortThreads / 32) + warp; k < K; k += stride) {
+        const int64_t b0 = ptr[k];
+        const int n = (int)(ptr[k + 1] - b0);
+        if (n == 0) continue;
+        if (n > kSortWarpMax) {
+            if (lane == 0) {
+                unsigned int at = atomicAdd(&dc->long_n, 1u);
+                long_list[at] = (unsigned int)k;
+            }
+            continue;
+        }
+        int np = 1;
+        while (np < n) np <<= 1;
+        for (int t = lane; t < np; t += 32) {
+            if (t < n) {
+                uint32_t j = (uint32_t)idx[b0 + t];
+                v[t] = ((unsigned long long)side_hash(h, j) << 32) | (uint32_t)t;
+            } else {
+                v[t] = ~0ull;
+            }
+        }
+        __syncwarp();
+        bitonic_sort_u64<kSortWarpMax>(v, np, lane, 32, true);
+        for (int t = lane; t < n; t += 32) {
+            unsigned long long x = v[t];
+            uint32_t src = (uint32_t)x;
+            out_idx[b0 + t] = idx[b0 + src];
+            out_hash[b0 + t] = (uint32_t)(x >> 32);
+            if (val) out_val[b0 + t] = val[b0 + src];
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+k_sort_by_hash_block(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                     const float *__restrict__ val, SideHash h, int32_t *__restrict__ out_idx,
+                     float *__restrict__ out_val, uint32_t *__restrict__ out_hash,
+                     DevCounters *dc, const unsigned int *long_list) {
+    extern __shared__ unsigned long long lv[];
+    const unsigned int nlong = dc->long_n;
+    for (unsigned int q = blockIdx.x; q < nlong; q += gridDim.x) {
+        const int64_t k = long_list[q];
+        const int64_t b0 = ptr[k];
+        const int n = (int)(ptr[k + 1] - b0);
+        if (n > kSortBlockMax) {
+            if (threadIdx.x == 0) atomicOr(&dc->status, kStatusBadIndex);
+            continue;
+        }
+        int np = 1;
+        while (np < n) np <<= 1;
+        for (int t = threadIdx.x; t < np; t += blockDim.x) {
+            if (t < n) {
+                uint32_t j = (uint32_t)idx[b0 + t];
+                lv[t] = ((unsigned long long)side_hash(h, j) << 32) | (uint32_t)t;
+            } else {
+                lv[t] = ~0ull;
+            }
+        }
+        __syncthreads();
+        bitonic_sort_u64<kSortBlockMax>(lv, np, threadIdx.x, blockDim.x, false);
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
+            unsigned long long x = lv[t];
+            uint32_t src = (uint32_t)x;
+            out_idx[b0 + t] = idx[b0 + src];
+            out_hash[b0 + t] = (uint32_t)(x >> 32);
+            if (val) out_val[b0 + t] = val[b0 + src];
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_sort_by_hash(const int64_t *ptr, const int32_t *idx, const float *val,
+                                     int64_t K, SideHash h, int32_t *out_idx, float *out_val,
+                                     uint32_t *out_hash, DevCounters *dc, unsigned int *long_list,
+                                     int sm_count, cudaStream_t s) {
+    if (K == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(&dc->long_n, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (K + (kSortThreads / 32) - 1) / (kSortThreads / 32);
+    int grid = (int)(blocks < (int64_t)sm_count * 8 ? blocks : (int64_t)sm_count * 8);
+    k_sort_by_hash_warp<<<grid, kSortThreads, 0, s>>>(ptr, idx, val, K, h, out_idx, out_val,
+                                                       out_hash, dc, long_list);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    size_t smem = (size_t)kSortBlockMax * sizeof(unsigned long long);
+    e = cudaFuncSetAttribute(k_sort_by_hash_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    k_sort_by_hash_block<<<sm_count, 1024, smem, s>>>(ptr, idx, val, h, out_idx, out_val, out_hash,
+                                                      dc, long_list);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+
+__global__ void k_count_terms(const int64_t *a_ptr, const int64_t *b_ptr, int64_t K,
+                              unsigned long long *out) {
+    unsigned long long acc = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x)
+        acc += (unsigned long long)(a_ptr[k + 1] - a_ptr[k]) * (unsigned long long)(b_ptr[k + 1] - b_ptr[k]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(kFull, acc, d);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
+cudaError_t launch_count_terms(const int64_t *a_ptr, const int64_t *b_ptr, int64_t K,
+                               unsigned long long *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || K == 0) return e;
+    int grid = (int)((K + 255) / 256 < 4096 ? (K + 255) / 256 : 4096);
+    k_count_terms<<<grid, 256, 0, s>>>(a_ptr, b_ptr, K, out);
+    return cudaGetLastError();
+}
+
+__global__ void k_fill_empty(Slot *slots, uint64_t n) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        slots[x].key = kEmptyKey;
+        slots[x].val = 0ull;
+    }
+}
+
+cudaError_t launch_fill_empty(Slot *slots, uint64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    int grid = (int)(blocks < 65536 ? blocks : 65536);
+    k_fill_empty<<<grid, 256, 0, s>>>(slots, n);
+    return cudaGetLastError();
+}
+
+// Per-partition sums (int mode: sum of counts = terms of the partition) and
+// live-entry counts.
+__global__ void k_partition_sums(const Slot *slots, const unsigned long long *part_off,
+                                 const unsigned long long *part_mask, uint32_t P, int value_type,
+                                 unsigned long long *terms_out, unsigned long long *live_out) {
+    for (uint32_t p = blockIdx.x; p < P; p += gridDim.x) {
+        const unsigned long long off = part_off[p], cap = part_mask[p] + 1ull;
+        unsigned long long t = 0, live = 0;
+        for (unsigned long long x = threadIdx.x; x < cap; x += blockDim.x) {
+            Slot s = slots[off + x];
+            if (s.key != kEmptyKey) {
+                ++live;
+                if (value_type == CRP_I32) t += (unsigned int)s.val;
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            t += __shfl_down_sync(kFull, t, d);
+            live += __shfl_down_sync(kFull, live, d);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&terms_out[p], t);
+            atomicAdd(&live_out[p], live);
+        }
+    }
+}
+
+cudaError_t launch_partition_sums(const Slot *slots, const unsigned long long *part_off,
+                                  const unsigned long long *part_mask, uint32_t P, int value_type,
+                                  unsigned long long *terms_out, unsigned long long *live_out,
+                                  cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(terms_out, 0, sizeof(unsigned long long) * P, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(live_out, 0, sizeof(unsigned long long) * P, s);
+    if (e != cudaSuccess) return e;
+    int grid = (int)(P < 8192 ? P : 8192);
+    k_partition_sums<<<grid, 256, 0, s>>>(slots, part_off, part_mask, P, value_type, terms_out,
+                                          live_out);
+    return cudaGetLastError();
+}
+
+// Re-insert spilled updates (after the full partitions were grown).
+__global__ void k_spill_reinsert(const SpillRec *spill, uint64_t n, HashPair hp, TableView tv) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        SpillRec r = spill[x];
+        uint32_t i = (uint32_t)(r.key >> 32), j = (uint32_t)r.key;
+        table_update(tv, partition_hash(hp, i, j), r.key, r.val);
+    }
+}
+
+cudaError_t launch_spill_reinsert(const SpillRec *spill, uint64_t n, HashPair hp, TableView tv,
+                                  cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    int grid = (int)(blocks < 16384 ? blocks : 16384);
+    k_spill_reinsert<<<grid, 256, 0, s>>>(spill, n, hp, tv);
+    return cudaGetLastError();
+}
+
+// Move the entries of one partition's old table into its new (larger) one.
+__global__ void k_rehash(const Slot *old_slots, uint64_t old_off, uint64_t old_cap, TableView tv,
+                         uint64_t new_off, uint64_t new_mask) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < old_cap;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        Slot s = old_slots[old_off + x];
+        if (s.key == kEmptyKey) continue;
+        unsigned long long h = slot_mix(s.key) & new_mask;
+        for (unsigned long long probe = 0; probe <= new_mask; ++probe) {
+            Slot *d = tv.slots + new_off + h;
+            unsigned long long prev = atomicCAS(&d->key, kEmptyKey, s.key);
+            if (prev == kEmptyKey) {
+                d->val = s.val;
+                break;
+            }
+            h = (h + 1) & new_mask;
+        }
+    }
+}
+
+cudaError_t launch_rehash_partition(const Slot *old_slots, uint64_t old_off, uint64_t old_cap,
+                                    TableView tv, uint64_t new_off, uint64_t new_mask,
+                                    cudaStream_t s) {
+    uint64_t blocks = (old_cap + 255) / 256;
+    int grid = (int)(blocks < 16384 ? blocks : 16384);
+    k_rehash<<<grid, 256, 0, s>>>(old_slots, old_off, old_cap, tv, new_off, new_mask);
+    return cudaGetLastError();
+}
+
+// Debug validation of a compressed input: ptr[0] == 0, ptr non-decreasing,
+// ptr[K] == nnz, every index in [0, n_minor).  Sets *bad on any violation.
+__global__ void k_validate_ptr(const int64_t *ptr, int64_t K, int64_t nnz, unsigned int *bad) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        if (ptr[k + 1] < ptr[k]) atomicOr(bad, 1u);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (ptr[0] != 0 || ptr[K] != nnz)) atomicOr(bad, 1u);
+}
+
+__global__ void k_validate_idx(const int32_t *idx, int64_t nnz, int32_t n_minor, unsigned int *bad) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nnz;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v = idx[x];
+        if (v < 0 || v >= n_minor) atomicOr(bad, 2u);
+    }
+}
+
+cudaError_t launch_validate_sparse(const int64_t *ptr, const int32_t *idx, int64_t K, int64_t nnz,
+                                   int32_t n_minor, unsigned int *bad, cudaStream_t s) {
+    int64_t b1 = (K + 255) / 256;
+    k_validate_ptr<<<(int)(b1 < 4096 ? (b1 > 0 ? b1 : 1) : 4096), 256, 0, s>>>(ptr, K, nnz, bad);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || nnz == 0) return e;
+    int64_t b2 = (nnz + 255) / 256;
+    k_validate_idx<<<(int)(b2 < 4096 ? b2 : 4096), 256, 0, s>>>(idx, nnz, n_minor, bad);
+    return cudaGetLastError();
+}
+
+}  // namespace crp

@@ -1,0 +1,779 @@
+// Host side of the C ABI declared in include/crp.h: plan creation and
+// validation, table sizing, launch configuration, status, top-k driver,
+// export and statistics.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "crp_internal.cuh"
+
+using namespace crp;
+
+namespace crp {
+cudaError_t launch_export_range(const Slot *slots, const unsigned long long *part_off,
+                                const unsigned long long *part_mask, uint32_t p0, uint32_t p1,
+                                const unsigned long long *base, int value_type, int32_t *i_out,
+                                int32_t *j_out, double *w_out, double *wl_out, cudaStream_t s);
+}
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+
+static thread_local std::string g_last_error;
+
+static crp_status fail(crp_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+#define CRP_CUDA(call)                                                                         \
+    do {                                                                                       \
+        cudaError_t _e = (call);                                                               \
+        if (_e != cudaSuccess)                                                                 \
+            return fail(_e == cudaErrorMemoryAllocation ? CRP_ENOMEM : CRP_ECUDA,              \
+                        std::string(#call) + ": " + cudaGetErrorString(_e));                   \
+    } while (0)
+
+extern "C" const char *crp_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char *crp_version(void) { return "crp 0.1.0 (sm_103a)"; }
+
+// ---------------------------------------------------------------------------
+// Hash parameters: SplitMix64 (Steele, Lea, Flood 2014) from each seed
+// ---------------------------------------------------------------------------
+
+static uint64_t splitmix64_next(uint64_t &state) {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static SideHash make_side_hash(uint64_t seed, uint32_t logP) {
+    SideHash h;
+    uint64_t st = seed;
+    h.a = splitmix64_next(st);
+    h.b = splitmix64_next(st);
+    h.shift = 64u - (logP > 0 ? logP : 1u);
+    h.mask = (1u << logP) - 1u;
+    return h;
+}
+
+// ---------------------------------------------------------------------------
+// Plan
+// ---------------------------------------------------------------------------
+
+struct crp_plan {
+    crp_plan_desc d;
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    HashPair hp;
+    uint32_t logP = 0;
+    // exact tables
+    Slot *slots = nullptr;
+    uint64_t n_slots = 0;
+    std::vector<unsigned long long> h_off, h_mask;
+    unsigned long long *d_off = nullptr, *d_mask = nullptr;
+    unsigned int *d_full = nullptr;
+    SpillRec *spill = nullptr;
+    uint64_t spill_cap = 0;
+    DevCounters *dc = nullptr;
+    unsigned long long *d_scratch64 = nullptr;  // 2*P + 8 u64 of small scratch
+    unsigned int *d_topk_hist = nullptr;
+    // sorted-b scratch (G > 1)
+    int32_t *s_idx = nullptr;
+    float *s_val = nullptr;
+    uint32_t *s_hash = nullptr;
+    unsigned int *s_long = nullptr;
+    uint64_t s_nnz_cap = 0, s_k_cap = 0;
+    // launch configuration
+    uint32_t G = 1, tile = 64, S = 8192;
+    int grid = 0;
+    bool tables_ready = false;
+    // timing of the enumeration kernel and a count of our launches
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool timed = false;
+    uint64_t launches = 0;
+};
+
+static bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
+static uint64_t next_pow2(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+static crp_status alloc_tables(crp_plan *pl, uint64_t cap_per_partition) {
+    const uint32_t P = pl->d.P;
+    cap_per_partition = next_pow2(std::max<uint64_t>(cap_per_partition, 64));
+    pl->h_off.resize(P);
+    pl->h_mask.resize(P);
+    for (uint32_t p = 0; p < P; ++p) {
+        pl->h_off[p] = (unsigned long long)p * cap_per_partition;
+        pl->h_mask[p] = cap_per_partition - 1;
+    }
+    uint64_t total = (uint64_t)P * cap_per_partition;
+    if (pl->slots) cudaFree(pl->slots);
+    pl->slots = nullptr;
+    CRP_CUDA(cudaMalloc(&pl->slots, total * sizeof(Slot)));
+    pl->n_slots = total;
+    CRP_CUDA(cudaMemcpyAsync(pl->d_off, pl->h_off.data(), P * sizeof(unsigned long long),
+                             cudaMemcpyHostToDevice, pl->stream));
+    CRP_CUDA(cudaMemcpyAsync(pl->d_mask, pl->h_mask.data(), P * sizeof(unsigned long long),
+                             cudaMemcpyHostToDevice, pl->stream));
+    CRP_CUDA(cudaMemsetAsync(pl->d_full, 0, P * sizeof(unsigned int), pl->stream));
+    CRP_CUDA(launch_fill_empty(pl->slots, total, pl->stream));
+    pl->launches += 1;
+    if (!pl->spill) {
+        pl->spill_cap = std::max<uint64_t>(1u << 16, std::min<uint64_t>(total / 8, 1ull << 24));
+        CRP_CUDA(cudaMalloc(&pl->spill, pl->spill_cap * sizeof(SpillRec)));
+    }
+    pl->tables_ready = true;
+    return CRP_OK;
+}
+
+extern "C" crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc, void *stream) {
+    if (!out || !desc) return fail(CRP_EINVAL, "crp_plan_create: null argument");
+    *out = nullptr;
+    const crp_plan_desc &d = *desc;
+    if (d.n_rows <= 0 || d.n_cols <= 0) return fail(CRP_EINVAL, "n_rows and n_cols must be > 0");
+    if (!is_pow2(d.P) || d.P > (1u << 24))
+        return fail(CRP_EINVAL, "P must be a power of two in [1, 2^24]");
+    if (d.value_type != CRP_I32 && d.value_type != CRP_F32_COMP)
+        return fail(CRP_EINVAL, "unknown value_type");
+    if (d.mode != CRP_FULL && d.mode != CRP_UPPER) return fail(CRP_EINVAL, "unknown mode");
+    if (d.smem_slots && (!is_pow2(d.smem_slots) || d.smem_slots < 4096 || d.smem_slots > 16384))
+        return fail(CRP_EINVAL, "smem_slots must be a power of two in [4096, 16384]");
+    if (d.groups && (!is_pow2(d.groups) || d.groups > d.P))
+        return fail(CRP_EINVAL, "groups must be a power of two <= P");
+    if (d.summary_counters)
+        return fail(CRP_EUNSUPPORTED, "summary mode is created with crp_summary_plan_create");
+    crp_plan *pl = new crp_plan();
+    pl->d = d;
+    pl->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&pl->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, pl->device);
+    if (e != cudaSuccess) {
+        delete pl;
+        return fail(CRP_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
+    pl->logP = 0;
+    while ((1u << pl->logP) < d.P) ++pl->logP;
+    pl->hp.ha = make_side_hash(d.seed_a, pl->logP);
+    pl->hp.hb = make_side_hash(d.seed_b, pl->logP);
+    pl->G = d.groups ? d.groups : 1u;
+    pl->tile = d.tile_vectors ? d.tile_vectors : 64u;
+    pl->S = d.smem_slots ? d.smem_slots : 8192u;
+    crp_status st = CRP_OK;
+#define ALLOC(ptr, bytes)                                                                      \
+    if (st == CRP_OK && cudaMalloc(&(ptr), (bytes)) != cudaSuccess)                            \
+        st = fail(CRP_ENOMEM, "device allocation failed");
+    ALLOC(pl->d_off, d.P * sizeof(unsigned long long));
+    ALLOC(pl->d_mask, d.P * sizeof(unsigned long long));
+    ALLOC(pl->d_full, d.P * sizeof(unsigned int));
+    ALLOC(pl->dc, sizeof(DevCounters));
+    ALLOC(pl->d_scratch64, (2ull * d.P + 16) * sizeof(unsigned long long));
+    ALLOC(pl->d_topk_hist, (kTopkBuckets + 512) * sizeof(unsigned int));
+#undef ALLOC
+    if (st == CRP_OK && cudaMemsetAsync(pl->dc, 0, sizeof(DevCounters), pl->stream) != cudaSuccess)
+        st = fail(CRP_ECUDA, "memset failed");
+    if (st == CRP_OK) {
+        int per_sm = accumulate_max_blocks_per_sm(d.value_type, pl->S);
+        if (per_sm <= 0) st = fail(CRP_ECUDA, "accumulate kernel cannot be resident");
+        pl->grid = per_sm * pl->sm_count;
+    }
+    if (st == CRP_OK && (cudaEventCreate(&pl->ev0) != cudaSuccess ||
+                         cudaEventCreate(&pl->ev1) != cudaSuccess))
+        st = fail(CRP_ECUDA, "cudaEventCreate failed");
+    if (st == CRP_OK && d.table_capacity_hint) {
+        uint64_t per = (d.table_capacity_hint + d.P - 1) / d.P;
+        st = alloc_tables(pl, per);
+    }
+    if (st != CRP_OK) {
+        crp_plan_destroy(pl);
+        return st;
+    }
+    *out = pl;
+    return CRP_OK;
+}
+
+extern "C" void crp_plan_destroy(crp_plan *pl) {
+    if (!pl) return;
+    cudaStreamSynchronize(pl->stream);
+    cudaFree(pl->slots);
+    cudaFree(pl->d_off);
+    cudaFree(pl->d_mask);
+    cudaFree(pl->d_full);
+    cudaFree(pl->spill);
+    cudaFree(pl->dc);
+    cudaFree(pl->d_scratch64);
+    cudaFree(pl->d_topk_hist);
+    cudaFree(pl->s_idx);
+    cudaFree(pl->s_val);
+    cudaFree(pl->s_hash);
+    cudaFree(pl->s_long);
+    if (pl->ev0) cudaEventDestroy(pl->ev0);
+    if (pl->ev1) cudaEventDestroy(pl->ev1);
+    delete pl;
+}
+
+extern "C" crp_status crp_reset(crp_plan *pl) {
+    if (!pl) return fail(CRP_EINVAL, "null plan");
+    CRP_CUDA(cudaMemsetAsync(pl->dc, 0, sizeof(DevCounters), pl->stream));
+    if (pl->tables_ready) {
+        CRP_CUDA(launch_fill_empty(pl->slots, pl->n_slots, pl->stream));
+        pl->launches += 1;
+        CRP_CUDA(cudaMemsetAsync(pl->d_full, 0, pl->d.P * sizeof(unsigned int), pl->stream));
+    }
+    return CRP_OK;
+}
+
+extern "C" uint32_t crp_partition_of(const crp_plan *pl, int32_t i, int32_t j) {
+    if (!pl) return 0;
+    return partition_hash(pl->hp, (uint32_t)i, (uint32_t)j);
+}
+
+// ---------------------------------------------------------------------------
+// Accumulate
+// ---------------------------------------------------------------------------
+
+static crp_status check_sparse(const crp_sparse *s, const char *name) {
+    if (!s) return fail(CRP_EINVAL, std::string(name) + " is null");
+    if (s->n_major < 0 || s->nnz < 0 || s->n_minor <= 0)
+        return fail(CRP_EINVAL, std::string(name) + ": negative size");
+    if (s->n_major > 0 && !s->ptr) return fail(CRP_EINVAL, std::string(name) + ": null ptr");
+    if (s->nnz > 0 && !s->idx) return fail(CRP_EINVAL, std::string(name) + ": null idx");
+    return CRP_OK;
+}
+
+static crp_status ensure_sort_scratch(crp_plan *pl, uint64_t nnz, uint64_t K, bool values) {
+    if (nnz > pl->s_nnz_cap || (values && !pl->s_val && nnz)) {
+        cudaFree(pl->s_idx);
+        cudaFree(pl->s_val);
+        cudaFree(pl->s_hash);
+        pl->s_idx = nullptr;
+        pl->s_val = nullptr;
+        pl->s_hash = nullptr;
+        uint64_t cap = std::max<uint64_t>(nnz, 1);
+        CRP_CUDA(cudaMalloc(&pl->s_idx, cap * sizeof(int32_t)));
+        CRP_CUDA(cudaMalloc(&pl->s_hash, cap * sizeof(uint32_t)));
+        if (values) CRP_CUDA(cudaMalloc(&pl->s_val, cap * sizeof(float)));
+        pl->s_nnz_cap = cap;
+    }
+    if (K > pl->s_k_cap) {
+        cudaFree(pl->s_long);
+        pl->s_long = nullptr;
+        uint64_t cap = std::max<uint64_t>(K, 1);
+        CRP_CUDA(cudaMalloc(&pl->s_long, cap * sizeof(unsigned int)));
+        pl->s_k_cap = cap;
+    }
+    return CRP_OK;
+}
+
+static TableView table_view(crp_plan *pl, Slot *slots, const unsigned long long *off,
+                            const unsigned long long *mask) {
+    TableView tv;
+    tv.slots = slots;
+    tv.part_off = off;
+    tv.part_mask = mask;
+    tv.part_full = pl->d_full;
+    tv.spill = pl->spill;
+    tv.spill_cap = pl->spill_cap;
+    tv.dc = pl->dc;
+    tv.value_type = pl->d.value_type;
+    return tv;
+}
+
+static AccumulateArgs make_args(crp_plan *pl, const crp_sparse *A, const crp_sparse *B,
+                                const int32_t *b_idx, const float *b_val, uint32_t G) {
+    AccumulateArgs a;
+    a.a_ptr = A->ptr;
+    a.a_idx = A->idx;
+    a.a_val = A->val;
+    a.b_ptr = B->ptr;
+    a.b_idx = b_idx;
+    a.b_val = b_val;
+    a.K = A->n_major;
+    a.n_rows = pl->d.n_rows;
+    a.n_cols = pl->d.n_cols;
+    a.groups = G;
+    a.group_begin = 0;
+    a.group_end = G;
+    a.tile = pl->tile;
+    a.n_tiles = (uint32_t)((A->n_major + pl->tile - 1) / pl->tile);
+    a.mode = pl->d.mode;
+    a.use_match = (pl->d.flags & CRP_PLAN_NO_WARP_MATCH) ? 0 : 1;
+    a.debug_checks = (pl->d.flags & CRP_PLAN_DEBUG_CHECKS) ? 1 : 0;
+    a.smem_slots = pl->S;
+    a.hp = pl->hp;
+    return a;
+}
+
+// Estimate the number of distinct entries (nonzeros of A B) from one group of
+// partitions: the terms hashing into partitions [0, P/Gs) are accumulated
+// exactly into a scratch table (Lemma 1 keeps that pass linear in the input
+// plus those terms), and their distinct count is scaled by Gs.  h is pairwise
+// independent, so each group holds ~1/Gs of the entries.  This is how the
+// paper's remark on estimating nnz(AB) from a sample of the output (Section 4,
+// "Parameters") is realised with the partition structure itself.
+static crp_status estimate_and_allocate(crp_plan *pl, const crp_sparse *A, const crp_sparse *B,
+                                        const int32_t *b_idx, const float *b_val) {
+    const uint32_t P = pl->d.P;
+    CRP_CUDA(launch_count_terms(A->ptr, B->ptr, A->n_major, pl->d_scratch64, pl->stream));
+    unsigned long long terms = 0;
+    CRP_CUDA(cudaMemcpyAsync(&terms, pl->d_scratch64, 8, cudaMemcpyDeviceToHost, pl->stream));
+    CRP_CUDA(cudaStreamSynchronize(pl->stream));
+    const uint64_t bound = std::min<uint64_t>(terms, (uint64_t)pl->d.n_rows * pl->d.n_cols);
+    uint64_t distinct;
+    const uint32_t Gs = std::min<uint32_t>(P, 64u);
+    if (Gs <= 1 || bound < (1ull << 22)) {
+        distinct = bound;
+    } else {
+        // scratch table for partitions [0, P/Gs) (others unused)
+        const uint32_t np = P / Gs;
+        const uint64_t cap = next_pow2(std::max<uint64_t>(2 * (bound / P + 1), 1024));
+        Slot *tmp = nullptr;
+        CRP_CUDA(cudaMalloc(&tmp, (uint64_t)np * cap * sizeof(Slot)));
+        std::vector<unsigned long long> off(P, 0), mask(P, cap - 1);
+        for (uint32_t p = 0; p < np; ++p) off[p] = (unsigned long long)p * cap;
+        unsigned long long *d_off = pl->d_scratch64, *d_mask = pl->d_scratch64 + P;
+        CRP_CUDA(cudaMemcpyAsync(d_off, off.data(), P * 8, cudaMemcpyHostToDevice, pl->stream));
+        CRP_CUDA(cudaMemcpyAsync(d_mask, mask.data(), P * 8, cudaMemcpyHostToDevice, pl->stream));
+        CRP_CUDA(launch_fill_empty(tmp, (uint64_t)np * cap, pl->stream));
+        CRP_CUDA(cudaMemsetAsync(pl->d_full, 0, P * sizeof(unsigned int), pl->stream));
+        CRP_CUDA(cudaMemsetAsync(pl->dc, 0, sizeof(DevCounters), pl->stream));
+        // sorted b is needed for a group run
+        const int32_t *sb_idx = b_idx;
+        const float *sb_val = b_val;
+        if (b_idx == B->idx) {
+            crp_status st = ensure_sort_scratch(pl, B->nnz, B->n_major, B->val != nullptr);
+            if (st != CRP_OK) { cudaFree(tmp); return st; }
+            CRP_CUDA(launch_sort_by_hash(B->ptr, B->idx, B->val, B->n_major, pl->hp.hb, pl->s_idx,
+                                         pl->s_val, pl->s_hash, pl->dc, pl->s_long, pl->sm_count,
+                                         pl->stream));
+            sb_idx = pl->s_idx;
+            sb_val = B->val ? pl->s_val : nullptr;
+        }
+        AccumulateArgs a = make_args(pl, A, B, sb_idx, sb_val, Gs);
+        a.group_begin = 0;
+        a.group_end = 1;
+        a.tv = table_view(pl, tmp, d_off, d_mask);
+        CRP_CUDA(launch_accumulate(a, pl->s_hash, pl->grid, pl->stream));
+        // live entries per sampled partition
+        std::vector<unsigned long long> live(np, 0);
+        unsigned long long *d_live = nullptr, *d_terms = nullptr;
+        CRP_CUDA(cudaMalloc(&d_live, np * 8));
+        CRP_CUDA(cudaMalloc(&d_terms, np * 8));
+        CRP_CUDA(launch_partition_sums(tmp, d_off, d_mask, np, pl->d.value_type, d_terms, d_live,
+                                       pl->stream));
+        CRP_CUDA(cudaMemcpyAsync(live.data(), d_live, np * 8, cudaMemcpyDeviceToHost, pl->stream));
+        unsigned int status = 0;
+        CRP_CUDA(cudaMemcpyAsync(&status, &pl->dc->status, 4, cudaMemcpyDeviceToHost, pl->stream));
+        CRP_CUDA(cudaStreamSynchronize(pl->stream));
+        cudaFree(d_live);
+        cudaFree(d_terms);
+        cudaFree(tmp);
+        CRP_CUDA(cudaMemsetAsync(pl->dc, 0, sizeof(DevCounters), pl->stream));
+        CRP_CUDA(cudaMemsetAsync(pl->d_full, 0, P * sizeof(unsigned int), pl->stream));
+        if (status & (kStatusTableFull | kStatusSpillFull)) {
+            distinct = bound;  // sample overflowed its bound: fall back
+        } else {
+            unsigned long long mx = 0, sum = 0;
+            for (auto v : live) { mx = std::max(mx, v); sum += v; }
+            distinct = std::max<uint64_t>((uint64_t)mx * P, (uint64_t)sum * Gs);
+        }
+    }
+    // target at most ~60% load per partition
+    uint64_t per = (uint64_t)((double)distinct / P / 0.6) + 64;
+    return alloc_tables(pl, per);
+}
+
+extern "C" crp_status crp_outer_accumulate(crp_plan *pl, const crp_sparse *A, const crp_sparse *B) {
+    if (!pl) return fail(CRP_EINVAL, "null plan");
+    crp_status st = check_sparse(A, "A");
+    if (st != CRP_OK) return st;
+    st = check_sparse(B, "B");
+    if (st != CRP_OK) return st;
+    if (A->n_major != B->n_major)
+        return fail(CRP_EINVAL, "A and B must hold the same number of outer products");
+    if (A->n_minor != pl->d.n_rows || B->n_minor != pl->d.n_cols)
+        return fail(CRP_EINVAL, "A->n_minor must equal n_rows and B->n_minor n_cols");
+    if (pl->d.value_type == CRP_I32 && (A->val || B->val))
+        return fail(CRP_EINVAL, "CRP_I32 counts {0,1} inputs: val must be NULL");
+    if (A->n_major == 0) return CRP_OK;
+    CRP_CUDA(cudaSetDevice(pl->device));
+    if (pl->d.flags & CRP_PLAN_DEBUG_CHECKS) {
+        unsigned int *bad = (unsigned int *)(pl->d_scratch64 + 2 * pl->d.P + 8);
+        CRP_CUDA(cudaMemsetAsync(bad, 0, 4, pl->stream));
+        CRP_CUDA(launch_validate_sparse(A->ptr, A->idx, A->n_major, A->nnz, A->n_minor, bad,
+                                        pl->stream));
+        CRP_CUDA(launch_validate_sparse(B->ptr, B->idx, B->n_major, B->nnz, B->n_minor, bad,
+                                        pl->stream));
+        unsigned int h_bad = 0;
+        CRP_CUDA(cudaMemcpyAsync(&h_bad, bad, 4, cudaMemcpyDeviceToHost, pl->stream));
+        CRP_CUDA(cudaStreamSynchronize(pl->stream));
+        if (h_bad) return fail(CRP_EINVAL, "input failed validation (ptr not monotone, "
+                                           "ptr[K] != nnz, or an index out of range)");
+    }
+    const int32_t *b_idx = B->idx;
+    const float *b_val = B->val;
+    const uint32_t *b_hash = nullptr;
+    if (pl->G > 1) {
+        st = ensure_sort_scratch(pl, B->nnz, B->n_major, B->val != nullptr);
+        if (st != CRP_OK) return st;
+        CRP_CUDA(launch_sort_by_hash(B->ptr, B->idx, B->val, B->n_major, pl->hp.hb, pl->s_idx,
+                                     pl->s_val, pl->s_hash, pl->dc, pl->s_long, pl->sm_count,
+                                     pl->stream));
+        b_idx = pl->s_idx;
+        b_val = B->val ? pl->s_val : nullptr;
+        b_hash = pl->s_hash;
+        pl->launches += 2;
+    }
+    if (!pl->tables_ready) {
+        st = estimate_and_allocate(pl, A, B, b_idx, b_val);
+        if (st != CRP_OK) return st;
+    }
+    AccumulateArgs a = make_args(pl, A, B, b_idx, b_val, pl->G);
+    a.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
+    CRP_CUDA(cudaMemsetAsync(&pl->dc->work_next, 0, sizeof(unsigned int), pl->stream));
+    CRP_CUDA(cudaEventRecord(pl->ev0, pl->stream));
+    CRP_CUDA(launch_accumulate(a, b_hash, pl->grid, pl->stream));
+    CRP_CUDA(cudaEventRecord(pl->ev1, pl->stream));
+    pl->timed = true;
+    pl->launches += 1;
+    return CRP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sync, growth of full partitions
+// ---------------------------------------------------------------------------
+
+static crp_status grow_full_partitions(crp_plan *pl) {
+    const uint32_t P = pl->d.P;
+    for (int round = 0; round < 8; ++round) {
+        std::vector<unsigned int> full(P);
+        CRP_CUDA(cudaMemcpyAsync(full.data(), pl->d_full, P * 4, cudaMemcpyDeviceToHost,
+                                 pl->stream));
+        unsigned long long n_spill = 0;
+        CRP_CUDA(cudaMemcpyAsync(&n_spill, &pl->dc->spill_n, 8, cudaMemcpyDeviceToHost,
+                                 pl->stream));
+        CRP_CUDA(cudaStreamSynchronize(pl->stream));
+        if (n_spill > pl->spill_cap)
+            return fail(CRP_ETABLE_FULL, "spill list overflowed; counts were lost (reset and "
+                                         "create the plan with a larger table_capacity_hint)");
+        bool any = false;
+        for (auto f : full) any |= f != 0;
+        if (!any && n_spill == 0) return CRP_OK;
+        // new layout: full partitions x4
+        std::vector<unsigned long long> noff(P), nmask(P);
+        uint64_t total = 0;
+        for (uint32_t p = 0; p < P; ++p) {
+            uint64_t cap = pl->h_mask[p] + 1;
+            if (full[p]) cap *= 4;
+            noff[p] = total;
+            nmask[p] = cap - 1;
+            total += cap;
+        }
+        Slot *ns = nullptr;
+        CRP_CUDA(cudaMalloc(&ns, total * sizeof(Slot)));
+        CRP_CUDA(launch_fill_empty(ns, total, pl->stream));
+        unsigned long long *d_noff = nullptr, *d_nmask = nullptr;
+        CRP_CUDA(cudaMalloc(&d_noff, P * 8));
+        CRP_CUDA(cudaMalloc(&d_nmask, P * 8));
+        CRP_CUDA(cudaMemcpyAsync(d_noff, noff.data(), P * 8, cudaMemcpyHostToDevice, pl->stream));
+        CRP_CUDA(cudaMemcpyAsync(d_nmask, nmask.data(), P * 8, cudaMemcpyHostToDevice, pl->stream));
+        TableView tv = table_view(pl, ns, d_noff, d_nmask);
+        for (uint32_t p = 0; p < P; ++p) {
+            uint64_t cap = pl->h_mask[p] + 1;
+            if (full[p])
+                CRP_CUDA(launch_rehash_partition(pl->slots, pl->h_off[p], cap, tv, noff[p],
+                                                 nmask[p], pl->stream));
+            else
+                CRP_CUDA(cudaMemcpyAsync(ns + noff[p], pl->slots + pl->h_off[p], cap * sizeof(Slot),
+                                         cudaMemcpyDeviceToDevice, pl->stream));
+        }
+        // move the spill list aside and re-insert it into the grown tables
+        SpillRec *old_spill = nullptr;
+        if (n_spill) {
+            CRP_CUDA(cudaMalloc(&old_spill, n_spill * sizeof(SpillRec)));
+            CRP_CUDA(cudaMemcpyAsync(old_spill, pl->spill, n_spill * sizeof(SpillRec),
+                                     cudaMemcpyDeviceToDevice, pl->stream));
+        }
+        CRP_CUDA(cudaMemsetAsync(&pl->dc->spill_n, 0, 8, pl->stream));
+        CRP_CUDA(cudaMemsetAsync(pl->d_full, 0, P * 4, pl->stream));
+        CRP_CUDA(cudaMemcpyAsync(pl->d_off, noff.data(), P * 8, cudaMemcpyHostToDevice, pl->stream));
+        CRP_CUDA(cudaMemcpyAsync(pl->d_mask, nmask.data(), P * 8, cudaMemcpyHostToDevice,
+                                 pl->stream));
+        TableView tv2 = table_view(pl, ns, pl->d_off, pl->d_mask);
+        if (n_spill) CRP_CUDA(launch_spill_reinsert(old_spill, n_spill, pl->hp, tv2, pl->stream));
+        CRP_CUDA(cudaStreamSynchronize(pl->stream));
+        cudaFree(old_spill);
+        cudaFree(d_noff);
+        cudaFree(d_nmask);
+        cudaFree(pl->slots);
+        pl->slots = ns;
+        pl->n_slots = total;
+        pl->h_off = noff;
+        pl->h_mask = nmask;
+    }
+    return fail(CRP_ETABLE_FULL, "partitions still full after repeated growth");
+}
+
+extern "C" crp_status crp_sync(crp_plan *pl) {
+    if (!pl) return fail(CRP_EINVAL, "null plan");
+    CRP_CUDA(cudaStreamSynchronize(pl->stream));
+    unsigned int status = 0;
+    CRP_CUDA(cudaMemcpy(&status, &pl->dc->status, 4, cudaMemcpyDeviceToHost));
+    if (status & kStatusBadIndex)
+        return fail(CRP_EINVAL, "an input index was out of range (or a vector too long to sort)");
+    if (status & kStatusSmemProbe) return fail(CRP_ECUDA, "on-chip table probe bound exceeded");
+    if (status & kStatusTimeout) return fail(CRP_ETIMEOUT, "a bounded device wait gave up");
+    if (status & (kStatusTableFull | kStatusSpillFull)) {
+        if (!pl->d.auto_grow || (status & kStatusSpillFull))
+            return fail(CRP_ETABLE_FULL, (status & kStatusSpillFull)
+                                             ? "spill list overflowed; counts were lost"
+                                             : "a partition table is full (auto_grow is off)");
+        crp_status st = grow_full_partitions(pl);
+        if (st != CRP_OK) return st;
+        unsigned int zero = 0;
+        CRP_CUDA(cudaMemcpy(&pl->dc->status, &zero, 4, cudaMemcpyHostToDevice));
+    }
+    return CRP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Top-k, export, stats
+// ---------------------------------------------------------------------------
+
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+extern "C" crp_status crp_topk(crp_plan *pl, int32_t k, uint32_t flags, int32_t *i_out,
+                               int32_t *j_out, double *w_out, double *w_lower, int32_t *n_out) {
+    if (!pl || !i_out || !j_out || !w_out || !n_out) return fail(CRP_EINVAL, "null argument");
+    if (k < 1 || k > kTopkSortMax) return fail(CRP_EINVAL, "k must be in [1, 8192]");
+    *n_out = 0;
+    if (!pl->tables_ready) return CRP_OK;
+    const int upper = (flags & CRP_TOPK_UPPER) ? 1 : 0;
+    cudaStream_t s = pl->stream;
+    CRP_CUDA(launch_topk_hist(pl->slots, pl->n_slots, pl->d.value_type, upper, pl->d_topk_hist, s));
+    pl->launches += 1;
+    std::vector<unsigned int> hist(kTopkBuckets);
+    CRP_CUDA(cudaMemcpyAsync(hist.data(), pl->d_topk_hist, kTopkBuckets * 4, cudaMemcpyDeviceToHost,
+                             s));
+    CRP_CUDA(cudaStreamSynchronize(s));
+    uint64_t cum = 0;
+    int b = kTopkBuckets - 1;
+    for (; b >= 0; --b) {
+        cum += hist[b];
+        if (cum >= (uint64_t)k) break;
+    }
+    if (b < 0) b = 0;
+    const uint64_t n_c = cum;
+    if (n_c == 0) return CRP_OK;
+    if (n_c > 0xffffffffull) return fail(CRP_EUNSUPPORTED, "too many top-k candidates");
+    TopkCand *cand = nullptr, *sel = nullptr, *keep = nullptr;
+    CRP_CUDA(cudaMalloc(&cand, n_c * sizeof(TopkCand)));
+    unsigned int *cnt = pl->d_topk_hist + kTopkBuckets;  // 3 counters + 256-bin hist after
+    unsigned int *dhist = cnt + 4;
+    crp_status st = CRP_OK;
+    auto cuda_ok = [&](cudaError_t e) {
+        if (e != cudaSuccess && st == CRP_OK)
+            st = fail(CRP_ECUDA, std::string("topk: ") + cudaGetErrorString(e));
+        return st == CRP_OK;
+    };
+    cuda_ok(launch_topk_collect(pl->slots, pl->n_slots, pl->d.value_type, upper, (unsigned)b, cand,
+                                cnt, (unsigned)n_c, s));
+    pl->launches += 1;
+    const TopkCand *final_c = cand;
+    unsigned int final_n = (unsigned int)std::min<uint64_t>(n_c, (uint64_t)k);
+    if (st == CRP_OK && n_c > (uint64_t)kTopkSortMax) {
+        // MSD radix select on the candidates down to exactly k
+        cuda_ok(cudaMalloc(&sel, (size_t)k * sizeof(TopkCand)));
+        cuda_ok(cudaMalloc(&keep, n_c * sizeof(TopkCand)));
+        TopkCand *und = cand, *nxt = keep;
+        unsigned int n_und = (unsigned int)n_c, n_sel = 0, need = (unsigned int)k;
+        cuda_ok(cudaMemsetAsync(cnt + 1, 0, 4, s));  // sel count
+        for (int d = 0; d < 16 && st == CRP_OK && need > 0; ++d) {
+            unsigned int h[256];
+            cuda_ok(launch_topk_digit_hist(und, n_und, d, dhist, s));
+            cuda_ok(cudaMemcpyAsync(h, dhist, sizeof h, cudaMemcpyDeviceToHost, s));
+            cuda_ok(cudaStreamSynchronize(s));
+            if (st != CRP_OK) break;
+            unsigned int above = 0;
+            int pivot = 255;
+            for (; pivot >= 0; --pivot) {
+                if (above + h[pivot] >= need) break;
+                above += h[pivot];
+            }
+            cuda_ok(launch_topk_digit_split(und, n_und, d, (unsigned)pivot, sel, cnt + 1, nxt,
+                                            cnt + 2, s));
+            pl->launches += 2;
+            unsigned int kn = 0;
+            cuda_ok(cudaMemcpyAsync(&kn, cnt + 2, 4, cudaMemcpyDeviceToHost, s));
+            cuda_ok(cudaStreamSynchronize(s));
+            n_sel += above;
+            need -= above;
+            std::swap(und, nxt);
+            n_und = kn;
+            if (n_und == need) {  // everything left at this prefix is in
+                cuda_ok(cudaMemcpyAsync(sel + n_sel, und, (size_t)n_und * sizeof(TopkCand),
+                                        cudaMemcpyDeviceToDevice, s));
+                n_sel += n_und;
+                need = 0;
+            }
+        }
+        final_c = sel;
+        final_n = n_sel;
+    }
+    // write out (through a device staging buffer when the outputs are host memory)
+    const bool dev_out = is_device_ptr(i_out);
+    int32_t *di = i_out, *dj = j_out;
+    double *dw = w_out, *dwl = w_lower;
+    void *stage = nullptr;
+    if (st == CRP_OK && !dev_out) {
+        cuda_ok(cudaMalloc(&stage, (size_t)k * (4 + 4 + 8 + 8)));
+        di = (int32_t *)stage;
+        dj = di + k;
+        dw = (double *)(dj + k);
+        dwl = w_lower ? dw + k : nullptr;
+    }
+    if (st == CRP_OK) cuda_ok(launch_topk_sort_write(final_c, final_n, di, dj, dw, dwl, s));
+    pl->launches += 1;
+    if (st == CRP_OK && !dev_out) {
+        cuda_ok(cudaMemcpyAsync(i_out, di, final_n * 4, cudaMemcpyDeviceToHost, s));
+        cuda_ok(cudaMemcpyAsync(j_out, dj, final_n * 4, cudaMemcpyDeviceToHost, s));
+        cuda_ok(cudaMemcpyAsync(w_out, dw, final_n * 8, cudaMemcpyDeviceToHost, s));
+        if (w_lower) cuda_ok(cudaMemcpyAsync(w_lower, dwl, final_n * 8, cudaMemcpyDeviceToHost, s));
+    }
+    cuda_ok(cudaStreamSynchronize(s));
+    cudaFree(stage);
+    cudaFree(cand);
+    cudaFree(sel);
+    cudaFree(keep);
+    if (st == CRP_OK) *n_out = (int32_t)final_n;
+    return st;
+}
+
+extern "C" crp_status crp_export_partitions(crp_plan *pl, uint32_t p0, uint32_t p1, int32_t *i_out,
+                                            int32_t *j_out, double *w_out, double *w_lower,
+                                            int64_t capacity, int64_t *n_out) {
+    if (!pl || !n_out) return fail(CRP_EINVAL, "null argument");
+    if (p0 > p1 || p1 > pl->d.P) return fail(CRP_EINVAL, "bad partition range");
+    *n_out = 0;
+    if (!pl->tables_ready || p0 == p1) return CRP_OK;
+    const uint32_t P = pl->d.P;
+    cudaStream_t s = pl->stream;
+    unsigned long long *d_terms = pl->d_scratch64, *d_live = pl->d_scratch64 + P;
+    CRP_CUDA(launch_partition_sums(pl->slots, pl->d_off, pl->d_mask, P, pl->d.value_type, d_terms,
+                                   d_live, s));
+    std::vector<unsigned long long> live(P);
+    CRP_CUDA(cudaMemcpyAsync(live.data(), d_live, P * 8, cudaMemcpyDeviceToHost, s));
+    CRP_CUDA(cudaStreamSynchronize(s));
+    std::vector<unsigned long long> base(p1 - p0);
+    unsigned long long tot = 0;
+    for (uint32_t p = p0; p < p1; ++p) {
+        base[p - p0] = tot;
+        tot += live[p];
+    }
+    *n_out = (int64_t)tot;
+    if ((int64_t)tot > capacity) return fail(CRP_EINVAL, "export capacity too small");
+    if (tot == 0) return CRP_OK;
+    if (!i_out || !j_out || !w_out) return fail(CRP_EINVAL, "null output");
+    const bool dev_out = is_device_ptr(i_out);
+    unsigned long long *d_base = nullptr;
+    CRP_CUDA(cudaMalloc(&d_base, base.size() * 8));
+    CRP_CUDA(cudaMemcpyAsync(d_base, base.data(), base.size() * 8, cudaMemcpyHostToDevice, s));
+    int32_t *di = i_out, *dj = j_out;
+    double *dw = w_out, *dwl = w_lower;
+    void *stage = nullptr;
+    if (!dev_out) {
+        CRP_CUDA(cudaMalloc(&stage, tot * (4 + 4 + 8 + 8)));
+        di = (int32_t *)stage;
+        dj = di + tot;
+        dw = (double *)(dj + tot);
+        dwl = w_lower ? dw + tot : nullptr;
+    }
+    CRP_CUDA(launch_export_range(pl->slots, pl->d_off, pl->d_mask, p0, p1, d_base, pl->d.value_type,
+                                 di, dj, dw, dwl, s));
+    if (!dev_out) {
+        CRP_CUDA(cudaMemcpyAsync(i_out, di, tot * 4, cudaMemcpyDeviceToHost, s));
+        CRP_CUDA(cudaMemcpyAsync(j_out, dj, tot * 4, cudaMemcpyDeviceToHost, s));
+        CRP_CUDA(cudaMemcpyAsync(w_out, dw, tot * 8, cudaMemcpyDeviceToHost, s));
+        if (w_lower) CRP_CUDA(cudaMemcpyAsync(w_lower, dwl, tot * 8, cudaMemcpyDeviceToHost, s));
+    }
+    CRP_CUDA(cudaStreamSynchronize(s));
+    cudaFree(stage);
+    cudaFree(d_base);
+    return CRP_OK;
+}
+
+extern "C" crp_status crp_stats(crp_plan *pl, crp_stats_t *out, uint64_t *terms_out) {
+    if (!pl || !out) return fail(CRP_EINVAL, "null argument");
+    memset(out, 0, sizeof *out);
+    const uint32_t P = pl->d.P;
+    out->P = P;
+    cudaStream_t s = pl->stream;
+    DevCounters dc;
+    CRP_CUDA(cudaMemcpyAsync(&dc, pl->dc, sizeof dc, cudaMemcpyDeviceToHost, s));
+    CRP_CUDA(cudaStreamSynchronize(s));
+    out->terms = dc.terms;
+    out->flushed_updates = dc.flushed;
+    out->spilled = dc.spill_n;
+    out->table_slots = pl->n_slots;
+    out->launches = pl->launches;
+    if (pl->timed) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pl->ev0, pl->ev1) == cudaSuccess) out->last_accumulate_ms = ms;
+        else cudaGetLastError();
+    }
+    if (!pl->tables_ready) return CRP_OK;
+    unsigned long long *d_terms = pl->d_scratch64, *d_live = pl->d_scratch64 + P;
+    CRP_CUDA(launch_partition_sums(pl->slots, pl->d_off, pl->d_mask, P, pl->d.value_type, d_terms,
+                                   d_live, s));
+    std::vector<unsigned long long> terms(P), live(P);
+    std::vector<unsigned int> full(P);
+    CRP_CUDA(cudaMemcpyAsync(terms.data(), d_terms, P * 8, cudaMemcpyDeviceToHost, s));
+    CRP_CUDA(cudaMemcpyAsync(live.data(), d_live, P * 8, cudaMemcpyDeviceToHost, s));
+    CRP_CUDA(cudaMemcpyAsync(full.data(), pl->d_full, P * 4, cudaMemcpyDeviceToHost, s));
+    CRP_CUDA(cudaStreamSynchronize(s));
+    unsigned long long mx = 0, sum = 0;
+    for (uint32_t p = 0; p < P; ++p) {
+        out->entries += live[p];
+        out->full_partitions += full[p] ? 1 : 0;
+        mx = std::max(mx, terms[p]);
+        sum += terms[p];
+        if (terms_out) terms_out[p] = terms[p];
+    }
+    out->max_over_mean_terms = sum ? (double)mx / ((double)sum / P) : 0.0;
+    return CRP_OK;
+}
+
+extern "C" crp_status crp_timing(crp_plan *pl, double *accumulate_ms, uint64_t *launches) {
+    if (!pl) return fail(CRP_EINVAL, "null plan");
+    if (launches) *launches = pl->launches;
+    if (accumulate_ms) {
+        *accumulate_ms = 0.0;
+        if (pl->timed) {
+            CRP_CUDA(cudaEventSynchronize(pl->ev1));
+            float ms = 0.f;
+            CRP_CUDA(cudaEventElapsedTime(&ms, pl->ev0, pl->ev1));
+            *accumulate_ms = ms;
+        }
+    }
+    return CRP_OK;
+}

@@ -1,0 +1,171 @@
+// Internal definitions shared by the CUDA translation units of libcrp.
+//
+// Partition hash (Section 4, Lemma 1 proof):  h(i,j) = (h_a(i) + h_b(j)) mod P
+// with multiply-add-shift side hashes h(x) = ((a x + b) mod 2^64) >> (64 - lg P),
+// (a, b) the first two SplitMix64 outputs of the side's seed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/crp.h"
+
+namespace crp {
+
+constexpr uint64_t kEmptyKey = ~0ull;   // i, j < 2^31 so no real key is all ones
+constexpr uint32_t kStatusTableFull = 1u;
+constexpr uint32_t kStatusSpillFull = 2u;
+constexpr uint32_t kStatusBadIndex = 4u;
+constexpr uint32_t kStatusTimeout = 8u;
+constexpr uint32_t kStatusSmemProbe = 16u;
+
+// One side hash, branch-free for P = 1: (v >> (64 - max(lg,1))) & (P - 1).
+struct SideHash {
+    uint64_t a, b;
+    uint32_t shift, mask;
+};
+
+struct HashPair {
+    SideHash ha, hb;
+};
+
+__host__ __device__ __forceinline__ uint32_t side_hash(const SideHash &h, uint32_t x) {
+    return (uint32_t)((h.a * (uint64_t)x + h.b) >> h.shift) & h.mask;
+}
+
+__host__ __device__ __forceinline__ uint32_t partition_hash(const HashPair &hp, uint32_t i,
+                                                            uint32_t j) {
+    return (side_hash(hp.ha, i) + side_hash(hp.hb, j)) & hp.ha.mask;
+}
+
+// Slot position hash inside one partition table (independent of the
+// partition hash): the 64-bit finaliser of MurmurHash3 (Appleby).
+__host__ __device__ __forceinline__ uint64_t slot_mix(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+__host__ __device__ __forceinline__ uint64_t make_key(uint32_t i, uint32_t j) {
+    return ((uint64_t)i << 32) | j;
+}
+
+// A 16-byte exact-table slot: the key, then an int32 count (int mode) or an
+// fp64 sum (real mode) in the second word.
+struct __align__(16) Slot {
+    unsigned long long key;
+    unsigned long long val;  // u32 count in the low half, or the bits of a double
+};
+
+// Device-side counters and the status word of one plan.
+struct DevCounters {
+    unsigned int status;
+    unsigned int work_next;          // dynamic work-item counter
+    unsigned long long terms;        // terms enumerated
+    unsigned long long flushed;      // entries flushed from on-chip tables
+    unsigned long long spill_n;      // spilled updates
+    unsigned long long bad_index;    // first bad index seen (debug checks)
+    unsigned int long_n;             // long vectors deferred by the sorter
+    unsigned int pad;
+};
+
+struct SpillRec {
+    unsigned long long key;
+    unsigned long long val;
+};
+
+// Everything a table-update kernel needs to reach the partition tables.
+struct TableView {
+    Slot *slots;
+    const unsigned long long *part_off;   // first slot of each partition
+    const unsigned long long *part_mask;  // capacity - 1 (capacity a power of two)
+    unsigned int *part_full;              // set once a partition had no free slot
+    SpillRec *spill;
+    unsigned long long spill_cap;
+    DevCounters *dc;
+    int value_type;
+};
+
+struct AccumulateArgs {
+    // inputs
+    const int64_t *a_ptr;
+    const int32_t *a_idx;
+    const float *a_val;
+    const int64_t *b_ptr;
+    const int32_t *b_idx;      // b indices in stream order, or sorted by h_b
+    const float *b_val;
+    int64_t K;
+    int32_t n_rows, n_cols;
+    // work decomposition
+    uint32_t groups;           // G; group g covers partitions [g P/G, (g+1) P/G)
+    uint32_t group_begin, group_end;
+    uint32_t tile;             // outer products per work item
+    uint32_t n_tiles;
+    int mode;                  // CRP_FULL | CRP_UPPER
+    int use_match;
+    int debug_checks;
+    uint32_t smem_slots;       // power of two
+    HashPair hp;
+    TableView tv;
+};
+
+// Launchers (defined in the .cu files).
+cudaError_t launch_sort_by_hash(const int64_t *ptr, const int32_t *idx, const float *val,
+                                int64_t K, SideHash h, int32_t *out_idx, float *out_val,
+                                uint32_t *out_hash, DevCounters *dc, unsigned int *long_list,
+                                int sm_count, cudaStream_t s);
+cudaError_t launch_accumulate(const AccumulateArgs &args, const uint32_t *b_hash, int grid,
+                              cudaStream_t s);
+int accumulate_block_threads();
+int accumulate_max_blocks_per_sm(int value_type, uint32_t smem_slots);
+size_t accumulate_smem_bytes(int value_type, uint32_t smem_slots);
+cudaError_t launch_count_terms(const int64_t *a_ptr, const int64_t *b_ptr, int64_t K,
+                               unsigned long long *out, cudaStream_t s);
+cudaError_t launch_fill_empty(Slot *slots, uint64_t n, cudaStream_t s);
+cudaError_t launch_partition_sums(const Slot *slots, const unsigned long long *part_off,
+                                  const unsigned long long *part_mask, uint32_t P,
+                                  int value_type, unsigned long long *terms_out,
+                                  unsigned long long *live_out, cudaStream_t s);
+cudaError_t launch_spill_reinsert(const SpillRec *spill, uint64_t n, HashPair hp,
+                                  TableView tv, cudaStream_t s);
+cudaError_t launch_rehash_partition(const Slot *old_slots, uint64_t old_off, uint64_t old_cap,
+                                    TableView tv, uint64_t new_off, uint64_t new_mask,
+                                    cudaStream_t s);
+cudaError_t launch_validate_sparse(const int64_t *ptr, const int32_t *idx, int64_t K, int64_t nnz,
+                                   int32_t n_minor, unsigned int *bad, cudaStream_t s);
+
+// Top-k (crp_topk.cu)
+struct TopkCand {
+    unsigned long long wkey;  // order-preserving bits of |w| (larger = heavier)
+    unsigned long long ij;    // (i << 32) | j
+    double w;
+    double wl;
+};
+cudaError_t launch_topk_hist(const Slot *slots, uint64_t n, int value_type, int upper_only,
+                             unsigned int *hist, cudaStream_t s);
+cudaError_t launch_topk_collect(const Slot *slots, uint64_t n, int value_type, int upper_only,
+                                unsigned int bucket_lo, TopkCand *out, unsigned int *count,
+                                unsigned int cap, cudaStream_t s);
+cudaError_t launch_topk_digit_hist(const TopkCand *c, unsigned int n, int digit,
+                                   unsigned int *hist, cudaStream_t s);
+cudaError_t launch_topk_digit_split(const TopkCand *c, unsigned int n, int digit,
+                                    unsigned int pivot, TopkCand *sel, unsigned int *sel_n,
+                                    TopkCand *keep, unsigned int *keep_n, cudaStream_t s);
+cudaError_t launch_topk_sort_write(const TopkCand *c, unsigned int n, int32_t *i_out,
+                                   int32_t *j_out, double *w_out, double *wl_out,
+                                   cudaStream_t s);
+cudaError_t launch_export_range(const Slot *slots, const unsigned long long *part_off,
+                                const unsigned long long *part_mask, uint32_t p0, uint32_t p1,
+                                const unsigned long long *base, int value_type, int32_t *i_out,
+                                int32_t *j_out, double *w_out, double *wl_out, cudaStream_t s);
+unsigned int topk_bucket_host(unsigned long long wkey);
+constexpr int kTopkBuckets = 4096;
+constexpr int kTopkSortMax = 8192;
+
+}  // namespace crp

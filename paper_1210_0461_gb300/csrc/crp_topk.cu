@@ -1,0 +1,259 @@
+// Heaviest entries of the partition tables (Section 6: the task is to find
+// the largest entries of the product) and table export.
+//
+// crp_topk runs:  (1) one pass over all slots building a log-linear histogram
+// of the weights, (2) one pass collecting the slots at or above the bucket
+// that holds the k-th largest weight, (3) when that candidate set is still
+// larger than one CTA can sort, an MSD radix select over the 128-bit order
+// key (weight descending, then (i, j) ascending) on the candidates only, and
+// (4) a single-CTA bitonic sort of the k survivors that writes the output.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "crp_internal.cuh"
+
+namespace crp {
+
+// Order-preserving 64-bit key of |w|: int counts as they are, doubles by the
+// bit pattern of their absolute value (IEEE order equals unsigned order for
+// non-negative doubles).
+__device__ __forceinline__ unsigned long long weight_key(const Slot &s, int value_type,
+                                                         double &w) {
+    if (value_type == CRP_I32) {
+        unsigned int c = (unsigned int)s.val;
+        w = (double)c;
+        return c;
+    }
+    w = __longlong_as_double((long long)s.val);
+    return (unsigned long long)__double_as_longlong(fabs(w));
+}
+
+// 65 exponents x 64 sub-buckets, but capped to kTopkBuckets.
+__host__ __device__ __forceinline__ unsigned int bucket_of(unsigned long long u) {
+    if (u == 0) return 0;
+#ifdef __CUDA_ARCH__
+    int e = 63 - __clzll((long long)u);
+#else
+    int e = 63 - __builtin_clzll(u);
+#endif
+    unsigned int m = e >= 6 ? (unsigned int)((u >> (e - 6)) & 63u)
+                            : (unsigned int)((u << (6 - e)) & 63u);
+    unsigned int b = 1u + (unsigned int)e * 64u + m;
+    return b < (unsigned)kTopkBuckets ? b : (unsigned)kTopkBuckets - 1u;
+}
+
+unsigned int topk_bucket_host(unsigned long long u) { return bucket_of(u); }
+
+__global__ void k_topk_hist(const Slot *__restrict__ slots, uint64_t n, int value_type,
+                            int upper_only, unsigned int *__restrict__ hist) {
+    __shared__ unsigned int h[kTopkBuckets];
+    for (int t = threadIdx.x; t < kTopkBuckets; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        Slot s = slots[x];
+        if (s.key == kEmptyKey) continue;
+        if (upper_only && !((uint32_t)(s.key >> 32) < (uint32_t)s.key)) continue;
+        double w;
+        atomicAdd(&h[bucket_of(weight_key(s, value_type, w))], 1u);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kTopkBuckets; t += blockDim.x)
+        if (h[t]) atomicAdd(&hist[t], h[t]);
+}
+
+cudaError_t launch_topk_hist(const Slot *slots, uint64_t n, int value_type, int upper_only,
+                             unsigned int *hist, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * kTopkBuckets, s);
+    if (e != cudaSuccess || n == 0) return e;
+    uint64_t blocks = (n + 511) / 512;
+    int grid = (int)(blocks < 4096 ? blocks : 4096);
+    k_topk_hist<<<grid, 512, 0, s>>>(slots, n, value_type, upper_only, hist);
+    return cudaGetLastError();
+}
+
+__global__ void k_topk_collect(const Slot *__restrict__ slots, uint64_t n, int value_type,
+                               int upper_only, unsigned int bucket_lo, TopkCand *out,
+                               unsigned int *count, unsigned int cap) {
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        Slot s = slots[x];
+        if (s.key == kEmptyKey) continue;
+        if (upper_only && !((uint32_t)(s.key >> 32) < (uint32_t)s.key)) continue;
+        double w;
+        unsigned long long u = weight_key(s, value_type, w);
+        if (bucket_of(u) < bucket_lo) continue;
+        unsigned int at = atomicAdd(count, 1u);
+        if (at < cap) {
+            TopkCand c;
+            c.wkey = u;
+            c.ij = s.key;
+            c.w = w;
+            c.wl = w;
+            out[at] = c;
+        }
+    }
+}
+
+cudaError_t launch_topk_collect(const Slot *slots, uint64_t n, int value_type, int upper_only,
+                                unsigned int bucket_lo, TopkCand *out, unsigned int *count,
+                                unsigned int cap, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess || n == 0) return e;
+    uint64_t blocks = (n + 511) / 512;
+    int grid = (int)(blocks < 4096 ? blocks : 4096);
+    k_topk_collect<<<grid, 512, 0, s>>>(slots, n, value_type, upper_only, bucket_lo, out, count,
+                                        cap);
+    return cudaGetLastError();
+}
+
+// Digit d (0 = most significant) of the descending 128-bit order key
+// (wkey, ~ij): larger digit = earlier in the output.
+__device__ __forceinline__ unsigned int order_digit(const TopkCand &c, int d) {
+    unsigned long long word = d < 8 ? c.wkey : ~c.ij;
+    int sh = 56 - 8 * (d & 7);
+    return (unsigned int)((word >> sh) & 255ull);
+}
+
+__global__ void k_topk_digit_hist(const TopkCand *__restrict__ c, unsigned int n, int digit,
+                                  unsigned int *hist) {
+    __shared__ unsigned int h[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    for (unsigned int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x)
+        atomicAdd(&h[order_digit(c[x], digit)], 1u);
+    __syncthreads();
+    for (int t = threadIdx.x; t < 256; t += blockDim.x)
+        if (h[t]) atomicAdd(&hist[t], h[t]);
+}
+
+cudaError_t launch_topk_digit_hist(const TopkCand *c, unsigned int n, int digit,
+                                   unsigned int *hist, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * 256, s);
+    if (e != cudaSuccess || n == 0) return e;
+    unsigned int blocks = (n + 255) / 256;
+    k_topk_digit_hist<<<blocks < 1024 ? blocks : 1024, 256, 0, s>>>(c, n, digit, hist);
+    return cudaGetLastError();
+}
+
+__global__ void k_topk_digit_split(const TopkCand *__restrict__ c, unsigned int n, int digit,
+                                   unsigned int pivot, TopkCand *sel, unsigned int *sel_n,
+                                   TopkCand *keep, unsigned int *keep_n) {
+    for (unsigned int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        TopkCand v = c[x];
+        unsigned int d = order_digit(v, digit);
+        if (d > pivot) sel[atomicAdd(sel_n, 1u)] = v;
+        else if (d == pivot) keep[atomicAdd(keep_n, 1u)] = v;
+    }
+}
+
+cudaError_t launch_topk_digit_split(const TopkCand *c, unsigned int n, int digit,
+                                    unsigned int pivot, TopkCand *sel, unsigned int *sel_n,
+                                    TopkCand *keep, unsigned int *keep_n, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(keep_n, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess || n == 0) return e;
+    unsigned int blocks = (n + 255) / 256;
+    k_topk_digit_split<<<blocks < 1024 ? blocks : 1024, 256, 0, s>>>(c, n, digit, pivot, sel,
+                                                                     sel_n, keep, keep_n);
+    return cudaGetLastError();
+}
+
+// One CTA sorts up to kTopkSortMax candidates by (wkey desc, ij asc) and
+// writes them out.
+__global__ void __launch_bounds__(1024)
+k_topk_sort_write(const TopkCand *__restrict__ c, unsigned int n, int32_t *i_out, int32_t *j_out,
+                  double *w_out, double *wl_out) {
+    extern __shared__ unsigned char sm[];
+    unsigned long long *kw = (unsigned long long *)sm;      // wkey
+    unsigned long long *kij = kw + kTopkSortMax;            // ~ij (descending sort)
+    unsigned short *src = (unsigned short *)(kij + kTopkSortMax);
+    int np = 1;
+    while (np < (int)n) np <<= 1;
+    for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        if (t < (int)n) {
+            kw[t] = c[t].wkey;
+            kij[t] = ~c[t].ij;
+        } else {
+            kw[t] = 0;
+            kij[t] = 0;
+        }
+        src[t] = (unsigned short)t;
+    }
+    __syncthreads();
+    // bitonic sort, descending by (kw, kij)
+    for (int size = 2; size <= np; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < (np >> 1); t += blockDim.x) {
+                int lo = 2 * t - (t & (stride - 1));
+                int hi = lo + stride;
+                bool desc = (lo & size) == 0;
+                bool lo_less = kw[lo] < kw[hi] || (kw[lo] == kw[hi] && kij[lo] < kij[hi]);
+                if (lo_less == desc) {
+                    unsigned long long a = kw[lo]; kw[lo] = kw[hi]; kw[hi] = a;
+                    a = kij[lo]; kij[lo] = kij[hi]; kij[hi] = a;
+                    unsigned short b = src[lo]; src[lo] = src[hi]; src[hi] = b;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int t = threadIdx.x; t < (int)n; t += blockDim.x) {
+        const TopkCand &v = c[src[t]];
+        i_out[t] = (int32_t)(v.ij >> 32);
+        j_out[t] = (int32_t)(uint32_t)v.ij;
+        w_out[t] = v.w;
+        if (wl_out) wl_out[t] = v.wl;
+    }
+}
+
+cudaError_t launch_topk_sort_write(const TopkCand *c, unsigned int n, int32_t *i_out,
+                                   int32_t *j_out, double *w_out, double *wl_out,
+                                   cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    size_t smem = (size_t)kTopkSortMax * (8 + 8 + 2);
+    cudaError_t e = cudaFuncSetAttribute(k_topk_sort_write,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_topk_sort_write<<<1, 1024, smem, s>>>(c, n, i_out, j_out, w_out, wl_out);
+    return cudaGetLastError();
+}
+
+// Export the live slots of partitions [p0, p1): block b handles partition
+// p0 + b (grid-stride), placing entries at base[p - p0] + a block cursor.
+__global__ void k_export(const Slot *__restrict__ slots, const unsigned long long *part_off,
+                         const unsigned long long *part_mask, uint32_t p0, uint32_t p1,
+                         const unsigned long long *base, int value_type, int32_t *i_out,
+                         int32_t *j_out, double *w_out, double *wl_out) {
+    __shared__ unsigned int cursor;
+    for (uint32_t p = p0 + blockIdx.x; p < p1; p += gridDim.x) {
+        if (threadIdx.x == 0) cursor = 0;
+        __syncthreads();
+        const unsigned long long off = part_off[p], cap = part_mask[p] + 1ull;
+        const unsigned long long b = base[p - p0];
+        for (unsigned long long x = threadIdx.x; x < cap; x += blockDim.x) {
+            Slot s = slots[off + x];
+            if (s.key == kEmptyKey) continue;
+            unsigned int at = atomicAdd(&cursor, 1u);
+            double w;
+            weight_key(s, value_type, w);
+            i_out[b + at] = (int32_t)(s.key >> 32);
+            j_out[b + at] = (int32_t)(uint32_t)s.key;
+            w_out[b + at] = w;
+            if (wl_out) wl_out[b + at] = w;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_export_range(const Slot *slots, const unsigned long long *part_off,
+                                const unsigned long long *part_mask, uint32_t p0, uint32_t p1,
+                                const unsigned long long *base, int value_type, int32_t *i_out,
+                                int32_t *j_out, double *w_out, double *wl_out, cudaStream_t s) {
+    if (p1 <= p0) return cudaSuccess;
+    uint32_t n = p1 - p0;
+    k_export<<<n < 4096 ? n : 4096, 256, 0, s>>>(slots, part_off, part_mask, p0, p1, base,
+                                                  value_type, i_out, j_out, w_out, wl_out);
+    return cudaGetLastError();
+}
+
+}  // namespace crp

@@ -1,0 +1,269 @@
+"""GPU parity of the exact column-row product against the CPU oracle.
+
+Every test drives the CUDA path through the C ABI (ctypes binding) and
+compares with the oracle on the same seeded inputs: integer counts bit-exact,
+real values within 1e-6 relative of the fp64 oracle (the bound stated for the
+compensated fp32 path)."""
+import numpy as np
+import pytest
+
+import crp_inputs as ci
+from oracle import crp_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+RTOL_REAL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def crp():
+    import torch
+    import paper_1210_0461_gb300 as pkg
+    pkg.build()
+    from paper_1210_0461_gb300 import crp as c
+    torch.cuda.init()
+    return c
+
+
+def _sorted(i, j, w):
+    o = np.lexsort((j, i))
+    return i[o].astype(np.int64), j[o].astype(np.int64), w[o]
+
+
+def _run(crp, A, B, n_rows, n_cols, P, mode=O.FULL, value_type=0, **kw):
+    dA = crp.to_device(A)
+    dB = dA if B is A else crp.to_device(B)
+    plan = crp.Plan(n_rows, n_cols, P, ci.SEED_A, ci.SEED_B, value_type=value_type, mode=mode,
+                    flags=kw.pop("flags", crp.CRP_PLAN_DEBUG_CHECKS), **kw)
+    plan.accumulate(dA, dB)
+    plan.sync()
+    return plan
+
+
+def _check_exact(crp, plan, ref, P):
+    i, j, w, _ = plan.export()
+    gi, gj, gw = _sorted(i, j, w)
+    assert np.array_equal(gi, ref.i) and np.array_equal(gj, ref.j)
+    assert np.array_equal(gw, ref.w)
+    # every entry sits in the partition h(i, j) and in no other
+    for p in range(0, P, max(1, P // 8)):
+        pi, pj, _, _ = plan.export(p, p + 1)
+        assert (O.partition_of(pi, pj, P, ci.SEED_A, ci.SEED_B) == p).all()
+    st = plan.stats(per_partition=True)
+    assert st["terms"] == ref.terms
+    assert st["entries"] == len(ref.i)
+    return st
+
+
+CONFIGS = [
+    dict(groups=1), dict(groups=4), dict(groups=64, tile_vectors=16),
+    dict(groups=1, smem_slots=4096, flags=0), dict(groups=16, smem_slots=16384, tile_vectors=256),
+    dict(groups=2, flags=1 | 2),  # no warp match
+]
+
+
+@pytest.mark.parametrize("cfg", CONFIGS, ids=lambda c: ",".join(f"{k}={v}" for k, v in c.items()))
+def test_c1_cooccurrence_full_bit_exact(crp, cfg):
+    T = ci.C1.generate()
+    Tc = O.Compressed.of(T)
+    ref = O.exact_product(Tc, Tc, O.FULL)
+    cfg = dict(cfg)
+    plan = _run(crp, T, T, 1000, 1000, 64, **cfg)
+    st = _check_exact(crp, plan, ref, 64)
+    want = O.partition_term_counts(Tc, Tc, 64, ci.SEED_A, ci.SEED_B)
+    assert st["partition_terms"].astype(np.int64).tolist() == want.tolist()
+    assert st["terms"] == int((T.lengths() ** 2).sum())
+    plan.close()
+
+
+def test_c1_upper_and_topk(crp):
+    T = ci.C1.generate()
+    Tc = O.Compressed.of(T)
+    ref = O.exact_product(Tc, Tc, O.UPPER)
+    plan = _run(crp, T, T, 1000, 1000, 64, mode=O.UPPER, groups=8)
+    _check_exact(crp, plan, ref, 64)
+    assert ref.terms == int((T.lengths() * (T.lengths() - 1) // 2).sum())
+    for k in (1, 10, 1000, 5000):
+        ti, tj, tw, _ = plan.topk(k)
+        ri, rj, rw = O.topk(ref.i, ref.j, ref.w, k)
+        assert np.array_equal(ti, ri) and np.array_equal(tj, rj) and np.array_equal(tw, rw)
+    plan.close()
+
+
+def test_topk_full_mode_upper_flag_and_large_k(crp):
+    T = ci.C1.generate()
+    Tc = O.Compressed.of(T)
+    ref = O.exact_product(Tc, Tc, O.FULL)
+    plan = _run(crp, T, T, 1000, 1000, 64, groups=2)
+    for k, up in ((1000, True), (8192, True), (8192, False), (3, False)):
+        ti, tj, tw, _ = plan.topk(k, upper=up)
+        ri, rj, rw = O.topk(ref.i, ref.j, ref.w, k, upper_only=up)
+        assert np.array_equal(ti, ri) and np.array_equal(tj, rj) and np.array_equal(tw, rw)
+    # device outputs
+    import torch
+    ti, tj, tw, _ = plan.topk(100, upper=True, device_out="cuda")
+    ri, rj, rw = O.topk(ref.i, ref.j, ref.w, 100, upper_only=True)
+    assert np.array_equal(ti.cpu().numpy(), ri) and np.array_equal(tw.cpu().numpy(), rw)
+    plan.close()
+
+
+def _random_case(seed, K, n_i, n_j, density, values):
+    rng = np.random.default_rng(seed)
+    ptrs, idxs = [], []
+    for n in (n_i, n_j):
+        ptr = [0]
+        idx = []
+        for k in range(K):
+            r = rng.random()
+            L = 0 if r < 0.1 else (1 if r < 0.2 else (n if r < 0.22 else rng.binomial(n, density)))
+            idx.extend(np.sort(rng.choice(n, L, replace=False)).tolist())
+            ptr.append(len(idx))
+        ptrs.append(np.array(ptr, np.int64))
+        idxs.append(np.array(idx, np.int32))
+    vA = rng.uniform(0.01, 3, len(idxs[0])).astype(np.float32) if values else None
+    vB = rng.uniform(0.01, 3, len(idxs[1])).astype(np.float32) if values else None
+    A = O.Compressed(ptrs[0], idxs[0], vA, n_i)
+    B = O.Compressed(ptrs[1], idxs[1], vB, n_j)
+    return A, B
+
+
+@pytest.mark.parametrize("seed,P,G", [(0, 1, 1), (1, 2, 2), (2, 64, 8), (3, 1024, 32),
+                                      (4, 4096, 4096), (5, 16, 1)])
+def test_random_edge_cases_int(crp, seed, P, G):
+    A, B = _random_case(seed, 700, 37 + seed * 50, 53 + seed * 30, 0.2, False)
+    ref = O.exact_product(A, B, O.FULL)
+    plan = _run(crp, A, B, A.n_minor, B.n_minor, P, groups=G, tile_vectors=7)
+    _check_exact(crp, plan, ref, P)
+    plan.close()
+
+
+@pytest.mark.parametrize("seed,G", [(10, 1), (11, 8)])
+def test_random_real_within_tolerance(crp, seed, G):
+    A, B = _random_case(seed, 600, 80, 90, 0.15, True)
+    ref = O.exact_product(A, B, O.FULL)
+    plan = _run(crp, A, B, 80, 90, 32, value_type=1, groups=G)
+    i, j, w, _ = plan.export()
+    gi, gj, gw = _sorted(i, j, w)
+    assert np.array_equal(gi, ref.i) and np.array_equal(gj, ref.j)
+    np.testing.assert_allclose(gw, ref.w, rtol=RTOL_REAL, atol=0)
+    plan.close()
+
+
+def test_real_single_product_entries_bit_exact(crp):
+    # Every column of A holds one nonzero, so each entry of A A is one product:
+    # the GPU's TwoProduct (p + e) must reproduce the fp64 product exactly.
+    rng = np.random.default_rng(3)
+    n = 3000
+    rows = rng.integers(0, n, n).astype(np.int32)
+    vals = rng.uniform(0.001, 1, n).astype(np.float32)
+    A = O.Compressed(np.arange(n + 1, dtype=np.int64), rows, vals, n)
+    At = O.Compressed.of(ci.transpose(ci.Sparse(A.ptr, A.idx, A.val, n)))
+    ref = O.exact_product(A, At, O.FULL)
+    plan = _run(crp, A, At, n, n, 16, value_type=1, groups=4)
+    i, j, w, _ = plan.export()
+    gi, gj, gw = _sorted(i, j, w)
+    assert np.array_equal(gi, ref.i) and np.array_equal(gj, ref.j)
+    assert np.array_equal(gw, ref.w)
+    plan.close()
+
+
+def test_c3_markov_expansion_scaled(crp):
+    A, At = ci.c3(n=20_000, cmax=400)
+    Ac, Atc = O.Compressed.of(A), O.Compressed.of(At)
+    ref = O.exact_product(Ac, Atc, O.FULL)
+    plan = _run(crp, A, At, A.n_minor, At.n_minor, 256, value_type=1, groups=16)
+    i, j, w, _ = plan.export()
+    gi, gj, gw = _sorted(i, j, w)
+    assert np.array_equal(gi, ref.i) and np.array_equal(gj, ref.j)
+    np.testing.assert_allclose(gw, ref.w, rtol=RTOL_REAL, atol=0)
+    # column-stochastic A: A A is column-stochastic too
+    colsum = np.bincount(gj, weights=gw, minlength=A.n_minor)
+    has = np.bincount(gj, minlength=A.n_minor) > 0
+    assert np.abs(colsum[has] - 1).max() < 1e-5
+    ti, tj, tw, _ = plan.topk(500)
+    ri, rj, rw = O.topk(ref.i, ref.j, ref.w, 500)
+    np.testing.assert_allclose(tw, rw, rtol=RTOL_REAL)
+    plan.close()
+
+
+def test_streaming_chunks_are_additive(crp):
+    T = ci.C1.scaled(m=9000).generate()
+    Tc = O.Compressed.of(T)
+    ref = O.exact_product(Tc, Tc, O.FULL)
+    plan = crp.Plan(1000, 1000, 64, ci.SEED_A, ci.SEED_B, groups=4,
+                    flags=crp.CRP_PLAN_DEBUG_CHECKS)
+    for lo, hi in ((0, 1000), (1000, 1001), (1001, 6000), (6000, 9000)):
+        ptr = T.ptr[lo:hi + 1] - T.ptr[lo]
+        part = ci.Sparse(ptr, T.idx[T.ptr[lo]:T.ptr[hi]], None, 1000)
+        d = crp.to_device(part)
+        plan.accumulate(d, d)
+    plan.sync()
+    _check_exact(crp, plan, ref, 64)
+    plan.close()
+
+
+def test_table_full_reported_and_auto_grow(crp):
+    T = ci.C1.scaled(m=5000).generate()
+    Tc = O.Compressed.of(T)
+    ref = O.exact_product(Tc, Tc, O.FULL)
+    d = crp.to_device(T)
+    plan = crp.Plan(1000, 1000, 16, ci.SEED_A, ci.SEED_B, capacity_hint=16 * 256)
+    plan.accumulate(d, d)
+    with pytest.raises(crp.CrpError) as e:
+        plan.sync()
+    assert e.value.status == crp.CRP_ETABLE_FULL
+    plan.close()
+    plan = crp.Plan(1000, 1000, 16, ci.SEED_A, ci.SEED_B, capacity_hint=16 * 256, auto_grow=True)
+    plan.accumulate(d, d)
+    plan.sync()
+    assert plan.stats()["full_partitions"] == 0
+    _check_exact(crp, plan, ref, 16)
+    plan.close()
+
+
+def test_invalid_arguments(crp):
+    with pytest.raises(crp.CrpError) as e:
+        crp.Plan(10, 10, 48, 1, 2)
+    assert e.value.status == crp.CRP_EINVAL
+    with pytest.raises(crp.CrpError):
+        crp.Plan(10, 10, 64, 1, 2, groups=128)
+    with pytest.raises(crp.CrpError):
+        crp.Plan(0, 10, 64, 1, 2)
+    plan = crp.Plan(100, 100, 4, 1, 2, flags=crp.CRP_PLAN_DEBUG_CHECKS)
+    bad = ci.Sparse(np.array([0, 2], np.int64), np.array([3, 150], np.int32), None, 100)
+    d = crp.to_device(bad)
+    with pytest.raises(crp.CrpError) as e:
+        plan.accumulate(d, d)
+    assert e.value.status == crp.CRP_EINVAL
+    vals = ci.Sparse(np.array([0, 1], np.int64), np.array([3], np.int32),
+                     np.array([1.0], np.float32), 100)
+    dv = crp.to_device(vals)
+    with pytest.raises(crp.CrpError) as e:
+        plan.accumulate(dv, dv)          # {0,1} plan given values
+    assert e.value.status == crp.CRP_EINVAL
+    plan.close()
+
+
+def test_partition_of_matches_oracle(crp):
+    plan = crp.Plan(10**6, 10**6, 8192, ci.SEED_A, ci.SEED_B, capacity_hint=8192 * 64)
+    rng = np.random.default_rng(0)
+    i = rng.integers(0, 10**6, 300)
+    j = rng.integers(0, 10**6, 300)
+    want = O.partition_of(i, j, 8192, ci.SEED_A, ci.SEED_B)
+    assert [plan.partition_of(int(a), int(b)) for a, b in zip(i, j)] == want.tolist()
+    plan.close()
+
+
+def test_repeat_runs_bit_identical(crp):
+    T = ci.C1.scaled(m=8000).generate()
+    d = crp.to_device(T)
+    outs = []
+    for G in (1, 8, 1):
+        plan = crp.Plan(1000, 1000, 64, ci.SEED_A, ci.SEED_B, groups=G)
+        plan.accumulate(d, d)
+        plan.sync()
+        outs.append(_sorted(*plan.export()[:3]))
+        plan.close()
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
