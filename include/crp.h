@@ -64,7 +64,10 @@ enum { CRP_FULL = 0,         /* every entry (i,j) */
 enum { CRP_TOPK_UPPER = 1 }; /* report only i < j */
 /* crp_plan_desc.flags */
 enum { CRP_PLAN_NO_WARP_MATCH = 1,  /* skip __match_any_sync pre-combining */
-       CRP_PLAN_DEBUG_CHECKS = 2 }; /* bounds-check every index on device */
+       CRP_PLAN_DEBUG_CHECKS = 2,   /* validate inputs and bounds-check indices */
+       CRP_PLAN_DIRECT = 4 };       /* no on-chip combining table: every
+                                       (warp-combined) term updates its
+                                       partition table in HBM directly */
 
 /* A compressed sparse matrix viewed as K vectors: vector k holds indices
  * idx[ptr[k] .. ptr[k+1]) (each < n_minor, distinct within a vector) with
@@ -190,6 +193,16 @@ crp_status crp_stats(crp_plan *plan, crp_stats_t *stats, uint64_t *terms_out);
  * kernels the plan has launched so far.  Either pointer may be NULL.  Cheap:
  * it does not scan the tables. */
 crp_status crp_timing(crp_plan *plan, double *accumulate_ms, uint64_t *launches);
+
+/* Measurement helper, not on the product path: device time (*ms_out) of
+ * n_updates random updates into a freshly allocated region of region_bytes
+ * (a power of two >= 4096; allocated and freed inside, default stream).
+ * mode 0: 32-bit atomic adds without return value at random words; mode 1:
+ * the exact-table update (read key, CAS an empty 16-byte slot, 32-bit add)
+ * with keys drawn from region/32 distinct values.  Gives the empirical update
+ * rate of an L2-resident vs an HBM-resident table.  Synchronises. */
+crp_status crp_probe_update_rate(uint64_t region_bytes, uint64_t n_updates, int mode,
+                                 double *ms_out);
 
 /* Library version string. */
 const char *crp_version(void);

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "CRP_OK", 1: "CRP_EINVAL", 2: "CRP_ENOMEM", 3: "CRP_ETABLE_FU
 CRP_I32, CRP_F32_COMP = 0, 1
 CRP_FULL, CRP_UPPER = 0, 1
 CRP_TOPK_UPPER = 1
-CRP_PLAN_NO_WARP_MATCH, CRP_PLAN_DEBUG_CHECKS = 1, 2
+CRP_PLAN_NO_WARP_MATCH, CRP_PLAN_DEBUG_CHECKS, CRP_PLAN_DIRECT = 1, 2, 4
 
 
 class CrpError(RuntimeError):
@@ -77,6 +77,8 @@ _SIGS = {
     "crp_stats": (ctypes.c_int, [_P, ctypes.POINTER(crp_stats_t), _P]),
     "crp_timing": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_uint64)]),
+    "crp_probe_update_rate": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_double)]),
     "crp_version": (ctypes.c_char_p, []),
     "crp_last_error": (ctypes.c_char_p, []),
 }
@@ -283,3 +285,11 @@ class Plan:
         if per_partition:
             d["partition_terms"] = terms
         return d
+
+
+def probe_update_rate(region_bytes: int, n_updates: int, mode: int) -> float:
+    """Updates per second of the random-update probe (see include/crp.h)."""
+    ms = ctypes.c_double(0)
+    _check(lib().crp_probe_update_rate(region_bytes, n_updates, mode, ctypes.byref(ms)),
+           "crp_probe_update_rate")
+    return n_updates / (ms.value / 1e3)

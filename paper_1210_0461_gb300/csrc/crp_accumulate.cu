@@ -255,11 +255,49 @@ __device__ void flush_table(unsigned long long *keys, void *vals, uint32_t S,
     }
 }
 
-template <int VT>
+// One chunk of a warp's enumeration: lane t takes flattened term pos + lane of
+// the current batch.  Returns the term (valid, i, j, a value, b value).
+__device__ __forceinline__ bool next_term(WarpEnum &st, const AccumulateArgs &A, int lane,
+                                          int value_type, uint32_t &oi, uint32_t &j, float &owa,
+                                          float &wb) {
+    const int32_t t = st.pos + lane;
+    bool valid = t < st.total;
+    int o = 0;
+#pragma unroll
+    for (int s2 = 16; s2 > 0; s2 >>= 1) {
+        int32_t e = __shfl_sync(kFull, st.excl, o + s2);
+        if (e <= t) o += s2;
+    }
+    oi = __shfl_sync(kFull, st.my_i, o);
+    owa = __shfl_sync(kFull, st.my_wa, o);
+    const int32_t olo1 = __shfl_sync(kFull, st.lo1, o);
+    const int32_t on1 = __shfl_sync(kFull, st.n1, o);
+    const int32_t olo2 = __shfl_sync(kFull, st.lo2, o);
+    const int32_t oex = __shfl_sync(kFull, st.excl, o);
+    st.pos += 32;
+    j = 0;
+    wb = 1.0f;
+    if (valid) {
+        const int32_t off = t - oex;
+        const int32_t m = off < on1 ? olo1 + off : olo2 + (off - on1);
+        j = (uint32_t)__ldg(A.b_idx + st.b_beg + m);
+        if (value_type != CRP_I32 && A.b_val) wb = __ldg(A.b_val + st.b_beg + m);
+        if (A.debug_checks && (oi >= (uint32_t)A.n_rows || j >= (uint32_t)A.n_cols)) {
+            atomicOr(&A.tv.dc->status, kStatusBadIndex);
+            valid = false;
+        }
+        if (A.mode == CRP_UPPER && !(oi < j)) valid = false;
+    }
+    return valid;
+}
+
+// VT: value type.  DIRECT: no on-chip table; every (warp-combined) term goes
+// straight to its partition table in HBM.
+template <int VT, bool DIRECT>
 __global__ void __launch_bounds__(kThreads, 2)
 k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const uint32_t S = A.smem_slots;
+    const uint32_t S = DIRECT ? 0u : A.smem_slots;
     const uint32_t smask = S - 1u;
     unsigned long long *keys = (unsigned long long *)smem_raw;
     void *vals = (void *)(keys + S);
@@ -276,7 +314,7 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
     if (threadIdx.x == 0) ctrl[0] = 0u;
     __syncthreads();
 
-    const uint32_t threshold = (3u * S) / 4u - (uint32_t)kMaxNewPerRound;
+    const uint32_t threshold = DIRECT ? 0u : (3u * S) / 4u - (uint32_t)kMaxNewPerRound;
     const uint32_t P = A.hp.ha.mask + 1u;
     const uint32_t w = P / A.groups;
     const uint32_t n_groups_here = A.group_end - A.group_begin;
@@ -301,38 +339,46 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
         st.total = 0;
         st.pos = 0;
 
+        if (DIRECT) {
+            while (advance(st, A, b_hash, q, w, lane)) {
+                uint32_t oi, j;
+                float owa, wb;
+                const bool valid = next_term(st, A, lane, VT, oi, j, owa, wb);
+                const unsigned long long key = make_key(oi, j);
+                const unsigned act = __ballot_sync(kFull, valid);
+                my_terms += valid ? 1 : 0;
+                if (valid) {
+                    if (VT == CRP_I32) {
+                        unsigned cnt = 1;
+                        bool lead = true;
+                        if (A.use_match) {
+                            unsigned peers = __match_any_sync(act, key);
+                            lead = lane == __ffs(peers) - 1;
+                            cnt = __popc(peers);
+                        }
+                        if (lead) {
+                            table_update(A.tv, partition_hash(A.hp, oi, j), key, cnt);
+                            ++flushed;
+                        }
+                    } else {
+                        const float p = __fmul_rn(owa, wb);
+                        const float e = __fmaf_rn(owa, wb, -p);
+                        const double d = (double)p + (double)e;
+                        table_update(A.tv, partition_hash(A.hp, oi, j), key,
+                                     (unsigned long long)__double_as_longlong(d));
+                        ++flushed;
+                    }
+                }
+            }
+            continue;
+        }
+
         while (true) {
             for (int r = 0; r < kRoundChunks; ++r) {
                 if (st.done || !advance(st, A, b_hash, q, w, lane)) break;
-                // one chunk: lane takes flattened term pos + lane
-                const int32_t t = st.pos + lane;
-                bool valid = t < st.total;
-                int o = 0;
-#pragma unroll
-                for (int s2 = 16; s2 > 0; s2 >>= 1) {
-                    int32_t e = __shfl_sync(kFull, st.excl, o + s2);
-                    if (e <= t) o += s2;
-                }
-                const uint32_t oi = __shfl_sync(kFull, st.my_i, o);
-                const float owa = __shfl_sync(kFull, st.my_wa, o);
-                const int32_t olo1 = __shfl_sync(kFull, st.lo1, o);
-                const int32_t on1 = __shfl_sync(kFull, st.n1, o);
-                const int32_t olo2 = __shfl_sync(kFull, st.lo2, o);
-                const int32_t oex = __shfl_sync(kFull, st.excl, o);
-                st.pos += 32;
-                uint32_t j = 0;
-                float wb = 1.0f;
-                if (valid) {
-                    const int32_t off = t - oex;
-                    const int32_t m = off < on1 ? olo1 + off : olo2 + (off - on1);
-                    j = (uint32_t)__ldg(A.b_idx + st.b_beg + m);
-                    if (VT != CRP_I32 && A.b_val) wb = __ldg(A.b_val + st.b_beg + m);
-                    if (A.debug_checks && (oi >= (uint32_t)A.n_rows || j >= (uint32_t)A.n_cols)) {
-                        atomicOr(&A.tv.dc->status, kStatusBadIndex);
-                        valid = false;
-                    }
-                    if (A.mode == CRP_UPPER && !(oi < j)) valid = false;
-                }
+                uint32_t oi, j;
+                float owa, wb;
+                const bool valid = next_term(st, A, lane, VT, oi, j, owa, wb);
                 const unsigned long long key = make_key(oi, j);
                 const unsigned act = __ballot_sync(kFull, valid);
                 my_terms += valid ? 1 : 0;
@@ -376,8 +422,10 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
             if (!more) break;
         }
     }
-    __syncthreads();
-    flush_table<VT>(keys, vals, S, A, flushed);
+    if (!DIRECT) {
+        __syncthreads();
+        flush_table<VT>(keys, vals, S, A, flushed);
+    }
 
     // aggregate counters: warp reduce then one atomic per warp
 #pragma unroll
@@ -391,40 +439,46 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
     }
 }
 
-cudaError_t launch_accumulate(const AccumulateArgs &args, const uint32_t *b_hash, int grid,
+template <int VT, bool DIRECT>
+static cudaError_t launch_one(const AccumulateArgs &args, const uint32_t *b_hash, int grid,
                               cudaStream_t s) {
-    const size_t smem = accumulate_smem_bytes(args.tv.value_type, args.smem_slots);
-    cudaError_t e;
-    if (args.tv.value_type == CRP_I32) {
-        e = cudaFuncSetAttribute(k_accumulate<CRP_I32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        k_accumulate<CRP_I32><<<grid, kThreads, smem, s>>>(args, b_hash);
-    } else {
-        e = cudaFuncSetAttribute(k_accumulate<CRP_F32_COMP>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_accumulate<CRP_F32_COMP><<<grid, kThreads, smem, s>>>(args, b_hash);
-    }
+    const size_t smem = DIRECT ? 64 : accumulate_smem_bytes(VT, args.smem_slots);
+    cudaError_t e = cudaFuncSetAttribute(k_accumulate<VT, DIRECT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_accumulate<VT, DIRECT><<<grid, kThreads, smem, s>>>(args, b_hash);
     return cudaGetLastError();
 }
 
-int accumulate_max_blocks_per_sm(int value_type, uint32_t smem_slots) {
-    const size_t smem = accumulate_smem_bytes(value_type, smem_slots);
+cudaError_t launch_accumulate(const AccumulateArgs &args, const uint32_t *b_hash, int grid,
+                              cudaStream_t s) {
+    const bool direct = args.direct != 0;
+    if (args.tv.value_type == CRP_I32)
+        return direct ? launch_one<CRP_I32, true>(args, b_hash, grid, s)
+                      : launch_one<CRP_I32, false>(args, b_hash, grid, s);
+    return direct ? launch_one<CRP_F32_COMP, true>(args, b_hash, grid, s)
+                  : launch_one<CRP_F32_COMP, false>(args, b_hash, grid, s);
+}
+
+template <int VT, bool DIRECT>
+static int occupancy_one(uint32_t smem_slots) {
+    const size_t smem = DIRECT ? 64 : accumulate_smem_bytes(VT, smem_slots);
     int n = 0;
-    if (value_type == CRP_I32) {
-        if (cudaFuncSetAttribute(k_accumulate<CRP_I32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess) return 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_accumulate<CRP_I32>, kThreads, smem)
-            != cudaSuccess) return 0;
-    } else {
-        if (cudaFuncSetAttribute(k_accumulate<CRP_F32_COMP>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_accumulate<CRP_F32_COMP>, kThreads,
-                                                          smem) != cudaSuccess) return 0;
-    }
+    if (cudaFuncSetAttribute(k_accumulate<VT, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_accumulate<VT, DIRECT>, kThreads, smem)
+        != cudaSuccess)
+        return 0;
     return n;
+}
+
+int accumulate_max_blocks_per_sm(int value_type, uint32_t smem_slots, bool direct) {
+    if (value_type == CRP_I32)
+        return direct ? occupancy_one<CRP_I32, true>(smem_slots)
+                      : occupancy_one<CRP_I32, false>(smem_slots);
+    return direct ? occupancy_one<CRP_F32_COMP, true>(smem_slots)
+                  : occupancy_one<CRP_F32_COMP, false>(smem_slots);
 }
 
 // ---------------------------------------------------------------------------

@@ -132,7 +132,7 @@ static crp_status alloc_tables(crp_plan *pl, uint64_t cap_per_partition) {
     CRP_CUDA(launch_fill_empty(pl->slots, total, pl->stream));
     pl->launches += 1;
     if (!pl->spill) {
-        pl->spill_cap = std::max<uint64_t>(1u << 16, std::min<uint64_t>(total / 8, 1ull << 24));
+        pl->spill_cap = std::max<uint64_t>(1u << 20, std::min<uint64_t>(total / 4, 1ull << 25));
         CRP_CUDA(cudaMalloc(&pl->spill, pl->spill_cap * sizeof(SpillRec)));
     }
     pl->tables_ready = true;
@@ -186,7 +186,8 @@ extern "C" crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc,
     if (st == CRP_OK && cudaMemsetAsync(pl->dc, 0, sizeof(DevCounters), pl->stream) != cudaSuccess)
         st = fail(CRP_ECUDA, "memset failed");
     if (st == CRP_OK) {
-        int per_sm = accumulate_max_blocks_per_sm(d.value_type, pl->S);
+        int per_sm = accumulate_max_blocks_per_sm(d.value_type, pl->S,
+                                                  (d.flags & CRP_PLAN_DIRECT) != 0);
         if (per_sm <= 0) st = fail(CRP_ECUDA, "accumulate kernel cannot be resident");
         pl->grid = per_sm * pl->sm_count;
     }
@@ -312,6 +313,7 @@ static AccumulateArgs make_args(crp_plan *pl, const crp_sparse *A, const crp_spa
     a.mode = pl->d.mode;
     a.use_match = (pl->d.flags & CRP_PLAN_NO_WARP_MATCH) ? 0 : 1;
     a.debug_checks = (pl->d.flags & CRP_PLAN_DEBUG_CHECKS) ? 1 : 0;
+    a.direct = (pl->d.flags & CRP_PLAN_DIRECT) ? 1 : 0;
     a.smem_slots = pl->S;
     a.hp = pl->hp;
     return a;
@@ -600,6 +602,7 @@ extern "C" crp_status crp_topk(crp_plan *pl, int32_t k, uint32_t flags, int32_t 
                                 cnt, (unsigned)n_c, s));
     pl->launches += 1;
     const TopkCand *final_c = cand;
+    unsigned int final_sort = (unsigned int)n_c;  // candidates to sort
     unsigned int final_n = (unsigned int)std::min<uint64_t>(n_c, (uint64_t)k);
     if (st == CRP_OK && n_c > (uint64_t)kTopkSortMax) {
         // MSD radix select on the candidates down to exactly k
@@ -639,6 +642,7 @@ extern "C" crp_status crp_topk(crp_plan *pl, int32_t k, uint32_t flags, int32_t 
         }
         final_c = sel;
         final_n = n_sel;
+        final_sort = n_sel;
     }
     // write out (through a device staging buffer when the outputs are host memory)
     const bool dev_out = is_device_ptr(i_out);
@@ -652,7 +656,8 @@ extern "C" crp_status crp_topk(crp_plan *pl, int32_t k, uint32_t flags, int32_t 
         dw = (double *)(dj + k);
         dwl = w_lower ? dw + k : nullptr;
     }
-    if (st == CRP_OK) cuda_ok(launch_topk_sort_write(final_c, final_n, di, dj, dw, dwl, s));
+    if (st == CRP_OK)
+        cuda_ok(launch_topk_sort_write(final_c, final_sort, final_n, di, dj, dw, dwl, s));
     pl->launches += 1;
     if (st == CRP_OK && !dev_out) {
         cuda_ok(cudaMemcpyAsync(i_out, di, final_n * 4, cudaMemcpyDeviceToHost, s));

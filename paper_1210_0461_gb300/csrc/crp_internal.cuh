@@ -110,6 +110,7 @@ struct AccumulateArgs {
     int mode;                  // CRP_FULL | CRP_UPPER
     int use_match;
     int debug_checks;
+    int direct;                // no on-chip table (CRP_PLAN_DIRECT)
     uint32_t smem_slots;       // power of two
     HashPair hp;
     TableView tv;
@@ -123,7 +124,7 @@ cudaError_t launch_sort_by_hash(const int64_t *ptr, const int32_t *idx, const fl
 cudaError_t launch_accumulate(const AccumulateArgs &args, const uint32_t *b_hash, int grid,
                               cudaStream_t s);
 int accumulate_block_threads();
-int accumulate_max_blocks_per_sm(int value_type, uint32_t smem_slots);
+int accumulate_max_blocks_per_sm(int value_type, uint32_t smem_slots, bool direct);
 size_t accumulate_smem_bytes(int value_type, uint32_t smem_slots);
 cudaError_t launch_count_terms(const int64_t *a_ptr, const int64_t *b_ptr, int64_t K,
                                unsigned long long *out, cudaStream_t s);
@@ -157,8 +158,9 @@ cudaError_t launch_topk_digit_hist(const TopkCand *c, unsigned int n, int digit,
 cudaError_t launch_topk_digit_split(const TopkCand *c, unsigned int n, int digit,
                                     unsigned int pivot, TopkCand *sel, unsigned int *sel_n,
                                     TopkCand *keep, unsigned int *keep_n, cudaStream_t s);
-cudaError_t launch_topk_sort_write(const TopkCand *c, unsigned int n, int32_t *i_out,
-                                   int32_t *j_out, double *w_out, double *wl_out,
+// Sort n candidates (n <= kTopkSortMax) and write the first n_write.
+cudaError_t launch_topk_sort_write(const TopkCand *c, unsigned int n, unsigned int n_write,
+                                   int32_t *i_out, int32_t *j_out, double *w_out, double *wl_out,
                                    cudaStream_t s);
 cudaError_t launch_export_range(const Slot *slots, const unsigned long long *part_off,
                                 const unsigned long long *part_mask, uint32_t p0, uint32_t p1,

@@ -161,8 +161,8 @@ cudaError_t launch_topk_digit_split(const TopkCand *c, unsigned int n, int digit
 // One CTA sorts up to kTopkSortMax candidates by (wkey desc, ij asc) and
 // writes them out.
 __global__ void __launch_bounds__(1024)
-k_topk_sort_write(const TopkCand *__restrict__ c, unsigned int n, int32_t *i_out, int32_t *j_out,
-                  double *w_out, double *wl_out) {
+k_topk_sort_write(const TopkCand *__restrict__ c, unsigned int n, unsigned int n_write,
+                  int32_t *i_out, int32_t *j_out, double *w_out, double *wl_out) {
     extern __shared__ unsigned char sm[];
     unsigned long long *kw = (unsigned long long *)sm;      // wkey
     unsigned long long *kij = kw + kTopkSortMax;            // ~ij (descending sort)
@@ -197,7 +197,7 @@ k_topk_sort_write(const TopkCand *__restrict__ c, unsigned int n, int32_t *i_out
             __syncthreads();
         }
     }
-    for (int t = threadIdx.x; t < (int)n; t += blockDim.x) {
+    for (int t = threadIdx.x; t < (int)n_write; t += blockDim.x) {
         const TopkCand &v = c[src[t]];
         i_out[t] = (int32_t)(v.ij >> 32);
         j_out[t] = (int32_t)(uint32_t)v.ij;
@@ -206,15 +206,16 @@ k_topk_sort_write(const TopkCand *__restrict__ c, unsigned int n, int32_t *i_out
     }
 }
 
-cudaError_t launch_topk_sort_write(const TopkCand *c, unsigned int n, int32_t *i_out,
-                                   int32_t *j_out, double *w_out, double *wl_out,
+cudaError_t launch_topk_sort_write(const TopkCand *c, unsigned int n, unsigned int n_write,
+                                   int32_t *i_out, int32_t *j_out, double *w_out, double *wl_out,
                                    cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     size_t smem = (size_t)kTopkSortMax * (8 + 8 + 2);
     cudaError_t e = cudaFuncSetAttribute(k_topk_sort_write,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_topk_sort_write<<<1, 1024, smem, s>>>(c, n, i_out, j_out, w_out, wl_out);
+    k_topk_sort_write<<<1, 1024, smem, s>>>(c, n, n_write < n ? n_write : n, i_out, j_out, w_out,
+                                            wl_out);
     return cudaGetLastError();
 }
 
