@@ -204,6 +204,34 @@ crp_status crp_timing(crp_plan *plan, double *accumulate_ms, uint64_t *launches)
 crp_status crp_probe_update_rate(uint64_t region_bytes, uint64_t n_updates, int mode,
                                  double *ms_out);
 
+/* An exact product for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc -- code running under an external memory manager that owns
+ * the device, code in a region where an allocation would synchronise or is
+ * forbidden, plug-ins whose host forbids the CUDA allocator.  It computes the
+ * same entries as crp_plan_create + crp_outer_accumulate + crp_export_partitions
+ * (desc fields n_rows, n_cols, P, seeds, value_type, mode are used; the rest
+ * are ignored) but keeps its partition tables in a file-scope static device
+ * array of 2^20 16-byte slots (16 MiB, held by every device that loads the
+ * library until the process exits) split evenly over P <= 1024 partitions.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   A, B: device inputs as for crp_outer_accumulate.
+ *   i_out, j_out, w_out: device arrays of `capacity` entries (caller-owned);
+ *     the entries are written unordered.  *n_out (host) = number of nonzero
+ *     entries, also when it exceeds capacity (then CRP_EINVAL).
+ *   stream: a cudaStream_t; the call synchronises it.
+ * Errors: CRP_EINVAL for P > 1024 or not a power of two, mismatched shapes or
+ * a too small output; CRP_ETABLE_FULL when a partition of the static table
+ * overflows (the product has too many entries for this entry point).
+ * The first call on a device looks up the static array's address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture.  Every call clears and reuses the same array,
+ * so calls whose work overlaps on the GPU race: serialise them. */
+crp_status crp_outer_product_noalloc(const crp_plan_desc *desc, const crp_sparse *A,
+                                     const crp_sparse *B, int32_t *i_out, int32_t *j_out,
+                                     double *w_out, int64_t capacity, int64_t *n_out,
+                                     void *stream);
+
 /* Library version string. */
 const char *crp_version(void);
 

@@ -79,6 +79,11 @@ _SIGS = {
                                   ctypes.POINTER(ctypes.c_uint64)]),
     "crp_probe_update_rate": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                              ctypes.POINTER(ctypes.c_double)]),
+    "crp_outer_product_noalloc": (ctypes.c_int, [ctypes.POINTER(crp_plan_desc),
+                                                 ctypes.POINTER(crp_sparse),
+                                                 ctypes.POINTER(crp_sparse), _P, _P, _P,
+                                                 ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                                 _P]),
     "crp_version": (ctypes.c_char_p, []),
     "crp_last_error": (ctypes.c_char_p, []),
 }

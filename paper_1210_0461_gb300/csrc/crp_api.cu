@@ -41,6 +41,10 @@ static crp_status fail(crp_status st, const std::string &msg) {
     } while (0)
 
 extern "C" const char *crp_last_error(void) { return g_last_error.c_str(); }
+
+namespace crp {
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}
 extern "C" const char *crp_version(void) { return "crp 0.1.0 (sm_103a)"; }
 
 // ---------------------------------------------------------------------------

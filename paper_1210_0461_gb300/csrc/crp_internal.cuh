@@ -116,6 +116,9 @@ struct AccumulateArgs {
     TableView tv;
 };
 
+// Record the calling thread's error message (read by crp_last_error).
+void set_last_error(const std::string &msg);
+
 // Launchers (defined in the .cu files).
 cudaError_t launch_sort_by_hash(const int64_t *ptr, const int32_t *idx, const float *val,
                                 int64_t K, SideHash h, int32_t *out_idx, float *out_val,
