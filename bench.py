@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--smem-slots", type=int, default=8192)
     ap.add_argument("--topk", type=int, default=1000)
     ap.add_argument("--no-match", action="store_true")
+    ap.add_argument("--mode", choices=["direct", "smem", "routed"], default="direct",
+                    help="accumulation variant (CRP_PLAN_DIRECT / on-chip table / CRP_PLAN_ROUTED)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -226,6 +228,7 @@ def main():
         dT = crp.to_device(T, f"cuda:{local}")
     torch.cuda.synchronize()
     flags = crp.CRP_PLAN_NO_WARP_MATCH if args.no_match else 0
+    flags |= {"direct": crp.CRP_PLAN_DIRECT, "smem": 0, "routed": crp.CRP_PLAN_ROUTED}[args.mode]
 
     # Partition-interval sharding (the paper's K processors with disjoint
     # intervals): with N ranks each rank owns G/N partition groups and reads
@@ -280,7 +283,7 @@ def main():
     entries = st["entries"]
     alg_bytes = (terms_step * BYTES_PER_TERM_UPDATE + dT.nbytes() + entries * SLOT_BYTES)
     achieved = alg_bytes / (acc / 1e3) / 1e9
-    tr = profiled_traffic(f"c2:P{args.P}:G{args.groups}:S{args.smem_slots}")
+    tr = profiled_traffic(f"c2:{args.mode}:P{args.P}:G{args.groups}:S{args.smem_slots}")
     traffic = tr * terms_step if tr is not None else None
 
     # ---- end to end through the C ABI from pinned host buffers ----
@@ -329,6 +332,7 @@ def main():
                                    "exact int32 T^T T (all entries), top-1000 pairs",
                        "P": args.P, "groups": args.groups, "tile_vectors": args.tile,
                        "smem_slots": args.smem_slots, "warp_match": not args.no_match,
+                       "mode": args.mode,
                        "terms_per_step": terms_step, "entries": entries,
                        "nnz": int(T.nnz), "l2": "inputs (0.8 GB) and tables "
                        f"({st['table_slots'] * 16 / 1e9:.1f} GB) exceed L2; no flush",

@@ -65,9 +65,15 @@ enum { CRP_TOPK_UPPER = 1 }; /* report only i < j */
 /* crp_plan_desc.flags */
 enum { CRP_PLAN_NO_WARP_MATCH = 1,  /* skip __match_any_sync pre-combining */
        CRP_PLAN_DEBUG_CHECKS = 2,   /* validate inputs and bounds-check indices */
-       CRP_PLAN_DIRECT = 4 };       /* no on-chip combining table: every
+       CRP_PLAN_DIRECT = 4,         /* no on-chip combining table: every
                                        (warp-combined) term updates its
                                        partition table in HBM directly */
+       CRP_PLAN_ROUTED = 8 };       /* two phases: enumerate every term once
+                                       into per-partition-group bins, then
+                                       apply the bins group by group so each
+                                       group's table region stays in L2
+                                       (bins = `groups` when set, else sized
+                                       to ~48 MB of table per group) */
 
 /* A compressed sparse matrix viewed as K vectors: vector k holds indices
  * idx[ptr[k] .. ptr[k+1]) (each < n_minor, distinct within a vector) with
@@ -131,6 +137,8 @@ typedef struct {
                                      combining kernel (CUDA events on the
                                      plan's stream) */
     uint64_t launches;            /* kernels this plan has launched */
+    double last_route_ms;         /* routed mode: device time of the routing
+                                     phase within last_accumulate_ms */
 } crp_stats_t;
 
 /* Create a plan: validates desc, derives the hash parameters and allocates

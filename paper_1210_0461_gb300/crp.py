@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "CRP_OK", 1: "CRP_EINVAL", 2: "CRP_ENOMEM", 3: "CRP_ETABLE_FU
 CRP_I32, CRP_F32_COMP = 0, 1
 CRP_FULL, CRP_UPPER = 0, 1
 CRP_TOPK_UPPER = 1
-CRP_PLAN_NO_WARP_MATCH, CRP_PLAN_DEBUG_CHECKS, CRP_PLAN_DIRECT = 1, 2, 4
+CRP_PLAN_NO_WARP_MATCH, CRP_PLAN_DEBUG_CHECKS, CRP_PLAN_DIRECT, CRP_PLAN_ROUTED = 1, 2, 4, 8
 
 
 class CrpError(RuntimeError):
@@ -55,7 +55,8 @@ class crp_stats_t(ctypes.Structure):
                 ("entries", ctypes.c_uint64), ("table_slots", ctypes.c_uint64),
                 ("spilled", ctypes.c_uint64), ("full_partitions", ctypes.c_uint32),
                 ("P", ctypes.c_uint32), ("max_over_mean_terms", ctypes.c_double),
-                ("last_accumulate_ms", ctypes.c_double), ("launches", ctypes.c_uint64)]
+                ("last_accumulate_ms", ctypes.c_double), ("launches", ctypes.c_uint64),
+                ("last_route_ms", ctypes.c_double)]
 
 
 _lock = threading.Lock()

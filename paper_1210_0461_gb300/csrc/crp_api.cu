@@ -101,9 +101,15 @@ struct crp_plan {
     uint32_t G = 1, tile = 64, S = 8192;
     int grid = 0;
     bool tables_ready = false;
+    // routed mode: per-group bins
+    void *bins = nullptr;
+    uint64_t bins_bytes = 0;
+    uint32_t B = 0;
+    unsigned long long *d_bin_off = nullptr, *d_bin_cap = nullptr, *d_bin_cnt = nullptr;
+    unsigned int *d_chunk_prefix = nullptr;
     // timing of the enumeration kernel and a count of our launches
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    bool timed = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;
+    bool timed = false, timed_mid = false;
     uint64_t launches = 0;
 };
 
@@ -196,7 +202,8 @@ extern "C" crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc,
         pl->grid = per_sm * pl->sm_count;
     }
     if (st == CRP_OK && (cudaEventCreate(&pl->ev0) != cudaSuccess ||
-                         cudaEventCreate(&pl->ev1) != cudaSuccess))
+                         cudaEventCreate(&pl->ev1) != cudaSuccess ||
+                         cudaEventCreate(&pl->evm) != cudaSuccess))
         st = fail(CRP_ECUDA, "cudaEventCreate failed");
     if (st == CRP_OK && d.table_capacity_hint) {
         uint64_t per = (d.table_capacity_hint + d.P - 1) / d.P;
@@ -225,8 +232,14 @@ extern "C" void crp_plan_destroy(crp_plan *pl) {
     cudaFree(pl->s_val);
     cudaFree(pl->s_hash);
     cudaFree(pl->s_long);
+    cudaFree(pl->bins);
+    cudaFree(pl->d_bin_off);
+    cudaFree(pl->d_bin_cap);
+    cudaFree(pl->d_bin_cnt);
+    cudaFree(pl->d_chunk_prefix);
     if (pl->ev0) cudaEventDestroy(pl->ev0);
     if (pl->ev1) cudaEventDestroy(pl->ev1);
+    if (pl->evm) cudaEventDestroy(pl->evm);
     delete pl;
 }
 
@@ -402,6 +415,78 @@ static crp_status estimate_and_allocate(crp_plan *pl, const crp_sparse *A, const
     return alloc_tables(pl, per);
 }
 
+// Routed mode: enumerate every term once into per-group bins, then apply the
+// bins group by group so each group's table region stays in L2.
+static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp_sparse *B) {
+    const uint32_t P = pl->d.P;
+    CRP_CUDA(launch_count_terms(A->ptr, B->ptr, A->n_major, pl->d_scratch64, pl->stream));
+    unsigned long long terms = 0;
+    CRP_CUDA(cudaMemcpyAsync(&terms, pl->d_scratch64, 8, cudaMemcpyDeviceToHost, pl->stream));
+    CRP_CUDA(cudaStreamSynchronize(pl->stream));
+    pl->launches += 1;
+    // groups of partitions whose table region is ~48 MB or less
+    const uint64_t table_bytes = pl->n_slots * sizeof(Slot);
+    uint64_t want = (table_bytes + (48ull << 20) - 1) / (48ull << 20);
+    uint32_t Bn = 1;
+    while (Bn < want && Bn < P) Bn <<= 1;
+    if (pl->d.groups) Bn = pl->G;  // explicit partition groups = bins
+    const int rec = pl->d.value_type == CRP_I32 ? 8 : 16;
+    const uint64_t per_bin = (uint64_t)((double)terms / Bn * 1.25) + 8192;
+    const uint64_t need = per_bin * Bn * rec;
+    if (Bn != pl->B) {
+        cudaFree(pl->d_bin_off);
+        cudaFree(pl->d_bin_cap);
+        cudaFree(pl->d_bin_cnt);
+        cudaFree(pl->d_chunk_prefix);
+        pl->d_bin_off = pl->d_bin_cap = pl->d_bin_cnt = nullptr;
+        pl->d_chunk_prefix = nullptr;
+        CRP_CUDA(cudaMalloc(&pl->d_bin_off, Bn * 8));
+        CRP_CUDA(cudaMalloc(&pl->d_bin_cap, Bn * 8));
+        CRP_CUDA(cudaMalloc(&pl->d_bin_cnt, Bn * 8));
+        CRP_CUDA(cudaMalloc(&pl->d_chunk_prefix, (Bn + 1) * 4));
+        pl->B = Bn;
+    }
+    if (need > pl->bins_bytes) {
+        cudaFree(pl->bins);
+        pl->bins = nullptr;
+        pl->bins_bytes = 0;
+        CRP_CUDA(cudaMalloc(&pl->bins, need));
+        pl->bins_bytes = need;
+    }
+    const uint64_t cap = pl->bins_bytes / rec / Bn;
+    std::vector<unsigned long long> off(Bn), capv(Bn, cap);
+    for (uint32_t b = 0; b < Bn; ++b) off[b] = (unsigned long long)b * cap;
+    CRP_CUDA(cudaMemcpyAsync(pl->d_bin_off, off.data(), Bn * 8, cudaMemcpyHostToDevice, pl->stream));
+    CRP_CUDA(cudaMemcpyAsync(pl->d_bin_cap, capv.data(), Bn * 8, cudaMemcpyHostToDevice,
+                             pl->stream));
+    CRP_CUDA(cudaMemsetAsync(pl->d_bin_cnt, 0, Bn * 8, pl->stream));
+    RouteArgs RA;
+    RA.acc = make_args(pl, A, B, B->idx, B->val, 1);
+    RA.acc.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
+    RA.bins = pl->bins;
+    RA.bin_off = pl->d_bin_off;
+    RA.bin_cap = pl->d_bin_cap;
+    RA.bin_cnt = pl->d_bin_cnt;
+    RA.B = Bn;
+    uint32_t lgB = 0;
+    while ((1u << lgB) < Bn) ++lgB;
+    RA.B_shift = pl->logP - lgB;
+    const size_t budget = 96u << 10;
+    uint64_t rs = (budget - (size_t)Bn * 4 - 16) / ((size_t)Bn * rec);
+    RA.R_s = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(rs, 1), 256);
+    RA.pad = 0;
+    CRP_CUDA(cudaMemsetAsync(&pl->dc->work_next, 0, sizeof(unsigned int), pl->stream));
+    CRP_CUDA(cudaEventRecord(pl->ev0, pl->stream));
+    CRP_CUDA(launch_route(RA, 2 * pl->sm_count, pl->stream));
+    CRP_CUDA(cudaEventRecord(pl->evm, pl->stream));
+    CRP_CUDA(launch_apply(RA, pl->d_chunk_prefix, 16384, 2 * pl->sm_count, pl->stream));
+    CRP_CUDA(cudaEventRecord(pl->ev1, pl->stream));
+    pl->timed = true;
+    pl->timed_mid = true;
+    pl->launches += 3;
+    return CRP_OK;
+}
+
 extern "C" crp_status crp_outer_accumulate(crp_plan *pl, const crp_sparse *A, const crp_sparse *B) {
     if (!pl) return fail(CRP_EINVAL, "null plan");
     crp_status st = check_sparse(A, "A");
@@ -432,7 +517,7 @@ extern "C" crp_status crp_outer_accumulate(crp_plan *pl, const crp_sparse *A, co
     const int32_t *b_idx = B->idx;
     const float *b_val = B->val;
     const uint32_t *b_hash = nullptr;
-    if (pl->G > 1) {
+    if (pl->G > 1 && !(pl->d.flags & CRP_PLAN_ROUTED)) {
         st = ensure_sort_scratch(pl, B->nnz, B->n_major, B->val != nullptr);
         if (st != CRP_OK) return st;
         CRP_CUDA(launch_sort_by_hash(B->ptr, B->idx, B->val, B->n_major, pl->hp.hb, pl->s_idx,
@@ -447,6 +532,7 @@ extern "C" crp_status crp_outer_accumulate(crp_plan *pl, const crp_sparse *A, co
         st = estimate_and_allocate(pl, A, B, b_idx, b_val);
         if (st != CRP_OK) return st;
     }
+    if (pl->d.flags & CRP_PLAN_ROUTED) return routed_accumulate(pl, A, B);
     AccumulateArgs a = make_args(pl, A, B, b_idx, b_val, pl->G);
     a.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
     CRP_CUDA(cudaMemsetAsync(&pl->dc->work_next, 0, sizeof(unsigned int), pl->stream));
@@ -454,6 +540,7 @@ extern "C" crp_status crp_outer_accumulate(crp_plan *pl, const crp_sparse *A, co
     CRP_CUDA(launch_accumulate(a, b_hash, pl->grid, pl->stream));
     CRP_CUDA(cudaEventRecord(pl->ev1, pl->stream));
     pl->timed = true;
+    pl->timed_mid = false;
     pl->launches += 1;
     return CRP_OK;
 }
@@ -748,6 +835,9 @@ extern "C" crp_status crp_stats(crp_plan *pl, crp_stats_t *out, uint64_t *terms_
     if (pl->timed) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, pl->ev0, pl->ev1) == cudaSuccess) out->last_accumulate_ms = ms;
+        else cudaGetLastError();
+        if (pl->timed_mid && cudaEventElapsedTime(&ms, pl->ev0, pl->evm) == cudaSuccess)
+            out->last_route_ms = ms;
         else cudaGetLastError();
     }
     if (!pl->tables_ready) return CRP_OK;

@@ -116,6 +116,19 @@ struct AccumulateArgs {
     TableView tv;
 };
 
+// Two-phase (routed) accumulation: bins of records per partition group.
+struct RouteArgs {
+    AccumulateArgs acc;        // enumeration inputs, hash and table view
+    void *bins;                // records: u64 keys (int) or {key, p, e} (real)
+    const unsigned long long *bin_off, *bin_cap;
+    unsigned long long *bin_cnt;
+    uint32_t B, B_shift, R_s, pad;
+};
+cudaError_t launch_route(const RouteArgs &RA, int grid, cudaStream_t s);
+cudaError_t launch_apply(const RouteArgs &RA, unsigned int *chunk_prefix, uint32_t CH, int grid,
+                         cudaStream_t s);
+size_t route_smem_bytes(int value_type, uint32_t B, uint32_t R_s);
+
 // Record the calling thread's error message (read by crp_last_error).
 void set_last_error(const std::string &msg);
 

@@ -56,7 +56,7 @@ def test_version_and_struct_sizes(libcrp):
     assert libcrp.crp_version().startswith(b"crp ")
     assert ctypes.sizeof(crp.crp_sparse) == 48
     assert ctypes.sizeof(crp.crp_plan_desc) == 80
-    assert ctypes.sizeof(crp.crp_stats_t) == 72
+    assert ctypes.sizeof(crp.crp_stats_t) == 80
 
 
 def test_sm103a_only_build_flags():

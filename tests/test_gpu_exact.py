@@ -59,6 +59,8 @@ CONFIGS = [
     dict(groups=1), dict(groups=4), dict(groups=64, tile_vectors=16),
     dict(groups=1, smem_slots=4096, flags=0), dict(groups=16, smem_slots=16384, tile_vectors=256),
     dict(groups=2, flags=1 | 2),  # no warp match
+    dict(flags=4 | 2), dict(groups=8, flags=4 | 2),  # direct HBM updates
+    dict(flags=8 | 2), dict(groups=16, flags=8 | 2), dict(groups=64, flags=8 | 1 | 2),  # routed
 ]
 
 
@@ -127,21 +129,22 @@ def _random_case(seed, K, n_i, n_j, density, values):
     return A, B
 
 
-@pytest.mark.parametrize("seed,P,G", [(0, 1, 1), (1, 2, 2), (2, 64, 8), (3, 1024, 32),
-                                      (4, 4096, 4096), (5, 16, 1)])
-def test_random_edge_cases_int(crp, seed, P, G):
+@pytest.mark.parametrize("seed,P,G,fl", [(0, 1, 1, 2), (1, 2, 2, 2), (2, 64, 8, 2),
+                                         (3, 1024, 32, 2), (4, 4096, 4096, 2), (5, 16, 1, 2),
+                                         (6, 256, 256, 8 | 2), (7, 1, 1, 8 | 2)])
+def test_random_edge_cases_int(crp, seed, P, G, fl):
     A, B = _random_case(seed, 700, 37 + seed * 50, 53 + seed * 30, 0.2, False)
     ref = O.exact_product(A, B, O.FULL)
-    plan = _run(crp, A, B, A.n_minor, B.n_minor, P, groups=G, tile_vectors=7)
+    plan = _run(crp, A, B, A.n_minor, B.n_minor, P, groups=G, tile_vectors=7, flags=fl)
     _check_exact(crp, plan, ref, P)
     plan.close()
 
 
-@pytest.mark.parametrize("seed,G", [(10, 1), (11, 8)])
-def test_random_real_within_tolerance(crp, seed, G):
+@pytest.mark.parametrize("seed,G,fl", [(10, 1, 2), (11, 8, 2), (12, 4, 8 | 2), (13, 1, 4 | 2)])
+def test_random_real_within_tolerance(crp, seed, G, fl):
     A, B = _random_case(seed, 600, 80, 90, 0.15, True)
     ref = O.exact_product(A, B, O.FULL)
-    plan = _run(crp, A, B, 80, 90, 32, value_type=1, groups=G)
+    plan = _run(crp, A, B, 80, 90, 32, value_type=1, groups=G, flags=fl)
     i, j, w, _ = plan.export()
     gi, gj, gw = _sorted(i, j, w)
     assert np.array_equal(gi, ref.i) and np.array_equal(gj, ref.j)
@@ -167,11 +170,12 @@ def test_real_single_product_entries_bit_exact(crp):
     plan.close()
 
 
-def test_c3_markov_expansion_scaled(crp):
+@pytest.mark.parametrize("fl", [2, 8 | 2])
+def test_c3_markov_expansion_scaled(crp, fl):
     A, At = ci.c3(n=20_000, cmax=400)
     Ac, Atc = O.Compressed.of(A), O.Compressed.of(At)
     ref = O.exact_product(Ac, Atc, O.FULL)
-    plan = _run(crp, A, At, A.n_minor, At.n_minor, 256, value_type=1, groups=16)
+    plan = _run(crp, A, At, A.n_minor, At.n_minor, 256, value_type=1, groups=16, flags=fl)
     i, j, w, _ = plan.export()
     gi, gj, gw = _sorted(i, j, w)
     assert np.array_equal(gi, ref.i) and np.array_equal(gj, ref.j)
