@@ -118,7 +118,7 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("crp_accumulate.cu", "crp_internal.cuh"):
+    for f in ("crp_accumulate.cu", "crp_device.cuh", "crp_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1210_0461_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

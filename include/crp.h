@@ -179,6 +179,22 @@ crp_status crp_sync(crp_plan *plan);
 crp_status crp_topk(crp_plan *plan, int32_t k, uint32_t flags, int32_t *i_out, int32_t *j_out,
                     double *w_out, double *w_lower, int32_t *n_out);
 
+/* Summary mode (desc.summary_counters = ell > 0, CRP_I32 only): each
+ * partition keeps a counter summary with the Space-Saving guarantees of the
+ * paper's Preliminaries -- for every key of partition p with stream weight
+ * W_p: lower <= true <= upper, upper - lower <= W_p / ell, and every key with
+ * true weight > W_p / ell is recorded; after each crp_outer_accumulate a
+ * partition holds at most ell keys.  crp_topk then ranks by the upper bound
+ * and reports the lower bound in w_lower; crp_export_partitions gives both.
+ *
+ * crp_reserve registers keys ((uint64_t)i << 32 | j; host or device array
+ * of n) whose updates go to exact counters probed before the summaries
+ * (desc.reserved_counters bounds their number).  Reserve before the
+ * accumulate calls whose terms should be counted exactly: weight added to a
+ * key before it was reserved stays in its partition's summary.  crp_reset
+ * keeps the reserved keys and zeroes their counts.  Synchronises. */
+crp_status crp_reserve(crp_plan *plan, const uint64_t *keys, int32_t n);
+
 /* Partition of entry (i,j): (h_a(i) + h_b(j)) mod P, computed on the host. */
 uint32_t crp_partition_of(const crp_plan *plan, int32_t i, int32_t j);
 

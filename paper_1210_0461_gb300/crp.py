@@ -73,6 +73,7 @@ _SIGS = {
     "crp_topk": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32, _P, _P, _P, _P,
                                 ctypes.POINTER(ctypes.c_int32)]),
     "crp_partition_of": (ctypes.c_uint32, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "crp_reserve": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
     "crp_export_partitions": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint32, _P, _P, _P, _P,
                                              ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "crp_stats": (ctypes.c_int, [_P, ctypes.POINTER(crp_stats_t), _P]),
@@ -184,13 +185,15 @@ class Plan:
     def __init__(self, n_rows: int, n_cols: int, P: int, seed_a: int, seed_b: int,
                  value_type: int = CRP_I32, mode: int = CRP_FULL, groups: int = 0,
                  tile_vectors: int = 0, smem_slots: int = 0, capacity_hint: int = 0,
-                 auto_grow: bool = False, flags: int = 0, stream=None):
+                 auto_grow: bool = False, flags: int = 0, stream=None,
+                 summary_counters: int = 0, reserved_counters: int = 0):
         self._lib = lib()
         d = crp_plan_desc()
         d.n_rows, d.n_cols, d.P = n_rows, n_cols, P
         d.seed_a, d.seed_b = seed_a & (2**64 - 1), seed_b & (2**64 - 1)
         d.value_type, d.mode = value_type, mode
         d.table_capacity_hint = capacity_hint
+        d.summary_counters, d.reserved_counters = summary_counters, reserved_counters
         d.auto_grow = 1 if auto_grow else 0
         d.groups, d.tile_vectors, d.smem_slots, d.flags = groups, tile_vectors, smem_slots, flags
         self.desc = d
@@ -229,6 +232,12 @@ class Plan:
 
     def sync(self):
         _check(self._lib.crp_sync(self._h), "crp_sync")
+
+    def reserve(self, keys):
+        """Register (i << 32 | j) keys for exact counting (summary mode)."""
+        k = np.ascontiguousarray(keys, dtype=np.uint64)
+        _check(self._lib.crp_reserve(self._h, k.ctypes.data if len(k) else None, len(k)),
+               "crp_reserve")
 
     def partition_of(self, i: int, j: int) -> int:
         return int(self._lib.crp_partition_of(self._h, i, j))

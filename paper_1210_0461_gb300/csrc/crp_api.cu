@@ -99,8 +99,19 @@ struct crp_plan {
     uint64_t s_nnz_cap = 0, s_k_cap = 0;
     // launch configuration
     uint32_t G = 1, tile = 64, S = 8192;
-    int grid = 0;
+    int grid = 0, grid_direct = 0;
     bool tables_ready = false;
+    float summary_ms = 0.f;
+    // summary mode
+    bool summary = false;
+    uint32_t ell = 0;
+    unsigned int *d_live = nullptr, *d_floor = nullptr;
+    Slot *d_ctmp = nullptr;
+    int ctmp_grid = 0;
+    SpillRec *d_spill2 = nullptr;
+    unsigned long long res_off = 0, res_mask = 0;
+    unsigned long long *d_res_keys = nullptr;
+    int32_t n_res = 0;
     // routed mode: per-group bins
     void *bins = nullptr;
     uint64_t bins_bytes = 0;
@@ -149,6 +160,50 @@ static crp_status alloc_tables(crp_plan *pl, uint64_t cap_per_partition) {
     return CRP_OK;
 }
 
+// Summary mode: every partition gets a table of next_pow2(4 ell) slots (at
+// most 2 ell occupied between compactions), followed by the reserved-counter
+// region; floors and live counts start at zero.
+static crp_status alloc_summary(crp_plan *pl) {
+    const uint32_t P = pl->d.P;
+    pl->summary = true;
+    pl->ell = pl->d.summary_counters;
+    const uint64_t cap = next_pow2(std::max<uint64_t>(4ull * pl->ell, 64));
+    const uint64_t rcap = pl->d.reserved_counters
+                              ? next_pow2(std::max<uint64_t>(2ull * pl->d.reserved_counters, 64))
+                              : 0;
+    pl->h_off.resize(P);
+    pl->h_mask.resize(P);
+    for (uint32_t p = 0; p < P; ++p) {
+        pl->h_off[p] = (unsigned long long)p * cap;
+        pl->h_mask[p] = cap - 1;
+    }
+    const uint64_t total = (uint64_t)P * cap + rcap;
+    CRP_CUDA(cudaMalloc(&pl->slots, total * sizeof(Slot)));
+    pl->n_slots = total;
+    pl->res_off = (uint64_t)P * cap;
+    pl->res_mask = rcap ? rcap - 1 : 0;
+    CRP_CUDA(cudaMemcpyAsync(pl->d_off, pl->h_off.data(), P * 8, cudaMemcpyHostToDevice,
+                             pl->stream));
+    CRP_CUDA(cudaMemcpyAsync(pl->d_mask, pl->h_mask.data(), P * 8, cudaMemcpyHostToDevice,
+                             pl->stream));
+    CRP_CUDA(cudaMemsetAsync(pl->d_full, 0, P * 4, pl->stream));
+    CRP_CUDA(cudaMalloc(&pl->d_live, P * 4));
+    CRP_CUDA(cudaMalloc(&pl->d_floor, P * 4));
+    CRP_CUDA(cudaMemsetAsync(pl->d_live, 0, P * 4, pl->stream));
+    CRP_CUDA(cudaMemsetAsync(pl->d_floor, 0, P * 4, pl->stream));
+    CRP_CUDA(launch_fill_empty(pl->slots, total, pl->stream));
+    pl->launches += 1;
+    pl->spill_cap = std::max<uint64_t>(1u << 20, std::min<uint64_t>((uint64_t)P * pl->ell, 1ull << 25));
+    CRP_CUDA(cudaMalloc(&pl->spill, pl->spill_cap * sizeof(SpillRec)));
+    CRP_CUDA(cudaMalloc(&pl->d_spill2, pl->spill_cap * sizeof(SpillRec)));
+    pl->ctmp_grid = (int)std::min<uint32_t>(P, (uint32_t)pl->sm_count);
+    CRP_CUDA(cudaMalloc(&pl->d_ctmp, (size_t)pl->ctmp_grid * pl->ell * sizeof(Slot)));
+    if (pl->d.reserved_counters)
+        CRP_CUDA(cudaMalloc(&pl->d_res_keys, (size_t)pl->d.reserved_counters * 8));
+    pl->tables_ready = true;
+    return CRP_OK;
+}
+
 extern "C" crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc, void *stream) {
     if (!out || !desc) return fail(CRP_EINVAL, "crp_plan_create: null argument");
     *out = nullptr;
@@ -163,8 +218,12 @@ extern "C" crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc,
         return fail(CRP_EINVAL, "smem_slots must be a power of two in [4096, 16384]");
     if (d.groups && (!is_pow2(d.groups) || d.groups > d.P))
         return fail(CRP_EINVAL, "groups must be a power of two <= P");
-    if (d.summary_counters)
-        return fail(CRP_EUNSUPPORTED, "summary mode is created with crp_summary_plan_create");
+    if (d.summary_counters && d.value_type != CRP_I32)
+        return fail(CRP_EUNSUPPORTED, "summaries count {0,1} inputs (CRP_I32) only");
+    if (d.summary_counters > (1u << 24))
+        return fail(CRP_EINVAL, "summary_counters must be <= 2^24 per partition");
+    if (d.reserved_counters > (1u << 24))
+        return fail(CRP_EINVAL, "reserved_counters must be <= 2^24");
     crp_plan *pl = new crp_plan();
     pl->d = d;
     pl->stream = (cudaStream_t)stream;
@@ -200,12 +259,15 @@ extern "C" crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc,
                                                   (d.flags & CRP_PLAN_DIRECT) != 0);
         if (per_sm <= 0) st = fail(CRP_ECUDA, "accumulate kernel cannot be resident");
         pl->grid = per_sm * pl->sm_count;
+        pl->grid_direct = accumulate_max_blocks_per_sm(d.value_type, pl->S, true) * pl->sm_count;
     }
     if (st == CRP_OK && (cudaEventCreate(&pl->ev0) != cudaSuccess ||
                          cudaEventCreate(&pl->ev1) != cudaSuccess ||
                          cudaEventCreate(&pl->evm) != cudaSuccess))
         st = fail(CRP_ECUDA, "cudaEventCreate failed");
-    if (st == CRP_OK && d.table_capacity_hint) {
+    if (st == CRP_OK && d.summary_counters) {
+        st = alloc_summary(pl);
+    } else if (st == CRP_OK && d.table_capacity_hint) {
         uint64_t per = (d.table_capacity_hint + d.P - 1) / d.P;
         st = alloc_tables(pl, per);
     }
@@ -232,6 +294,11 @@ extern "C" void crp_plan_destroy(crp_plan *pl) {
     cudaFree(pl->s_val);
     cudaFree(pl->s_hash);
     cudaFree(pl->s_long);
+    cudaFree(pl->d_live);
+    cudaFree(pl->d_floor);
+    cudaFree(pl->d_ctmp);
+    cudaFree(pl->d_spill2);
+    cudaFree(pl->d_res_keys);
     cudaFree(pl->bins);
     cudaFree(pl->d_bin_off);
     cudaFree(pl->d_bin_cap);
@@ -250,6 +317,15 @@ extern "C" crp_status crp_reset(crp_plan *pl) {
         CRP_CUDA(launch_fill_empty(pl->slots, pl->n_slots, pl->stream));
         pl->launches += 1;
         CRP_CUDA(cudaMemsetAsync(pl->d_full, 0, pl->d.P * sizeof(unsigned int), pl->stream));
+    }
+    if (pl->summary) {
+        CRP_CUDA(cudaMemsetAsync(pl->d_live, 0, pl->d.P * 4, pl->stream));
+        CRP_CUDA(cudaMemsetAsync(pl->d_floor, 0, pl->d.P * 4, pl->stream));
+        if (pl->n_res) {  // reserved keys stay registered; their counts restart at 0
+            CRP_CUDA(launch_reserve_insert(pl->slots, pl->res_off, pl->res_mask, pl->d_res_keys,
+                                           pl->n_res, pl->stream));
+            pl->launches += 1;
+        }
     }
     return CRP_OK;
 }
@@ -307,6 +383,13 @@ static TableView table_view(crp_plan *pl, Slot *slots, const unsigned long long 
     tv.spill_cap = pl->spill_cap;
     tv.dc = pl->dc;
     tv.value_type = pl->d.value_type;
+    tv.summary = pl->summary ? 1 : 0;
+    tv.live = pl->d_live;
+    tv.floor = pl->d_floor;
+    tv.hard_cap = 2u * pl->ell;
+    tv.res_off = pl->res_off;
+    tv.res_mask = pl->res_mask;
+    tv.has_reserved = (pl->summary && pl->n_res > 0) ? 1 : 0;
     return tv;
 }
 
@@ -413,6 +496,70 @@ static crp_status estimate_and_allocate(crp_plan *pl, const crp_sparse *A, const
     // target at most ~60% load per partition
     uint64_t per = (uint64_t)((double)distinct / P / 0.6) + 64;
     return alloc_tables(pl, per);
+}
+
+// Compact every partition holding more than ell keys, then re-insert spilled
+// updates (each re-insert may spill again when a partition refills; repeat).
+static crp_status summary_settle(crp_plan *pl) {
+    const uint32_t P = pl->d.P;
+    for (int round = 0; round < 256; ++round) {
+        CRP_CUDA(launch_summary_compact(pl->slots, pl->d_off, pl->d_mask, pl->d_live, pl->d_floor,
+                                        nullptr, P, pl->ell, pl->d_ctmp, pl->ctmp_grid,
+                                        pl->stream));
+        pl->launches += 1;
+        unsigned long long n_spill = 0;
+        CRP_CUDA(cudaMemcpyAsync(&n_spill, &pl->dc->spill_n, 8, cudaMemcpyDeviceToHost, pl->stream));
+        CRP_CUDA(cudaStreamSynchronize(pl->stream));
+        if (n_spill == 0) return CRP_OK;
+        if (n_spill > pl->spill_cap)
+            return fail(CRP_ETABLE_FULL, "summary spill list overflowed; counts were lost");
+        CRP_CUDA(cudaMemcpyAsync(pl->d_spill2, pl->spill, n_spill * sizeof(SpillRec),
+                                 cudaMemcpyDeviceToDevice, pl->stream));
+        CRP_CUDA(cudaMemsetAsync(&pl->dc->spill_n, 0, 8, pl->stream));
+        TableView tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
+        CRP_CUDA(launch_spill_reinsert(pl->d_spill2, n_spill, pl->hp, tv, pl->stream));
+        pl->launches += 1;
+    }
+    return fail(CRP_ETABLE_FULL, "summary did not settle");
+}
+
+// Summary mode: the outer products are processed in chunks of about P * ell
+// terms (about ell new keys per partition), each followed by compaction.
+static crp_status summary_accumulate(crp_plan *pl, const crp_sparse *A, const crp_sparse *B) {
+    const uint32_t P = pl->d.P;
+    CRP_CUDA(launch_count_terms(A->ptr, B->ptr, A->n_major, pl->d_scratch64, pl->stream));
+    unsigned long long terms = 0;
+    CRP_CUDA(cudaMemcpyAsync(&terms, pl->d_scratch64, 8, cudaMemcpyDeviceToHost, pl->stream));
+    CRP_CUDA(cudaStreamSynchronize(pl->stream));
+    pl->launches += 1;
+    const uint64_t chunk_terms = std::max<uint64_t>((uint64_t)P * pl->ell, 1);
+    const uint64_t n_chunks = std::max<uint64_t>((terms + chunk_terms - 1) / chunk_terms, 1);
+    const int64_t K = A->n_major;
+    const int64_t kstep = (K + (int64_t)n_chunks - 1) / (int64_t)n_chunks;
+    float total_ms = 0.f;
+    for (int64_t k0 = 0; k0 < K; k0 += kstep) {
+        const int64_t k1 = std::min(K, k0 + kstep);
+        crp_sparse As = *A, Bs = *B;
+        As.ptr = A->ptr + k0;
+        As.n_major = k1 - k0;
+        Bs.ptr = B->ptr + k0;
+        Bs.n_major = k1 - k0;
+        AccumulateArgs a = make_args(pl, &As, &Bs, B->idx, B->val, 1);
+        a.direct = 1;
+        a.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
+        CRP_CUDA(cudaMemsetAsync(&pl->dc->work_next, 0, sizeof(unsigned int), pl->stream));
+        CRP_CUDA(cudaEventRecord(pl->ev0, pl->stream));
+        CRP_CUDA(launch_accumulate(a, nullptr, pl->grid_direct, pl->stream));
+        CRP_CUDA(cudaEventRecord(pl->ev1, pl->stream));
+        pl->launches += 1;
+        crp_status st = summary_settle(pl);
+        if (st != CRP_OK) return st;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pl->ev0, pl->ev1) == cudaSuccess) total_ms += ms;
+    }
+    pl->summary_ms = total_ms;
+    pl->timed = false;
+    return CRP_OK;
 }
 
 // Routed mode: enumerate every term once into per-group bins, then apply the
@@ -532,6 +679,7 @@ extern "C" crp_status crp_outer_accumulate(crp_plan *pl, const crp_sparse *A, co
         st = estimate_and_allocate(pl, A, B, b_idx, b_val);
         if (st != CRP_OK) return st;
     }
+    if (pl->summary) return summary_accumulate(pl, A, B);
     if (pl->d.flags & CRP_PLAN_ROUTED) return routed_accumulate(pl, A, B);
     AccumulateArgs a = make_args(pl, A, B, b_idx, b_val, pl->G);
     a.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
@@ -663,7 +811,8 @@ extern "C" crp_status crp_topk(crp_plan *pl, int32_t k, uint32_t flags, int32_t 
     if (!pl->tables_ready) return CRP_OK;
     const int upper = (flags & CRP_TOPK_UPPER) ? 1 : 0;
     cudaStream_t s = pl->stream;
-    CRP_CUDA(launch_topk_hist(pl->slots, pl->n_slots, pl->d.value_type, upper, pl->d_topk_hist, s));
+    const int vt = pl->summary ? kVTSummary : pl->d.value_type;
+    CRP_CUDA(launch_topk_hist(pl->slots, pl->n_slots, vt, upper, pl->d_topk_hist, s));
     pl->launches += 1;
     std::vector<unsigned int> hist(kTopkBuckets);
     CRP_CUDA(cudaMemcpyAsync(hist.data(), pl->d_topk_hist, kTopkBuckets * 4, cudaMemcpyDeviceToHost,
@@ -689,7 +838,7 @@ extern "C" crp_status crp_topk(crp_plan *pl, int32_t k, uint32_t flags, int32_t 
             st = fail(CRP_ECUDA, std::string("topk: ") + cudaGetErrorString(e));
         return st == CRP_OK;
     };
-    cuda_ok(launch_topk_collect(pl->slots, pl->n_slots, pl->d.value_type, upper, (unsigned)b, cand,
+    cuda_ok(launch_topk_collect(pl->slots, pl->n_slots, vt, upper, (unsigned)b, cand,
                                 cnt, (unsigned)n_c, s));
     pl->launches += 1;
     const TopkCand *final_c = cand;
@@ -804,8 +953,8 @@ extern "C" crp_status crp_export_partitions(crp_plan *pl, uint32_t p0, uint32_t 
         dw = (double *)(dj + tot);
         dwl = w_lower ? dw + tot : nullptr;
     }
-    CRP_CUDA(launch_export_range(pl->slots, pl->d_off, pl->d_mask, p0, p1, d_base, pl->d.value_type,
-                                 di, dj, dw, dwl, s));
+    CRP_CUDA(launch_export_range(pl->slots, pl->d_off, pl->d_mask, p0, p1, d_base,
+                                 pl->summary ? kVTSummary : pl->d.value_type, di, dj, dw, dwl, s));
     if (!dev_out) {
         CRP_CUDA(cudaMemcpyAsync(i_out, di, tot * 4, cudaMemcpyDeviceToHost, s));
         CRP_CUDA(cudaMemcpyAsync(j_out, dj, tot * 4, cudaMemcpyDeviceToHost, s));
@@ -866,7 +1015,7 @@ extern "C" crp_status crp_timing(crp_plan *pl, double *accumulate_ms, uint64_t *
     if (!pl) return fail(CRP_EINVAL, "null plan");
     if (launches) *launches = pl->launches;
     if (accumulate_ms) {
-        *accumulate_ms = 0.0;
+        *accumulate_ms = pl->summary ? pl->summary_ms : 0.0;
         if (pl->timed) {
             CRP_CUDA(cudaEventSynchronize(pl->ev1));
             float ms = 0.f;
@@ -874,5 +1023,23 @@ extern "C" crp_status crp_timing(crp_plan *pl, double *accumulate_ms, uint64_t *
             *accumulate_ms = ms;
         }
     }
+    return CRP_OK;
+}
+
+extern "C" crp_status crp_reserve(crp_plan *pl, const uint64_t *keys, int32_t n) {
+    if (!pl || (n > 0 && !keys) || n < 0) return fail(CRP_EINVAL, "bad argument");
+    if (!pl->summary || !pl->d.reserved_counters)
+        return fail(CRP_EINVAL, "the plan has no reserved counters (summary mode only)");
+    if ((int64_t)pl->n_res + n > (int64_t)pl->d.reserved_counters)
+        return fail(CRP_EINVAL, "more keys than reserved_counters");
+    if (n == 0) return CRP_OK;
+    const bool dev = is_device_ptr(keys);
+    CRP_CUDA(cudaMemcpyAsync(pl->d_res_keys + pl->n_res, keys, (size_t)n * 8,
+                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, pl->stream));
+    CRP_CUDA(launch_reserve_insert(pl->slots, pl->res_off, pl->res_mask, pl->d_res_keys + pl->n_res,
+                                   n, pl->stream));
+    pl->launches += 1;
+    pl->n_res += n;
+    CRP_CUDA(cudaStreamSynchronize(pl->stream));
     return CRP_OK;
 }

@@ -32,9 +32,59 @@ __device__ __forceinline__ void spill_update(const TableView &tv, unsigned long 
     }
 }
 
+// Summary-mode update of partition p (Space-Saving semantics, weighted):
+// a recorded key gains v; a new key, while the partition holds fewer than
+// hard_cap keys, is recorded with count floor + v and overestimation floor
+// (the floor bounds the weight of every key not recorded); otherwise the
+// update is spilled and re-inserted after the partition is compacted.
+// Reserved keys (exact counters) are looked up first.
+__device__ __forceinline__ void summary_update(const TableView &tv, uint32_t p,
+                                               unsigned long long key, unsigned long long v) {
+    if (tv.has_reserved) {
+        unsigned long long h = slot_mix(key) & tv.res_mask;
+        for (unsigned long long probe = 0; probe <= tv.res_mask; ++probe) {
+            const Slot *s = tv.slots + tv.res_off + h;
+            const unsigned long long k = s->key;
+            if (k == key) {
+                atomicAdd((unsigned int *)&tv.slots[tv.res_off + h].val, (unsigned int)v);
+                return;
+            }
+            if (k == kEmptyKey) break;
+            h = (h + 1) & tv.res_mask;
+        }
+    }
+    const unsigned long long off = tv.part_off[p];
+    const unsigned long long mask = tv.part_mask[p];
+    unsigned long long h = slot_mix(key) & mask;
+    for (unsigned long long probe = 0; probe <= mask; ++probe) {
+        Slot *s = tv.slots + off + h;
+        unsigned long long k = s->key;
+        if (k == kEmptyKey) {
+            if (*(volatile unsigned int *)&tv.live[p] >= tv.hard_cap) break;
+            k = atomicCAS(&s->key, kEmptyKey, key);
+            if (k == kEmptyKey) {
+                atomicAdd(&tv.live[p], 1u);
+                const unsigned long long fl = tv.floor[p];
+                atomicAdd(&s->val, (fl << 32) | (fl + v));
+                return;
+            }
+        }
+        if (k == key) {
+            atomicAdd((unsigned int *)&s->val, (unsigned int)v);
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+    spill_update(tv, key, v);
+}
+
 // Add v (u32 count, or the bits of a double) to entry `key` of partition p.
 __device__ __forceinline__ void table_update(const TableView &tv, uint32_t p,
                                              unsigned long long key, unsigned long long v) {
+    if (tv.summary) {
+        summary_update(tv, p, key, v);
+        return;
+    }
     // Plain (cacheable) loads are enough here: a partition marked full stays
     // full, and a key, once written, never changes, so a stale "not full" or a
     // stale empty key only costs a probe or a failed CAS, never a wrong count.

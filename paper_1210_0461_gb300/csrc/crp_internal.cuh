@@ -21,6 +21,9 @@ constexpr uint32_t kStatusSpillFull = 2u;
 constexpr uint32_t kStatusBadIndex = 4u;
 constexpr uint32_t kStatusTimeout = 8u;
 constexpr uint32_t kStatusSmemProbe = 16u;
+// Value-type code of summary slots inside the top-k / export kernels:
+// low 32 bits = count (upper bound), high 32 bits = overestimation.
+constexpr int kVTSummary = 2;
 
 // One side hash, branch-free for P = 1: (v >> (64 - max(lg,1))) & (P - 1).
 struct SideHash {
@@ -90,6 +93,14 @@ struct TableView {
     unsigned long long spill_cap;
     DevCounters *dc;
     int value_type;
+    // summary mode (Space-Saving semantics per partition)
+    int summary;                          // 1: tables are counter summaries
+    unsigned int *live;                   // occupied slots per partition
+    const unsigned int *floor;            // current floor (min count) per partition
+    unsigned int hard_cap;                // max live slots before new keys spill
+    // reserved exact counters probed before the summaries (0 slots = none)
+    unsigned long long res_off, res_mask; // region [res_off, res_off + res_mask + 1)
+    int has_reserved;
 };
 
 struct AccumulateArgs {
@@ -128,6 +139,15 @@ cudaError_t launch_route(const RouteArgs &RA, int grid, cudaStream_t s);
 cudaError_t launch_apply(const RouteArgs &RA, unsigned int *chunk_prefix, uint32_t CH, int grid,
                          cudaStream_t s);
 size_t route_smem_bytes(int value_type, uint32_t B, uint32_t R_s);
+
+// Summary mode (crp_summary.cu)
+cudaError_t launch_summary_compact(Slot *slots, const unsigned long long *part_off,
+                                   const unsigned long long *part_mask, unsigned int *live,
+                                   unsigned int *floor, const unsigned int *todo, uint32_t n_todo,
+                                   uint32_t ell, Slot *tmp, int grid, cudaStream_t s);
+cudaError_t launch_reserve_insert(Slot *slots, unsigned long long res_off,
+                                  unsigned long long res_mask, const unsigned long long *keys,
+                                  int32_t n, cudaStream_t s);
 
 // Record the calling thread's error message (read by crp_last_error).
 void set_last_error(const std::string &msg);

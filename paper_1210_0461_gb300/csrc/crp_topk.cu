@@ -19,13 +19,21 @@ namespace crp {
 // non-negative doubles).
 __device__ __forceinline__ unsigned long long weight_key(const Slot &s, int value_type,
                                                          double &w) {
-    if (value_type == CRP_I32) {
+    if (value_type != CRP_F32_COMP) {  // int counts, or summary upper bounds
         unsigned int c = (unsigned int)s.val;
         w = (double)c;
         return c;
     }
     w = __longlong_as_double((long long)s.val);
     return (unsigned long long)__double_as_longlong(fabs(w));
+}
+
+// Lower bound of an entry: the weight itself for exact tables, count minus
+// overestimation for summary slots (value type kVTSummary).
+__device__ __forceinline__ double weight_lower(const Slot &s, int value_type, double w) {
+    if (value_type == kVTSummary)
+        return (double)((unsigned int)s.val - (unsigned int)(s.val >> 32));
+    return w;
 }
 
 // 65 exponents x 64 sub-buckets, but capped to kTopkBuckets.
@@ -89,7 +97,7 @@ __global__ void k_topk_collect(const Slot *__restrict__ slots, uint64_t n, int v
             c.wkey = u;
             c.ij = s.key;
             c.w = w;
-            c.wl = w;
+            c.wl = weight_lower(s, value_type, w);
             out[at] = c;
         }
     }
@@ -240,7 +248,7 @@ __global__ void k_export(const Slot *__restrict__ slots, const unsigned long lon
             i_out[b + at] = (int32_t)(s.key >> 32);
             j_out[b + at] = (int32_t)(uint32_t)s.key;
             w_out[b + at] = w;
-            if (wl_out) wl_out[b + at] = w;
+            if (wl_out) wl_out[b + at] = weight_lower(s, value_type, w);
         }
         __syncthreads();
     }
