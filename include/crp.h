@@ -256,6 +256,41 @@ crp_status crp_outer_product_noalloc(const crp_plan_desc *desc, const crp_sparse
                                      double *w_out, int64_t capacity, int64_t *n_out,
                                      void *stream);
 
+/* Batched products (many independent problems, one persistent launch).
+ * Problem q computes A[q] B[q] (A[q] CSC, B[q] CSR, {0,1} values, device
+ * pointers; A and B are HOST arrays of nprob descriptors) into its own P
+ * partition tables; desc supplies P (<= 4096), seeds, mode and tile_vectors
+ * (CRP_I32 only).  crp_batch_create counts each problem's terms, sizes its
+ * tables from a sampling launch (terms of partitions [0, P/16) accumulated
+ * exactly, distinct count scaled up; Section 4 "Parameters"), and captures
+ * table reset + the persistent kernel into one CUDA graph on a private
+ * stream.  All problems' work items (problem, tile of outer products) form a
+ * single queue drained by that kernel.
+ * wait_timeout_ns > 0 enables per-problem ready flags (crp_batch_set_ready;
+ * all start ready): a CTA that meets a problem whose flag is cleared waits at
+ * most wait_timeout_ns, then skips it and crp_batch_sync returns
+ * CRP_ETIMEOUT.  stream: where runs are launched (a cudaStream_t). */
+typedef struct crp_batch crp_batch;
+crp_status crp_batch_create(crp_batch **out, const crp_plan_desc *desc, int32_t nprob,
+                            const crp_sparse *A, const crp_sparse *B, uint64_t wait_timeout_ns,
+                            void *stream);
+/* Launch the captured graph (reset every table, accumulate every problem). */
+crp_status crp_batch_run(crp_batch *batch);
+/* Wait; *ms (nullable) = device time of the last run, *terms (nullable) =
+ * terms it enumerated.  Returns the recorded status (CRP_ETIMEOUT,
+ * CRP_ETABLE_FULL). */
+crp_status crp_batch_sync(crp_batch *batch, double *ms, uint64_t *terms);
+/* Mark problem q's inputs ready (1) or withheld (0); synchronous copy. */
+crp_status crp_batch_set_ready(crp_batch *batch, int32_t q, int32_t ready);
+/* Entries of problem q (host or device outputs, `capacity` each; grouped by
+ * partition); *n_out = entries, also when > capacity (then CRP_EINVAL). */
+crp_status crp_batch_export(crp_batch *batch, int32_t q, int32_t *i_out, int32_t *j_out,
+                            double *w_out, int64_t capacity, int64_t *n_out);
+/* Total terms over all problems, allocated table slots, kernels launched. */
+crp_status crp_batch_info(const crp_batch *batch, uint64_t *total_terms, uint64_t *table_slots,
+                          uint64_t *launches);
+void crp_batch_destroy(crp_batch *batch);
+
 /* Library version string. */
 const char *crp_version(void);
 

@@ -86,6 +86,18 @@ _SIGS = {
                                                  ctypes.POINTER(crp_sparse), _P, _P, _P,
                                                  ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                                  _P]),
+    "crp_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(crp_plan_desc),
+                                        ctypes.c_int32, _P, _P, ctypes.c_uint64, _P]),
+    "crp_batch_run": (ctypes.c_int, [_P]),
+    "crp_batch_sync": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_uint64)]),
+    "crp_batch_set_ready": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "crp_batch_export": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_int64)]),
+    "crp_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64),
+                                      ctypes.POINTER(ctypes.c_uint64),
+                                      ctypes.POINTER(ctypes.c_uint64)]),
+    "crp_batch_destroy": (None, [_P]),
     "crp_version": (ctypes.c_char_p, []),
     "crp_last_error": (ctypes.c_char_p, []),
 }
@@ -308,3 +320,72 @@ def probe_update_rate(region_bytes: int, n_updates: int, mode: int) -> float:
     _check(lib().crp_probe_update_rate(region_bytes, n_updates, mode, ctypes.byref(ms)),
            "crp_probe_update_rate")
     return n_updates / (ms.value / 1e3)
+
+
+class Batch:
+    """Many independent co-occurrence products in one persistent, graph-captured
+    launch (crp_batch_* in include/crp.h).  ``problems``: list of
+    (A, B) DeviceSparse pairs."""
+
+    def __init__(self, problems, P: int, seed_a: int, seed_b: int, mode: int = CRP_FULL,
+                 tile_vectors: int = 0, wait_timeout_ns: int = 0, stream=None):
+        self._lib = lib()
+        d = crp_plan_desc()
+        d.n_rows = d.n_cols = 1
+        d.P, d.seed_a, d.seed_b = P, seed_a & (2**64 - 1), seed_b & (2**64 - 1)
+        d.value_type, d.mode, d.tile_vectors = CRP_I32, mode, tile_vectors
+        n = len(problems)
+        self._keep = problems
+        A = (crp_sparse * n)(*[a.c_struct() for a, _ in problems])
+        B = (crp_sparse * n)(*[b.c_struct() for _, b in problems])
+        h = _P()
+        _check(self._lib.crp_batch_create(ctypes.byref(h), ctypes.byref(d), n,
+                                          ctypes.cast(A, _P), ctypes.cast(B, _P), wait_timeout_ns,
+                                          _stream_handle(stream)), "crp_batch_create")
+        self._h = h
+        self.n = n
+
+    def run(self):
+        _check(self._lib.crp_batch_run(self._h), "crp_batch_run")
+
+    def sync(self):
+        ms = ctypes.c_double(0)
+        t = ctypes.c_uint64(0)
+        _check(self._lib.crp_batch_sync(self._h, ctypes.byref(ms), ctypes.byref(t)),
+               "crp_batch_sync")
+        return ms.value, t.value
+
+    def set_ready(self, q: int, ready: bool):
+        _check(self._lib.crp_batch_set_ready(self._h, q, 1 if ready else 0), "crp_batch_set_ready")
+
+    def export(self, q: int):
+        n = ctypes.c_int64(0)
+        st = self._lib.crp_batch_export(self._h, q, None, None, None, 0, ctypes.byref(n))
+        if st not in (CRP_OK, CRP_EINVAL):
+            _check(st, "crp_batch_export")
+        cap = n.value
+        i = np.zeros(cap, np.int32)
+        j = np.zeros(cap, np.int32)
+        w = np.zeros(cap, np.float64)
+        if cap:
+            _check(self._lib.crp_batch_export(self._h, q, i.ctypes.data, j.ctypes.data,
+                                              w.ctypes.data, cap, ctypes.byref(n)),
+                   "crp_batch_export")
+        return i, j, w
+
+    def info(self):
+        t, s, l = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+        _check(self._lib.crp_batch_info(self._h, ctypes.byref(t), ctypes.byref(s),
+                                        ctypes.byref(l)), "crp_batch_info")
+        return {"total_terms": t.value, "table_slots": s.value, "launches": l.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.crp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

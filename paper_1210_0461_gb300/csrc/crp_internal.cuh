@@ -76,6 +76,7 @@ struct DevCounters {
     unsigned long long bad_index;    // first bad index seen (debug checks)
     unsigned int long_n;             // long vectors deferred by the sorter
     unsigned int pad;
+    unsigned long long work64;       // 64-bit work-item counter (batched launch)
 };
 
 struct SpillRec {
