@@ -291,6 +291,40 @@ crp_status crp_batch_info(const crp_batch *batch, uint64_t *total_terms, uint64_
                           uint64_t *launches);
 void crp_batch_destroy(crp_batch *batch);
 
+/* Heavy-pair predictor (not in the paper): a 2 -> 64 -> 64 -> 1 ReLU network
+ * y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 whose two hidden products run on
+ * the tcgen05 tensor cores (bf16 operands, fp32 accumulation in TMEM).
+ * params: device fp32 array of crp_mlp_param_count() = 4417 values laid out as
+ * W1[64][2], b1[64], W2[64][64], b2[64], w3[64], b3.  All pointers device;
+ * every call synchronises `stream` (a cudaStream_t) and returns CRP_ETIMEOUT
+ * if a bounded wait for tensor-core completion gave up. */
+int32_t crp_mlp_param_count(void);
+/* y[m] = network(x[2m], x[2m+1]) for m < n. */
+crp_status crp_mlp_forward(const float *params, const float *x, float *y, int64_t n,
+                           void *stream);
+/* Mean squared error over n rows, L = sum_m (y_m - t_m)^2 / n_total, into
+ * *loss, and dL/dparams into grad (4417 floats, overwritten).  The backward
+ * products use bf16 operands (dZ2, dZ1, the saved activations). */
+crp_status crp_mlp_grad(const float *params, const float *x, const float *t, int64_t n,
+                        int64_t n_total, float *grad, float *loss, void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step >= 1) on params with
+ * moment buffers m, v (4417 floats each).  Asynchronous. */
+crp_status crp_mlp_adam(float *params, float *m, float *v, const float *grad, float lr,
+                        int32_t step, void *stream);
+/* Candidate heavy pairs from a prefix of the stream: item counts c over the
+ * prefix transactions (CSR, device), the R items of largest count, and every
+ * pair i < j of them with features x = (log(1+c_i), log(1+c_j)) / log(1+max c).
+ * Outputs (device, capacity >= R(R-1)/2): i_out, j_out, x_out (2 per pair). */
+crp_status crp_candidate_pairs(const crp_sparse *prefix, int32_t n_items, int32_t R,
+                               int32_t *i_out, int32_t *j_out, float *x_out, int64_t capacity,
+                               int64_t *n_out, void *stream);
+/* Score the candidate pairs with the network (params, device) or, when params
+ * is NULL, with the product-of-marginals heuristic log(1+c_i) + log(1+c_j),
+ * and crp_reserve the n_reserve best (both orders when full_mode != 0). */
+crp_status crp_predict_reserve(crp_plan *plan, const crp_sparse *prefix, int32_t n_items,
+                               const float *params, int32_t R, int32_t n_reserve,
+                               int32_t full_mode, void *stream);
+
 /* Library version string. */
 const char *crp_version(void);
 

@@ -383,3 +383,106 @@ def partition_streams(A: Compressed, B: Compressed, P: int, seed_a: int, seed_b:
         m = p == q
         out.append(list(zip((i[m] * n_cols + j[m]).tolist(), w[m].tolist())))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Heavy-pair predictor (a 2 -> 64 -> 64 -> 1 MLP; not in the paper)
+# ---------------------------------------------------------------------------
+# Parameter vector layout (fp32 master weights), shared with the CUDA kernels
+# only through this documented layout: W1[64][2], b1[64], W2[64][64], b2[64],
+# w3[64], b3[1].
+MLP_H = 64
+MLP_SIZES = (("W1", (64, 2)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("w3", (64,)),
+             ("b3", (1,)))
+MLP_NPARAM = sum(int(np.prod(s)) for _, s in MLP_SIZES)
+
+
+def mlp_unpack(theta):
+    out, o = {}, 0
+    for name, shape in MLP_SIZES:
+        n = int(np.prod(shape))
+        out[name] = np.asarray(theta[o:o + n], dtype=np.float64).reshape(shape)
+        o += n
+    return out
+
+
+def mlp_pack(d) -> np.ndarray:
+    return np.concatenate([np.asarray(d[name], np.float64).ravel() for name, _ in MLP_SIZES])
+
+
+def bf16_round(x) -> np.ndarray:
+    """Round to the nearest bfloat16 (ties to even), via float32."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def mlp_forward(theta, X, rounding: bool = True):
+    """y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 per row of X (M x 2).
+    With ``rounding`` the operands of the two matrix products (x, W1, the
+    first hidden layer, W2) are bf16, as the tensor-core kernels use them;
+    everything else is fp64."""
+    p = mlp_unpack(theta)
+    rd = bf16_round if rounding else (lambda a: np.asarray(a, np.float64))
+    Xb = rd(X)
+    W1b = rd(p["W1"])
+    Z1 = Xb @ W1b.T + p["b1"]
+    H1 = np.maximum(Z1, 0.0)
+    H1b = rd(H1)
+    W2b = rd(p["W2"])
+    Z2 = H1b @ W2b.T + p["b2"]
+    H2 = np.maximum(Z2, 0.0)
+    y = H2 @ p["w3"] + p["b3"][0]
+    return y, dict(Xb=Xb, W1b=W1b, Z1=Z1, H1b=H1b, W2b=W2b, Z2=Z2, H2=H2, p=p)
+
+
+def mlp_loss_grad(theta, X, t, rounding: bool = True, n_total: int | None = None):
+    """Mean squared error L = sum((y - t)^2) / n_total and its gradient with
+    respect to the master parameters (straight through the bf16 copies).  With
+    ``rounding`` the backward products use bf16 operands (dZ2, dZ1, the
+    saved activations) like the kernels do."""
+    y, c = mlp_forward(theta, X, rounding)
+    rd = bf16_round if rounding else (lambda a: np.asarray(a, np.float64))
+    n = len(y) if n_total is None else n_total
+    r = y - t
+    L = float(np.dot(r, r) / n)
+    dy = 2.0 * r / n
+    p = c["p"]
+    dw3 = c["H2"].T @ dy
+    db3 = np.array([dy.sum()])
+    dZ2 = np.outer(dy, p["w3"]) * (c["Z2"] > 0)
+    db2 = dZ2.sum(axis=0)
+    dZ2b = rd(dZ2)
+    dW2 = dZ2b.T @ c["H1b"]
+    dH1 = dZ2b @ c["W2b"]
+    dZ1 = dH1 * (c["Z1"] > 0)
+    db1 = dZ1.sum(axis=0)
+    dZ1b = rd(dZ1)
+    dW1 = dZ1b.T @ c["Xb"]
+    g = mlp_pack(dict(W1=dW1, b1=db1, W2=dW2, b2=db2, w3=dw3, b3=db3))
+    return L, g, y
+
+
+def mlp_init(seed: int) -> np.ndarray:
+    """He-style initial parameters (fp32 values)."""
+    rng = np.random.default_rng(seed)
+    d = dict(W1=rng.normal(0, np.sqrt(2 / 2), (64, 2)), b1=np.full(64, 0.01),
+             W2=rng.normal(0, np.sqrt(2 / 64), (64, 64)), b2=np.full(64, 0.01),
+             w3=rng.normal(0, np.sqrt(1 / 64), 64), b3=np.zeros(1))
+    return mlp_pack(d).astype(np.float32).astype(np.float64)
+
+
+def adam_step(theta, m, v, g, lr, step, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015) of fp32 master parameters."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** step)
+    vh = v / (1 - b2 ** step)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def marginal_features(counts_i, counts_j, scale):
+    """Predictor inputs of a pair: log(1 + c_i) / scale, log(1 + c_j) / scale,
+    the items' counts in a prefix of the stream."""
+    return np.stack([np.log1p(counts_i) / scale, np.log1p(counts_j) / scale], axis=1)

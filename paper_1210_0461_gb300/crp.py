@@ -98,6 +98,15 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_uint64),
                                       ctypes.POINTER(ctypes.c_uint64)]),
     "crp_batch_destroy": (None, [_P]),
+    "crp_mlp_param_count": (ctypes.c_int32, []),
+    "crp_mlp_forward": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P]),
+    "crp_mlp_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P]),
+    "crp_mlp_adam": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_float, ctypes.c_int32, _P]),
+    "crp_candidate_pairs": (ctypes.c_int, [ctypes.POINTER(crp_sparse), ctypes.c_int32,
+                                           ctypes.c_int32, _P, _P, _P, ctypes.c_int64,
+                                           ctypes.POINTER(ctypes.c_int64), _P]),
+    "crp_predict_reserve": (ctypes.c_int, [_P, ctypes.POINTER(crp_sparse), ctypes.c_int32, _P,
+                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]),
     "crp_version": (ctypes.c_char_p, []),
     "crp_last_error": (ctypes.c_char_p, []),
 }
@@ -389,3 +398,78 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Heavy-pair predictor (tcgen05 MLP)
+# ---------------------------------------------------------------------------
+
+def mlp_param_count() -> int:
+    return int(lib().crp_mlp_param_count())
+
+
+def mlp_forward(params, x):
+    """y for the rows of x (torch tensors on the device: params fp32 [4417],
+    x fp32 [n, 2])."""
+    import torch
+    y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+    _check(lib().crp_mlp_forward(params.data_ptr(), x.data_ptr(), y.data_ptr(), x.shape[0],
+                                 _stream_handle(None)), "crp_mlp_forward")
+    return y
+
+
+def mlp_grad(params, x, t, n_total=None):
+    """(loss, grad) of sum (y - t)^2 / n_total (device tensors)."""
+    import torch
+    g = torch.empty(mlp_param_count(), dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    n = x.shape[0]
+    _check(lib().crp_mlp_grad(params.data_ptr(), x.data_ptr(), t.data_ptr(), n,
+                              n if n_total is None else n_total, g.data_ptr(), loss.data_ptr(),
+                              _stream_handle(None)), "crp_mlp_grad")
+    return float(loss.item()), g
+
+
+class MLPTrainer:
+    """Adam on the fp32 master parameters with the tensor-core gradient kernel."""
+
+    def __init__(self, params, lr=1e-2):
+        import torch
+        self.params = params
+        self.m = torch.zeros_like(params)
+        self.v = torch.zeros_like(params)
+        self.lr = lr
+        self.step_n = 0
+
+    def step(self, x, t):
+        loss, g = mlp_grad(self.params, x, t)
+        self.step_n += 1
+        _check(lib().crp_mlp_adam(self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(),
+                                  g.data_ptr(), self.lr, self.step_n, _stream_handle(None)),
+               "crp_mlp_adam")
+        return loss
+
+
+def candidate_pairs(prefix: DeviceSparse, n_items: int, R: int):
+    """(i, j, x) device tensors of the candidate pairs of a stream prefix."""
+    import torch
+    nc = R * (R - 1) // 2
+    dev = prefix.idx.device
+    i = torch.empty(nc, dtype=torch.int32, device=dev)
+    j = torch.empty(nc, dtype=torch.int32, device=dev)
+    x = torch.empty((nc, 2), dtype=torch.float32, device=dev)
+    n = ctypes.c_int64(0)
+    s = prefix.c_struct()
+    _check(lib().crp_candidate_pairs(ctypes.byref(s), n_items, R, i.data_ptr(), j.data_ptr(),
+                                     x.data_ptr(), nc, ctypes.byref(n), _stream_handle(None)),
+           "crp_candidate_pairs")
+    return i, j, x
+
+
+def predict_reserve(plan: "Plan", prefix: DeviceSparse, n_items: int, params, R: int,
+                    n_reserve: int, full_mode: bool = False):
+    s = prefix.c_struct()
+    _check(lib().crp_predict_reserve(plan._h, ctypes.byref(s), n_items,
+                                     params.data_ptr() if params is not None else None, R,
+                                     n_reserve, 1 if full_mode else 0, _stream_handle(None)),
+           "crp_predict_reserve")
