@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-match", action="store_true")
     ap.add_argument("--mode", choices=["direct", "smem", "routed"], default="direct",
                     help="accumulation variant (CRP_PLAN_DIRECT / on-chip table / CRP_PLAN_ROUTED)")
+    ap.add_argument("--autotune", type=int, default=2_500_000,
+                    help="outer products of the workload the autotuner samples (0 = off: use "
+                         "--P/--mode/--tile/--smem-slots)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -230,9 +233,18 @@ def main():
     flags = crp.CRP_PLAN_NO_WARP_MATCH if args.no_match else 0
     flags |= {"direct": crp.CRP_PLAN_DIRECT, "smem": 0, "routed": crp.CRP_PLAN_ROUTED}[args.mode]
 
-    # Partition-interval sharding (the paper's K processors with disjoint
-    # intervals): with N ranks each rank owns G/N partition groups and reads
-    # the whole input; there is no exchange during accumulation.
+    tuned = None
+    if args.autotune:
+        t0 = time.time()
+        kw, tps = crp.autotune(dT, dT, T.n_minor, T.n_minor, ci.SEED_A, ci.SEED_B,
+                               sample_vectors=min(args.autotune, T.n_major), stream=stream)
+        tuned = {"choice": kw, "sample_terms_per_s": tps, "sample_vectors": args.autotune,
+                 "seconds": round(time.time() - t0, 1)}
+        args.P, args.groups, args.tile, args.smem_slots = (kw["P"], kw["groups"],
+                                                           kw["tile_vectors"], kw["smem_slots"])
+        flags = kw["flags"] | (crp.CRP_PLAN_NO_WARP_MATCH if args.no_match else 0)
+        args.mode = ("routed" if flags & crp.CRP_PLAN_ROUTED else
+                     "direct" if flags & crp.CRP_PLAN_DIRECT else "smem")
     plan = crp.Plan(T.n_minor, T.n_minor, args.P, ci.SEED_A, ci.SEED_B, groups=args.groups,
                     tile_vectors=args.tile, smem_slots=args.smem_slots, flags=flags,
                     stream=stream)
@@ -332,7 +344,7 @@ def main():
                                    "exact int32 T^T T (all entries), top-1000 pairs",
                        "P": args.P, "groups": args.groups, "tile_vectors": args.tile,
                        "smem_slots": args.smem_slots, "warp_match": not args.no_match,
-                       "mode": args.mode,
+                       "mode": args.mode, "autotune": tuned,
                        "terms_per_step": terms_step, "entries": entries,
                        "nnz": int(T.nnz), "l2": "inputs (0.8 GB) and tables "
                        f"({st['table_slots'] * 16 / 1e9:.1f} GB) exceed L2; no flush",

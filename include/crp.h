@@ -325,6 +325,20 @@ crp_status crp_predict_reserve(crp_plan *plan, const crp_sparse *prefix, int32_t
                                const float *params, int32_t R, int32_t n_reserve,
                                int32_t full_mode, void *stream);
 
+/* Launch-configuration autotuner.  Times candidate configurations of the exact
+ * product -- P in {256, 1024, 4096}; the on-chip combining table (8192 or
+ * 16384 slots), direct HBM updates (tiles of 32/64/256 outer products) or the
+ * routed two-phase variant -- on the first sample_vectors outer products of
+ * A and B (<= 0: all), with tables sized by the library's estimate, and
+ * writes into *best a copy of *base with P, groups, tile_vectors, smem_slots
+ * and the variant flags of the fastest (*best_terms_per_s, nullable, its
+ * rate).  cache_path (nullable): a text file of previous results keyed by
+ * device name and input shape class; a hit returns without timing, a miss
+ * appends the new result.  Creates and destroys plans; synchronises. */
+crp_status crp_autotune(const crp_plan_desc *base, const crp_sparse *A, const crp_sparse *B,
+                        int64_t sample_vectors, const char *cache_path, crp_plan_desc *best,
+                        double *best_terms_per_s, void *stream);
+
 /* Library version string. */
 const char *crp_version(void);
 

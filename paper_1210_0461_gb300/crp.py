@@ -107,6 +107,10 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_int64), _P]),
     "crp_predict_reserve": (ctypes.c_int, [_P, ctypes.POINTER(crp_sparse), ctypes.c_int32, _P,
                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]),
+    "crp_autotune": (ctypes.c_int, [ctypes.POINTER(crp_plan_desc), ctypes.POINTER(crp_sparse),
+                                    ctypes.POINTER(crp_sparse), ctypes.c_int64, ctypes.c_char_p,
+                                    ctypes.POINTER(crp_plan_desc),
+                                    ctypes.POINTER(ctypes.c_double), _P]),
     "crp_version": (ctypes.c_char_p, []),
     "crp_last_error": (ctypes.c_char_p, []),
 }
@@ -473,3 +477,23 @@ def predict_reserve(plan: "Plan", prefix: DeviceSparse, n_items: int, params, R:
                                      params.data_ptr() if params is not None else None, R,
                                      n_reserve, 1 if full_mode else 0, _stream_handle(None)),
            "crp_predict_reserve")
+
+
+def autotune(A: DeviceSparse, B: DeviceSparse, n_rows: int, n_cols: int, seed_a: int, seed_b: int,
+             value_type: int = CRP_I32, mode: int = CRP_FULL, sample_vectors: int = 0,
+             cache_path: str | None = None, stream=None):
+    """Fastest launch configuration for this input (see crp_autotune):
+    returns (dict of Plan keyword arguments, terms/s measured)."""
+    d = crp_plan_desc()
+    d.n_rows, d.n_cols, d.P = n_rows, n_cols, 1024
+    d.seed_a, d.seed_b = seed_a & (2**64 - 1), seed_b & (2**64 - 1)
+    d.value_type, d.mode = value_type, mode
+    best = crp_plan_desc()
+    tps = ctypes.c_double(0)
+    a, b = A.c_struct(), B.c_struct()
+    _check(lib().crp_autotune(ctypes.byref(d), ctypes.byref(a), ctypes.byref(b), sample_vectors,
+                              cache_path.encode() if cache_path else None, ctypes.byref(best),
+                              ctypes.byref(tps), _stream_handle(stream)), "crp_autotune")
+    kw = dict(P=best.P, groups=best.groups, tile_vectors=best.tile_vectors,
+              smem_slots=best.smem_slots, flags=best.flags)
+    return kw, tps.value

@@ -1,0 +1,160 @@
+// Launch-configuration autotuner.  It times candidate configurations of the
+// exact product (partition count P, variant: on-chip combining table / direct
+// HBM updates / routed two-phase, tile of outer products per work item) on a
+// prefix of the caller's outer products, and keeps the fastest.  Results are
+// cached in a text file keyed by device name and a shape class of the input
+// (log2 buckets of K, n_rows, n_cols and of the mean terms per outer
+// product, plus value type and mode), one "key value..." line per entry.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "crp_internal.cuh"
+
+using namespace crp;
+
+static int ilog2u(uint64_t x) {
+    int l = 0;
+    while (x > 1) { x >>= 1; ++l; }
+    return l;
+}
+
+static std::string shape_key(const crp_plan_desc &d, int64_t K, double mean_terms) {
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    std::string name = prop.name;
+    for (auto &c : name) if (c == ' ') c = '_';
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s:K%d:R%d:C%d:T%d:v%d:m%d", name.c_str(), ilog2u((uint64_t)K),
+             ilog2u((uint64_t)d.n_rows), ilog2u((uint64_t)d.n_cols),
+             ilog2u((uint64_t)(mean_terms + 1)), d.value_type, d.mode);
+    return buf;
+}
+
+static bool cache_lookup(const char *path, const std::string &key, crp_plan_desc *out,
+                         double *tps) {
+    if (!path) return false;
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (fgets(line, sizeof line, f)) {
+        char k[256];
+        unsigned P, groups, tile, slots, flags;
+        double v;
+        if (sscanf(line, "%255s %u %u %u %u %u %lf", k, &P, &groups, &tile, &slots, &flags, &v) == 7 &&
+            key == k) {
+            out->P = P;
+            out->groups = groups;
+            out->tile_vectors = tile;
+            out->smem_slots = slots;
+            out->flags = flags;
+            if (tps) *tps = v;
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+static void cache_store(const char *path, const std::string &key, const crp_plan_desc &d,
+                        double tps) {
+    if (!path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %u %u %u %u %u %.6g\n", key.c_str(), d.P, d.groups, d.tile_vectors,
+            d.smem_slots, d.flags, tps);
+    fclose(f);
+}
+
+extern "C" crp_status crp_autotune(const crp_plan_desc *base, const crp_sparse *A,
+                                   const crp_sparse *B, int64_t sample_vectors,
+                                   const char *cache_path, crp_plan_desc *best,
+                                   double *best_terms_per_s, void *stream) {
+    if (!base || !A || !B || !best || A->n_major != B->n_major) {
+        set_last_error("crp_autotune: bad argument");
+        return CRP_EINVAL;
+    }
+    *best = *base;
+    const int64_t K = A->n_major;
+    const int64_t Ks = sample_vectors > 0 && sample_vectors < K ? sample_vectors : K;
+    crp_sparse As = *A, Bs = *B;
+    As.n_major = Bs.n_major = Ks;
+    // terms of the sample (for the shape class and the rate)
+    int64_t ptr_a[2], ptr_b[2];
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *d_terms = nullptr;
+    if (cudaMalloc(&d_terms, 8) != cudaSuccess) return CRP_ENOMEM;
+    launch_count_terms(A->ptr, B->ptr, Ks, d_terms, s);
+    unsigned long long terms = 0;
+    cudaMemcpyAsync(&terms, d_terms, 8, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(ptr_a, A->ptr + Ks, 8, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(ptr_b, B->ptr + Ks, 8, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(d_terms);
+    if (e != cudaSuccess) {
+        set_last_error(std::string("crp_autotune: ") + cudaGetErrorString(e));
+        return CRP_ECUDA;
+    }
+    As.nnz = ptr_a[0];
+    Bs.nnz = ptr_b[0];
+    const std::string key = shape_key(*base, K, Ks ? (double)terms / (double)Ks : 0.0);
+    if (cache_lookup(cache_path, key, best, best_terms_per_s)) return CRP_OK;
+
+    struct Cand { uint32_t P, groups, tile, slots, flags; };
+    std::vector<Cand> cands;
+    const uint32_t Ps[] = {256, 1024, 4096};
+    const uint32_t tiles[] = {32, 64, 256};
+    for (uint32_t P : Ps) {
+        for (uint32_t t : tiles) cands.push_back({P, 1, t, 8192, CRP_PLAN_DIRECT});
+        cands.push_back({P, 1, 64, 8192, 0u});
+        cands.push_back({P, 1, 64, 16384, 0u});
+        cands.push_back({P, 0, 64, 8192, CRP_PLAN_ROUTED});
+    }
+    double best_tps = -1.0;
+    for (const Cand &c : cands) {
+        if (c.P > (uint32_t)std::max(base->n_rows, 1) * 64u && c.P > 256) continue;
+        crp_plan_desc d = *base;
+        d.P = c.P;
+        d.groups = c.groups;
+        d.tile_vectors = c.tile;
+        d.smem_slots = c.slots;
+        d.flags = (base->flags & ~(CRP_PLAN_DIRECT | CRP_PLAN_ROUTED)) | c.flags;
+        d.table_capacity_hint = 0;
+        d.auto_grow = 1;
+        crp_plan *pl = nullptr;
+        if (crp_plan_create(&pl, &d, stream) != CRP_OK) continue;
+        double ms_best = 1e30;
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; ++rep) {
+            ok = crp_reset(pl) == CRP_OK && crp_outer_accumulate(pl, &As, &Bs) == CRP_OK &&
+                 crp_sync(pl) == CRP_OK;
+            double ms = 0;
+            if (ok && rep > 0 && crp_timing(pl, &ms, nullptr) == CRP_OK && ms > 0)
+                ms_best = std::min(ms_best, ms);
+        }
+        crp_plan_destroy(pl);
+        if (!ok || ms_best >= 1e29) continue;
+        const double tps = (double)terms / (ms_best * 1e-3);
+        if (tps > best_tps) {
+            best_tps = tps;
+            *best = d;
+            best->table_capacity_hint = base->table_capacity_hint;
+            best->auto_grow = base->auto_grow;
+        }
+    }
+    if (best_tps < 0) {
+        set_last_error("crp_autotune: no candidate configuration ran");
+        return CRP_ECUDA;
+    }
+    if (best_terms_per_s) *best_terms_per_s = best_tps;
+    cache_store(cache_path, key, *best, best_tps);
+    return CRP_OK;
+}
