@@ -117,7 +117,14 @@ typedef struct {
     uint32_t smem_slots;          /* on-chip combining table slots per CTA
                                      (power of two); 0 = default */
     uint32_t flags;               /* CRP_PLAN_* */
-    uint32_t _pad1;
+    uint32_t hot_items;           /* CRP_PLAN_DIRECT or CRP_PLAN_ROUTED with
+                                     CRP_I32 only: R > 0
+                                     keeps exact dense counters (R x R, in L2)
+                                     for the pairs of the R most frequent rows
+                                     and columns, chosen per call from the
+                                     first 1/64 of the outer products; their
+                                     counts are added to the partition tables
+                                     at the end of the call.  R <= 4096. */
 } crp_plan_desc;
 
 typedef struct crp_plan crp_plan;
@@ -328,7 +335,8 @@ crp_status crp_predict_reserve(crp_plan *plan, const crp_sparse *prefix, int32_t
 /* Launch-configuration autotuner.  Times candidate configurations of the exact
  * product -- P in {256, 1024, 4096}; the on-chip combining table (8192 or
  * 16384 slots), direct HBM updates (tiles of 32/64/256 outer products) or the
- * routed two-phase variant -- on the first sample_vectors outer products of
+ * routed two-phase variant (128, 256 or size-derived bins); for CRP_I32 also
+ * hot blocks of 1024 or 4096 items -- on the first sample_vectors outer products of
  * A and B (<= 0: all), with tables sized by the library's estimate, and
  * writes into *best a copy of *base with P, groups, tile_vectors, smem_slots
  * and the variant flags of the fastest (*best_terms_per_s, nullable, its

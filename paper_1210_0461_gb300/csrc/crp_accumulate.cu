@@ -106,7 +106,9 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
             while (advance(st, A, b_hash, q, w, lane)) {
                 uint32_t oi, j;
                 float owa, wb;
-                const bool valid = next_term(st, A, lane, VT, oi, j, owa, wb);
+                int owner;
+                const bool valid = next_term(st, A, lane, VT, oi, j, owa, wb, &owner);
+                const uint32_t orank = __shfl_sync(kFull, st.my_rank, owner);
                 const unsigned long long key = make_key(oi, j);
                 const unsigned act = __ballot_sync(kFull, valid);
                 my_terms += valid ? 1 : 0;
@@ -119,9 +121,18 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
                             lead = lane == __ffs(peers) - 1;
                             cnt = __popc(peers);
                         }
+                        uint32_t hot_slot = 0xFFFFFFFFu;
+                        if (orank < A.hot_R) {
+                            const uint32_t rb = __ldg(A.hot_rank_b + j);
+                            if (rb < A.hot_R) hot_slot = orank * A.hot_R + rb;
+                        }
                         if (lead) {
-                            table_update(A.tv, partition_hash(A.hp, oi, j), key, cnt);
-                            ++flushed;
+                            if (hot_slot != 0xFFFFFFFFu) {
+                                atomicAdd(&A.hot_block[hot_slot], cnt);
+                            } else {
+                                table_update(A.tv, partition_hash(A.hp, oi, j), key, cnt);
+                                ++flushed;
+                            }
                         }
                     } else {
                         const float p = __fmul_rn(owa, wb);
@@ -527,6 +538,53 @@ cudaError_t launch_validate_sparse(const int64_t *ptr, const int32_t *idx, int64
     if (e != cudaSuccess || nnz == 0) return e;
     int64_t b2 = (nnz + 255) / 256;
     k_validate_idx<<<(int)(b2 < 4096 ? b2 : 4096), 256, 0, s>>>(idx, nnz, n_minor, bad);
+    return cudaGetLastError();
+}
+
+// Add the hot block's counts to the partition tables and clear it.
+__global__ void k_hot_flush(unsigned int *hot, uint32_t R, const int64_t *items_a,
+                            const int64_t *items_b, HashPair hp, TableView tv,
+                            unsigned long long *flushed) {
+    unsigned long long n = 0;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < (uint64_t)R * R;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned int c = hot[x];
+        if (!c) continue;
+        hot[x] = 0u;
+        const uint32_t i = (uint32_t)items_a[x / R], j = (uint32_t)items_b[x % R];
+        table_update(tv, partition_hash(hp, i, j), make_key(i, j), c);
+        ++n;
+    }
+    if (n) atomicAdd(flushed, n);
+}
+
+__global__ void k_hot_ranks(uint16_t *rank, int32_t n, const int64_t *items, uint32_t R) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x)
+        rank[x] = 0xFFFFu;
+    __syncthreads();
+}
+
+__global__ void k_hot_scatter(uint16_t *rank, const int64_t *items, uint32_t R) {
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x)
+        rank[items[r]] = (uint16_t)r;
+}
+
+cudaError_t launch_hot_flush(unsigned int *hot, uint32_t R, const int64_t *items_a,
+                             const int64_t *items_b, HashPair hp, TableView tv,
+                             unsigned long long *flushed, cudaStream_t s) {
+    const uint64_t n = (uint64_t)R * R;
+    k_hot_flush<<<(int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192), 256, 0, s>>>(
+        hot, R, items_a, items_b, hp, tv, flushed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hot_ranks(uint16_t *rank, int32_t n, const int64_t *items, uint32_t R,
+                             cudaStream_t s) {
+    k_hot_ranks<<<(n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096, 256, 0, s>>>(rank, n, items, R);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_hot_scatter<<<(R + 255) / 256, 256, 0, s>>>(rank, items, R);
     return cudaGetLastError();
 }
 

@@ -112,6 +112,11 @@ struct crp_plan {
     unsigned long long res_off = 0, res_mask = 0;
     unsigned long long *d_res_keys = nullptr;
     int32_t n_res = 0;
+    // hot block (direct mode)
+    uint32_t hot_R = 0;
+    unsigned int *d_hot = nullptr, *d_cnt_a = nullptr, *d_cnt_b = nullptr, *d_sel = nullptr;
+    uint16_t *d_rank_a = nullptr, *d_rank_b = nullptr;
+    int64_t *d_items_a = nullptr, *d_items_b = nullptr;
     // routed mode: per-group bins
     void *bins = nullptr;
     uint64_t bins_bytes = 0;
@@ -218,6 +223,10 @@ extern "C" crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc,
         return fail(CRP_EINVAL, "smem_slots must be a power of two in [4096, 16384]");
     if (d.groups && (!is_pow2(d.groups) || d.groups > d.P))
         return fail(CRP_EINVAL, "groups must be a power of two <= P");
+    if (d.hot_items && (d.hot_items > 4096 || d.value_type != CRP_I32 ||
+                        !(d.flags & (CRP_PLAN_DIRECT | CRP_PLAN_ROUTED)) || d.summary_counters))
+        return fail(CRP_EINVAL, "hot_items needs CRP_PLAN_DIRECT or CRP_PLAN_ROUTED, CRP_I32, "
+                                "exact mode, <= 4096");
     if (d.summary_counters && d.value_type != CRP_I32)
         return fail(CRP_EUNSUPPORTED, "summaries count {0,1} inputs (CRP_I32) only");
     if (d.summary_counters > (1u << 24))
@@ -294,6 +303,14 @@ extern "C" void crp_plan_destroy(crp_plan *pl) {
     cudaFree(pl->s_val);
     cudaFree(pl->s_hash);
     cudaFree(pl->s_long);
+    cudaFree(pl->d_hot);
+    cudaFree(pl->d_cnt_a);
+    cudaFree(pl->d_cnt_b);
+    cudaFree(pl->d_sel);
+    cudaFree(pl->d_rank_a);
+    cudaFree(pl->d_rank_b);
+    cudaFree(pl->d_items_a);
+    cudaFree(pl->d_items_b);
     cudaFree(pl->d_live);
     cudaFree(pl->d_floor);
     cudaFree(pl->d_ctmp);
@@ -498,6 +515,8 @@ static crp_status estimate_and_allocate(crp_plan *pl, const crp_sparse *A, const
     return alloc_tables(pl, per);
 }
 
+static crp_status select_hot_items(crp_plan *pl, const crp_sparse *A, const crp_sparse *B);
+
 // Compact every partition holding more than ell keys, then re-insert spilled
 // updates (each re-insert may spill again when a partition refills; repeat).
 static crp_status summary_settle(crp_plan *pl) {
@@ -610,6 +629,14 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
     RouteArgs RA;
     RA.acc = make_args(pl, A, B, B->idx, B->val, 1);
     RA.acc.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
+    if (pl->d.hot_items) {
+        crp_status hs = select_hot_items(pl, A, B);
+        if (hs != CRP_OK) return hs;
+        RA.acc.hot_rank_a = pl->d_rank_a;
+        RA.acc.hot_rank_b = pl->d_rank_b;
+        RA.acc.hot_block = pl->d_hot;
+        RA.acc.hot_R = pl->hot_R;
+    }
     RA.bins = pl->bins;
     RA.bin_off = pl->d_bin_off;
     RA.bin_cap = pl->d_bin_cap;
@@ -619,18 +646,60 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
     while ((1u << lgB) < Bn) ++lgB;
     RA.B_shift = pl->logP - lgB;
     const size_t budget = 96u << 10;
-    uint64_t rs = (budget - (size_t)Bn * 4 - 16) / ((size_t)Bn * rec);
+    uint64_t rs = (budget - (size_t)Bn * 12 - 16) / ((size_t)Bn * rec);
     RA.R_s = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(rs, 1), 256);
     RA.pad = 0;
     CRP_CUDA(cudaMemsetAsync(&pl->dc->work_next, 0, sizeof(unsigned int), pl->stream));
     CRP_CUDA(cudaEventRecord(pl->ev0, pl->stream));
     CRP_CUDA(launch_route(RA, 2 * pl->sm_count, pl->stream));
     CRP_CUDA(cudaEventRecord(pl->evm, pl->stream));
-    CRP_CUDA(launch_apply(RA, pl->d_chunk_prefix, 16384, 2 * pl->sm_count, pl->stream));
+    CRP_CUDA(launch_apply(RA, pl->d_chunk_prefix, 2048, 2 * pl->sm_count, pl->stream));
+    if (RA.acc.hot_R) {
+        CRP_CUDA(launch_hot_flush(pl->d_hot, pl->hot_R, pl->d_items_a, pl->d_items_b, pl->hp,
+                                  RA.acc.tv, &pl->dc->flushed, pl->stream));
+        pl->launches += 1;
+    }
     CRP_CUDA(cudaEventRecord(pl->ev1, pl->stream));
     pl->timed = true;
     pl->timed_mid = true;
     pl->launches += 3;
+    return CRP_OK;
+}
+
+// Hot items of this call: the R most frequent row indices of A and column
+// indices of B over the first 1/64 of the outer products (at least 4096);
+// ranks map an item to its row / column of the hot block.
+static crp_status select_hot_items(crp_plan *pl, const crp_sparse *A, const crp_sparse *B) {
+    const uint32_t R = std::min<uint32_t>(pl->d.hot_items,
+                                          (uint32_t)std::min(pl->d.n_rows, pl->d.n_cols));
+    cudaStream_t s = pl->stream;
+    if (!pl->d_hot) {
+        CRP_CUDA(cudaMalloc(&pl->d_hot, (size_t)R * R * 4));
+        CRP_CUDA(cudaMemsetAsync(pl->d_hot, 0, (size_t)R * R * 4, s));
+        CRP_CUDA(cudaMalloc(&pl->d_cnt_a, (size_t)pl->d.n_rows * 4));
+        CRP_CUDA(cudaMalloc(&pl->d_cnt_b, (size_t)pl->d.n_cols * 4));
+        CRP_CUDA(cudaMalloc(&pl->d_rank_a, (size_t)pl->d.n_rows * 2));
+        CRP_CUDA(cudaMalloc(&pl->d_rank_b, (size_t)pl->d.n_cols * 2));
+        CRP_CUDA(cudaMalloc(&pl->d_items_a, (size_t)R * 8));
+        CRP_CUDA(cudaMalloc(&pl->d_items_b, (size_t)R * 8));
+        CRP_CUDA(cudaMalloc(&pl->d_sel, 260 * 4));
+        pl->hot_R = R;
+    }
+    const int64_t K = A->n_major;
+    const int64_t S = std::min<int64_t>(K, std::max<int64_t>(4096, K / 64));
+    int64_t ea = 0, eb = 0;
+    CRP_CUDA(cudaMemcpyAsync(&ea, A->ptr + S, 8, cudaMemcpyDeviceToHost, s));
+    CRP_CUDA(cudaMemcpyAsync(&eb, B->ptr + S, 8, cudaMemcpyDeviceToHost, s));
+    CRP_CUDA(cudaMemsetAsync(pl->d_cnt_a, 0, (size_t)pl->d.n_rows * 4, s));
+    CRP_CUDA(cudaMemsetAsync(pl->d_cnt_b, 0, (size_t)pl->d.n_cols * 4, s));
+    CRP_CUDA(cudaStreamSynchronize(s));
+    CRP_CUDA(launch_item_counts(A->idx, ea, pl->d.n_rows, pl->d_cnt_a, s));
+    CRP_CUDA(launch_item_counts(B->idx, eb, pl->d.n_cols, pl->d_cnt_b, s));
+    CRP_CUDA(select_top(pl->d_cnt_a, pl->d.n_rows, R, pl->d_items_a, pl->d_sel, s));
+    CRP_CUDA(select_top(pl->d_cnt_b, pl->d.n_cols, R, pl->d_items_b, pl->d_sel, s));
+    CRP_CUDA(launch_hot_ranks(pl->d_rank_a, pl->d.n_rows, pl->d_items_a, R, s));
+    CRP_CUDA(launch_hot_ranks(pl->d_rank_b, pl->d.n_cols, pl->d_items_b, R, s));
+    pl->launches += 2 + 2 * 5 + 4;
     return CRP_OK;
 }
 
@@ -683,9 +752,22 @@ extern "C" crp_status crp_outer_accumulate(crp_plan *pl, const crp_sparse *A, co
     if (pl->d.flags & CRP_PLAN_ROUTED) return routed_accumulate(pl, A, B);
     AccumulateArgs a = make_args(pl, A, B, b_idx, b_val, pl->G);
     a.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
+    if (pl->d.hot_items) {
+        st = select_hot_items(pl, A, B);
+        if (st != CRP_OK) return st;
+        a.hot_rank_a = pl->d_rank_a;
+        a.hot_rank_b = pl->d_rank_b;
+        a.hot_block = pl->d_hot;
+        a.hot_R = pl->hot_R;
+    }
     CRP_CUDA(cudaMemsetAsync(&pl->dc->work_next, 0, sizeof(unsigned int), pl->stream));
     CRP_CUDA(cudaEventRecord(pl->ev0, pl->stream));
     CRP_CUDA(launch_accumulate(a, b_hash, pl->grid, pl->stream));
+    if (a.hot_R) {
+        CRP_CUDA(launch_hot_flush(pl->d_hot, pl->hot_R, pl->d_items_a, pl->d_items_b, pl->hp, a.tv,
+                                  &pl->dc->flushed, pl->stream));
+        pl->launches += 1;
+    }
     CRP_CUDA(cudaEventRecord(pl->ev1, pl->stream));
     pl->timed = true;
     pl->timed_mid = false;

@@ -1,6 +1,7 @@
 // Launch-configuration autotuner.  It times candidate configurations of the
 // exact product (partition count P, variant: on-chip combining table / direct
-// HBM updates / routed two-phase, tile of outer products per work item) on a
+// HBM updates / routed two-phase with 128, 256 or size-derived bins, hot
+// blocks of 1024 or 4096 items, tile of outer products per work item) on a
 // prefix of the caller's outer products, and keeps the fastest.  Results are
 // cached in a text file keyed by device name and a shape class of the input
 // (log2 buckets of K, n_rows, n_cols and of the mean terms per outer
@@ -47,11 +48,12 @@ static bool cache_lookup(const char *path, const std::string &key, crp_plan_desc
     bool found = false;
     while (fgets(line, sizeof line, f)) {
         char k[256];
-        unsigned P, groups, tile, slots, flags;
+        unsigned P, groups, tile, slots, flags, hot;
         double v;
-        if (sscanf(line, "%255s %u %u %u %u %u %lf", k, &P, &groups, &tile, &slots, &flags, &v) == 7 &&
-            key == k) {
+        if (sscanf(line, "%255s %u %u %u %u %u %u %lf", k, &P, &groups, &tile, &slots, &flags, &hot,
+                   &v) == 8 && key == k) {
             out->P = P;
+            out->hot_items = hot;
             out->groups = groups;
             out->tile_vectors = tile;
             out->smem_slots = slots;
@@ -69,8 +71,8 @@ static void cache_store(const char *path, const std::string &key, const crp_plan
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %u %u %u %u %u %.6g\n", key.c_str(), d.P, d.groups, d.tile_vectors,
-            d.smem_slots, d.flags, tps);
+    fprintf(f, "%s %u %u %u %u %u %u %.6g\n", key.c_str(), d.P, d.groups, d.tile_vectors,
+            d.smem_slots, d.flags, d.hot_items, tps);
     fclose(f);
 }
 
@@ -108,15 +110,23 @@ extern "C" crp_status crp_autotune(const crp_plan_desc *base, const crp_sparse *
     const std::string key = shape_key(*base, K, Ks ? (double)terms / (double)Ks : 0.0);
     if (cache_lookup(cache_path, key, best, best_terms_per_s)) return CRP_OK;
 
-    struct Cand { uint32_t P, groups, tile, slots, flags; };
+    struct Cand { uint32_t P, groups, tile, slots, flags, hot; };
     std::vector<Cand> cands;
     const uint32_t Ps[] = {256, 1024, 4096};
     const uint32_t tiles[] = {32, 64, 256};
+    const bool ints = base->value_type == CRP_I32;
     for (uint32_t P : Ps) {
-        for (uint32_t t : tiles) cands.push_back({P, 1, t, 8192, CRP_PLAN_DIRECT});
-        cands.push_back({P, 1, 64, 8192, 0u});
-        cands.push_back({P, 1, 64, 16384, 0u});
-        cands.push_back({P, 0, 64, 8192, CRP_PLAN_ROUTED});
+        for (uint32_t t : tiles) cands.push_back({P, 1, t, 8192, CRP_PLAN_DIRECT, 0});
+        cands.push_back({P, 1, 64, 8192, 0u, 0});
+        cands.push_back({P, 1, 64, 16384, 0u, 0});
+        cands.push_back({P, 0, 64, 8192, CRP_PLAN_ROUTED, 0});
+        if (ints) {
+            for (uint32_t h : {1024u, 4096u}) {
+                cands.push_back({P, 1, 64, 8192, CRP_PLAN_DIRECT, h});
+                for (uint32_t g : {0u, 128u, 256u})
+                    if (g <= P) cands.push_back({P, g, 64, 8192, CRP_PLAN_ROUTED, h});
+            }
+        }
     }
     double best_tps = -1.0;
     for (const Cand &c : cands) {
@@ -127,6 +137,7 @@ extern "C" crp_status crp_autotune(const crp_plan_desc *base, const crp_sparse *
         d.tile_vectors = c.tile;
         d.smem_slots = c.slots;
         d.flags = (base->flags & ~(CRP_PLAN_DIRECT | CRP_PLAN_ROUTED)) | c.flags;
+        d.hot_items = c.hot;
         d.table_capacity_hint = 0;
         d.auto_grow = 1;
         crp_plan *pl = nullptr;

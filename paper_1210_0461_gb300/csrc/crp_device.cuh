@@ -179,6 +179,7 @@ struct WarpEnum {
     int32_t b_len;
     // this lane's a entry of the current batch of 32
     uint32_t my_i;
+    uint32_t my_rank;          // row of my_i in the hot block, or 0xFFFF
     float my_wa;
     int32_t lo1, n1, lo2, excl;
     int32_t total, pos;
@@ -201,10 +202,12 @@ __device__ __forceinline__ void load_batch(WarpEnum &st, const AccumulateArgs &A
     bool va = idx < st.a_end;
     int32_t c = 0;
     st.my_i = 0;
+    st.my_rank = 0xFFFFu;
     st.my_wa = 1.0f;
     st.lo1 = 0; st.n1 = 0; st.lo2 = 0;
     if (va) {
         st.my_i = (uint32_t)__ldg(A.a_idx + idx);
+        if (A.hot_rank_a) st.my_rank = __ldg(A.hot_rank_a + st.my_i);
         if (A.a_val) st.my_wa = __ldg(A.a_val + idx);
         if (A.groups == 1) {
             st.n1 = st.b_len;
@@ -270,7 +273,7 @@ __device__ __forceinline__ bool advance(WarpEnum &st, const AccumulateArgs &A,
 // the current batch.  Returns the term (valid, i, j, a value, b value).
 __device__ __forceinline__ bool next_term(WarpEnum &st, const AccumulateArgs &A, int lane,
                                           int value_type, uint32_t &oi, uint32_t &j, float &owa,
-                                          float &wb) {
+                                          float &wb, int *owner = nullptr) {
     const int32_t t = st.pos + lane;
     bool valid = t < st.total;
     int o = 0;
@@ -279,6 +282,7 @@ __device__ __forceinline__ bool next_term(WarpEnum &st, const AccumulateArgs &A,
         int32_t e = __shfl_sync(kFull, st.excl, o + s2);
         if (e <= t) o += s2;
     }
+    if (owner) *owner = o;
     oi = __shfl_sync(kFull, st.my_i, o);
     owa = __shfl_sync(kFull, st.my_wa, o);
     const int32_t olo1 = __shfl_sync(kFull, st.lo1, o);

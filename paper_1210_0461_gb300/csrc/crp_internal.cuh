@@ -126,6 +126,13 @@ struct AccumulateArgs {
     uint32_t smem_slots;       // power of two
     HashPair hp;
     TableView tv;
+    // hot block: exact dense counters for pairs of frequent items (direct,
+    // int mode); rank arrays hold the item's row/column in the block or
+    // 0xFFFF
+    const uint16_t *hot_rank_a = nullptr;
+    const uint16_t *hot_rank_b = nullptr;
+    unsigned int *hot_block = nullptr;
+    uint32_t hot_R = 0;
 };
 
 // Two-phase (routed) accumulation: bins of records per partition group.
@@ -149,6 +156,20 @@ cudaError_t launch_summary_compact(Slot *slots, const unsigned long long *part_o
 cudaError_t launch_reserve_insert(Slot *slots, unsigned long long res_off,
                                   unsigned long long res_mask, const unsigned long long *keys,
                                   int32_t n, cudaStream_t s);
+
+// Hot block (crp_accumulate.cu)
+cudaError_t launch_hot_flush(unsigned int *hot, uint32_t R, const int64_t *items_a,
+                             const int64_t *items_b, HashPair hp, TableView tv,
+                             unsigned long long *flushed, cudaStream_t s);
+cudaError_t launch_hot_ranks(uint16_t *rank, int32_t n, const int64_t *items, uint32_t R,
+                             cudaStream_t s);
+
+// Selections (crp_select.cu)
+int select_grid_for(int64_t n);
+cudaError_t select_top(const uint32_t *key, int64_t n, int64_t K, int64_t *out,
+                       unsigned int *scratch /* 258 */, cudaStream_t s);
+cudaError_t launch_item_counts(const int32_t *idx, int64_t nnz, int32_t n_items, unsigned int *cnt,
+                               cudaStream_t s);
 
 // Record the calling thread's error message (read by crp_last_error).
 void set_last_error(const std::string &msg);

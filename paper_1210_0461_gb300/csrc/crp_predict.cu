@@ -24,40 +24,6 @@ extern "C" crp_status crp_reserve(crp_plan *plan, const uint64_t *keys, int32_t 
 
 namespace crp {
 
-__global__ void k_item_counts(const int32_t *idx, int64_t nnz, int32_t n_items, unsigned int *cnt) {
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nnz;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t v = idx[x];
-        if (v >= 0 && v < n_items) atomicAdd(&cnt[v], 1u);
-    }
-}
-
-__global__ void k_sel_hist(const uint32_t *key, int64_t n, uint32_t prefix, uint32_t pmask,
-                           int shift, unsigned int *hist) {
-    __shared__ unsigned int h[256];
-    for (int t = threadIdx.x; t < 256; t += blockDim.x) h[t] = 0;
-    __syncthreads();
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t k = key[x];
-        if ((k & pmask) == prefix) atomicAdd(&h[(k >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < 256; t += blockDim.x)
-        if (h[t]) atomicAdd(&hist[t], h[t]);
-}
-
-__global__ void k_sel_emit(const uint32_t *key, int64_t n, uint32_t tau, uint32_t need_at_tau,
-                           int64_t *out, unsigned int *cnt, unsigned int *tie) {
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t k = key[x];
-        bool take = k > tau;
-        if (k == tau) take = atomicAdd(tie, 1u) < need_at_tau;
-        if (take) out[atomicAdd(cnt, 1u)] = x;
-    }
-}
-
 // Order-preserving key of a float (larger float -> larger key).
 __global__ void k_float_keys(const float *v, int64_t n, uint32_t *key) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
@@ -111,42 +77,6 @@ __global__ void k_pair_keys(const int64_t *sel, int64_t n, const int32_t *ci, co
     }
 }
 
-static int grid_for(int64_t n) {
-    int64_t g = (n + 255) / 256;
-    return (int)(g < 4096 ? (g > 0 ? g : 1) : 4096);
-}
-
-// Indices (unordered) of the K largest keys.  out: device, K entries.
-static cudaError_t select_top(const uint32_t *key, int64_t n, int64_t K, int64_t *out,
-                              unsigned int *scratch /* 258 */, cudaStream_t s) {
-    uint32_t prefix = 0, pmask = 0;
-    uint64_t need = (uint64_t)K;
-    for (int pass = 0; pass < 4; ++pass) {
-        const int shift = 24 - 8 * pass;
-        cudaError_t e = cudaMemsetAsync(scratch, 0, 256 * 4, s);
-        if (e != cudaSuccess) return e;
-        k_sel_hist<<<grid_for(n), 256, 0, s>>>(key, n, prefix, pmask, shift, scratch);
-        unsigned int h[256];
-        e = cudaMemcpyAsync(h, scratch, sizeof h, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return e;
-        uint64_t cum = 0;
-        int d = 255;
-        for (; d > 0; --d) {
-            if (cum + h[d] >= need) break;
-            cum += h[d];
-        }
-        need -= cum;
-        prefix |= (uint32_t)d << shift;
-        pmask |= 255u << shift;
-    }
-    cudaError_t e = cudaMemsetAsync(scratch + 256, 0, 8, s);
-    if (e != cudaSuccess) return e;
-    k_sel_emit<<<grid_for(n), 256, 0, s>>>(key, n, prefix, (uint32_t)need, out, scratch + 256,
-                                           scratch + 257);
-    return cudaGetLastError();
-}
-
 }  // namespace crp
 
 using namespace crp;
@@ -184,14 +114,12 @@ extern "C" crp_status crp_candidate_pairs(const crp_sparse *prefix, int32_t n_it
         ok(cudaMalloc(&b.scratch, 260 * 4)) && ok(cudaMalloc(&b.items, (size_t)R * 8))) {
         ok(cudaMemsetAsync(b.cnt, 0, (size_t)n_items * 4, s));
         ok(cudaMemsetAsync(b.mx, 0, 4, s));
-        if (prefix->nnz > 0)
-            k_item_counts<<<grid_for(prefix->nnz), 256, 0, s>>>(prefix->idx, prefix->nnz, n_items,
-                                                                b.cnt);
-        k_max_u32<<<grid_for(n_items), 256, 0, s>>>(b.cnt, n_items, b.mx);
+        ok(launch_item_counts(prefix->idx, prefix->nnz, n_items, b.cnt, s));
+        k_max_u32<<<select_grid_for(n_items), 256, 0, s>>>(b.cnt, n_items, b.mx);
         ok(cudaGetLastError());
         if (st == CRP_OK) ok(select_top(b.cnt, n_items, R, b.items, b.scratch, s));
         if (st == CRP_OK) {
-            k_candidates<<<grid_for((int64_t)R * R), 256, 0, s>>>(b.items, R, b.cnt, b.mx, i_out,
+            k_candidates<<<select_grid_for((int64_t)R * R), 256, 0, s>>>(b.items, R, b.cnt, b.mx, i_out,
                                                                   j_out, x_out);
             ok(cudaGetLastError());
             ok(cudaStreamSynchronize(s));
@@ -237,17 +165,17 @@ extern "C" crp_status crp_predict_reserve(crp_plan *plan, const crp_sparse *pref
         if (st == CRP_OK) {
             if (params) st = crp_mlp_forward(params, x, score, nc, stream);
             else {
-                k_heuristic<<<grid_for(nc), 256, 0, s>>>(x, nc, score);
+                k_heuristic<<<select_grid_for(nc), 256, 0, s>>>(x, nc, score);
                 ok(cudaGetLastError());
             }
         }
         if (st == CRP_OK) {
-            k_float_keys<<<grid_for(nc), 256, 0, s>>>(score, nc, key);
+            k_float_keys<<<select_grid_for(nc), 256, 0, s>>>(score, nc, key);
             ok(cudaGetLastError());
         }
         if (st == CRP_OK) ok(select_top(key, nc, take, sel, scratch, s));
         if (st == CRP_OK) {
-            k_pair_keys<<<grid_for(take), 256, 0, s>>>(sel, take, ci, cj, full_mode ? 1 : 0, keys);
+            k_pair_keys<<<select_grid_for(take), 256, 0, s>>>(sel, take, ci, cj, full_mode ? 1 : 0, keys);
             ok(cudaGetLastError());
             ok(cudaStreamSynchronize(s));
         }

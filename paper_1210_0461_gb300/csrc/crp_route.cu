@@ -23,6 +23,8 @@
 
 namespace crp {
 
+constexpr int kRouteChunks = 8;   // chunks of 32 terms per warp between CTA barriers
+
 struct Rec16 {
     unsigned long long key;
     float p, e;  // exact product p + e
@@ -42,6 +44,22 @@ __device__ __forceinline__ unsigned long long rec_val(const Rec16 &r) {
     return (unsigned long long)__double_as_longlong((double)r.p + (double)r.e);
 }
 
+// Records are written once and read once: evict-first hints keep them from
+// displacing the table region that the apply phase wants in L2.
+__device__ __forceinline__ void store_stream(unsigned long long *p, unsigned long long v) {
+    __stcs(p, v);
+}
+__device__ __forceinline__ void store_stream(Rec16 *p, const Rec16 &v) {
+    __stcs((ulonglong2 *)p, *(const ulonglong2 *)&v);
+}
+__device__ __forceinline__ unsigned long long load_stream(const unsigned long long *p) {
+    return __ldcs(p);
+}
+__device__ __forceinline__ Rec16 load_stream(const Rec16 *p) {
+    ulonglong2 v = __ldcs((const ulonglong2 *)p);
+    return *(Rec16 *)&v;
+}
+
 template <typename R>
 __device__ __forceinline__ void apply_record(const RouteArgs &RA, const R &r) {
     const unsigned long long key = rec_key(r);
@@ -57,27 +75,26 @@ __device__ __forceinline__ void bin_append(const RouteArgs &RA, uint32_t b, cons
     else apply_record(RA, r);
 }
 
+// Write bin b's staged records out (all of them; the count is reset).
 template <int VT>
-__device__ void flush_bins(const RouteArgs &RA, typename RecT<VT>::type *stage, unsigned int *scnt,
-                           uint32_t thr, int warp, int lane) {
+__device__ __forceinline__ void flush_bin(const RouteArgs &RA, typename RecT<VT>::type *stage,
+                                          unsigned int *scnt, uint32_t b, int lane) {
     typedef typename RecT<VT>::type R;
     R *bins = (R *)RA.bins;
-    for (uint32_t b = warp; b < RA.B; b += kWarps) {
-        const uint32_t c = scnt[b];
-        const uint32_t n = c < RA.R_s ? c : RA.R_s;
-        if (n == 0 || n < thr) continue;
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&RA.bin_cnt[b], (unsigned long long)n);
-        base = __shfl_sync(kFull, base, 0);
-        const unsigned long long cap = RA.bin_cap[b], off = RA.bin_off[b];
-        for (uint32_t t = lane; t < n; t += 32) {
-            const R r = stage[(size_t)b * RA.R_s + t];
-            if (base + t < cap) bins[off + base + t] = r;
-            else apply_record(RA, r);
-        }
-        __syncwarp();
-        if (lane == 0) scnt[b] = 0;
+    const uint32_t c = scnt[b];
+    const uint32_t n = c < RA.R_s ? c : RA.R_s;
+    if (n == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&RA.bin_cnt[b], (unsigned long long)n);
+    base = __shfl_sync(kFull, base, 0);
+    const unsigned long long cap = RA.bin_cap[b], off = RA.bin_off[b];
+    for (uint32_t t = lane; t < n; t += 32) {
+        const R r = stage[(size_t)b * RA.R_s + t];
+        if (base + t < cap) store_stream(bins + off + base + t, r);
+        else apply_record(RA, r);
     }
+    __syncwarp();
+    if (lane == 0) scnt[b] = 0;
 }
 
 template <int VT>
@@ -86,11 +103,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_route(RouteArgs RA) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *stage = (R *)smem_raw;
     unsigned int *scnt = (unsigned int *)(stage + (size_t)RA.B * RA.R_s);
-    unsigned int *ctrl = scnt + RA.B;
+    unsigned int *ready = scnt + RA.B;          // two lists of bins that reached the threshold
+    unsigned int *ctrl = ready + 2 * RA.B;      // ctrl[0] work item, ctrl[1..2] list counts
     const AccumulateArgs &A = RA.acc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (uint32_t b = threadIdx.x; b < RA.B; b += kThreads) scnt[b] = 0;
+    if (threadIdx.x == 0) ctrl[1] = ctrl[2] = 0;
     __syncthreads();
+    uint32_t parity = 0;
     const uint32_t thr = RA.R_s / 2 > 0 ? RA.R_s / 2 : 1;
     unsigned long long my_terms = 0;
     while (true) {
@@ -107,12 +127,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_route(RouteArgs RA) {
         st.total = 0;
         st.pos = 0;
         while (true) {
-            for (int r = 0; r < kRoundChunks; ++r) {
+            unsigned int *rlist = ready + parity * RA.B;
+            unsigned int *rcount = &ctrl[1 + parity];
+            for (int r = 0; r < kRouteChunks; ++r) {
                 if (st.done || !advance(st, A, nullptr, 0u, A.hp.ha.mask + 1u, lane)) break;
                 uint32_t oi, j;
                 float owa, wb;
-                const bool valid = next_term(st, A, lane, VT, oi, j, owa, wb);
+                int owner;
+                bool valid = next_term(st, A, lane, VT, oi, j, owa, wb, &owner);
+                const uint32_t orank = __shfl_sync(kFull, st.my_rank, owner);
                 my_terms += valid ? 1 : 0;
+                if (VT == CRP_I32 && valid && orank < A.hot_R) {
+                    const uint32_t rb = __ldg(A.hot_rank_b + j);
+                    if (rb < A.hot_R) {
+                        atomicAdd(&A.hot_block[orank * A.hot_R + rb], 1u);
+                        valid = false;
+                    }
+                }
                 if (valid) {
                     const unsigned long long key = make_key(oi, j);
                     const uint32_t b = partition_hash(A.hp, oi, j) >> RA.B_shift;
@@ -127,15 +158,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_route(RouteArgs RA) {
                     const unsigned int pos = atomicAdd(&scnt[b], 1u);
                     if (pos < RA.R_s) stage[(size_t)b * RA.R_s + pos] = rec;
                     else bin_append(RA, b, rec);
+                    if (pos == thr - 1) rlist[atomicAdd(rcount, 1u)] = b;
                 }
             }
             const int more = __syncthreads_or(st.done ? 0 : 1);
-            flush_bins<VT>(RA, stage, scnt, thr, warp, lane);
+            const unsigned int nready = *rcount;
+            for (unsigned int q = warp; q < nready; q += kWarps)
+                flush_bin<VT>(RA, stage, scnt, rlist[q], lane);
+            if (threadIdx.x == 0) ctrl[2 - parity] = 0;   // the other list, for the next round
+            parity ^= 1u;
             __syncthreads();
             if (!more) break;
         }
     }
-    flush_bins<VT>(RA, stage, scnt, 1u, warp, lane);
+    for (uint32_t b = warp; b < RA.B; b += kWarps) flush_bin<VT>(RA, stage, scnt, b, lane);
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) my_terms += __shfl_down_sync(kFull, my_terms, d);
     if (lane == 0 && my_terms) atomicAdd(&A.tv.dc->terms, my_terms);
@@ -170,21 +206,22 @@ k_bin_chunks(const unsigned long long *bin_cnt, const unsigned long long *bin_ca
     if (threadIdx.x == 1023) chunk_prefix[B] = part[1023];
 }
 
+// Each warp takes chunks of CH records (bins in order, so all warps work on
+// one or two groups' table regions at a time) and applies them; no CTA-wide
+// barriers.
 template <int VT>
 __global__ void __launch_bounds__(kThreads, 2)
 k_apply(RouteArgs RA, const unsigned int *__restrict__ chunk_prefix, uint32_t CH) {
     typedef typename RecT<VT>::type R;
-    __shared__ unsigned int item_s;
     const R *bins = (const R *)RA.bins;
     const unsigned int total = chunk_prefix[RA.B];
+    const int lane = threadIdx.x & 31;
     unsigned long long applied = 0;
     while (true) {
-        if (threadIdx.x == 0) item_s = atomicAdd(&RA.acc.tv.dc->work_next, 1u);
-        __syncthreads();
-        const unsigned int item = item_s;
-        __syncthreads();
+        unsigned int item = 0;
+        if (lane == 0) item = atomicAdd(&RA.acc.tv.dc->work_next, 1u);
+        item = __shfl_sync(kFull, item, 0);
         if (item >= total) break;
-        // bin of this chunk: last b with chunk_prefix[b] <= item
         uint32_t lo = 0, hi = RA.B;
         while (hi - lo > 1) {
             uint32_t mid = (lo + hi) >> 1;
@@ -195,19 +232,19 @@ k_apply(RouteArgs RA, const unsigned int *__restrict__ chunk_prefix, uint32_t CH
         const unsigned long long start = (unsigned long long)(item - chunk_prefix[b]) * CH;
         const unsigned long long end = start + CH < n ? start + CH : n;
         const unsigned long long off = RA.bin_off[b];
-        for (unsigned long long x = start + threadIdx.x; x < end; x += kThreads) {
-            apply_record(RA, bins[off + x]);
+        for (unsigned long long x = start + lane; x < end; x += 32) {
+            apply_record(RA, load_stream(bins + off + x));
             ++applied;
         }
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) applied += __shfl_down_sync(kFull, applied, d);
-    if ((threadIdx.x & 31) == 0 && applied) atomicAdd(&RA.acc.tv.dc->flushed, applied);
+    if (lane == 0 && applied) atomicAdd(&RA.acc.tv.dc->flushed, applied);
 }
 
 size_t route_smem_bytes(int value_type, uint32_t B, uint32_t R_s) {
     const size_t rec = value_type == CRP_I32 ? 8 : 16;
-    return (size_t)B * R_s * rec + (size_t)B * 4 + 16;
+    return (size_t)B * R_s * rec + (size_t)B * 12 + 16;
 }
 
 cudaError_t launch_route(const RouteArgs &RA, int grid, cudaStream_t s) {

@@ -1,0 +1,89 @@
+// Selections on the GPU: item counts over a compressed index array, and the
+// indices of the K largest 32-bit keys (MSD radix select, 8-bit digits, ties
+// at the threshold taken in arbitrary order).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "crp_internal.cuh"
+
+namespace crp {
+
+__global__ void k_item_counts(const int32_t *idx, int64_t nnz, int32_t n_items, unsigned int *cnt) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nnz;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = idx[x];
+        if (v >= 0 && v < n_items) atomicAdd(&cnt[v], 1u);
+    }
+}
+
+__global__ void k_sel_hist(const uint32_t *key, int64_t n, uint32_t prefix, uint32_t pmask,
+                           int shift, unsigned int *hist) {
+    __shared__ unsigned int h[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = key[x];
+        if ((k & pmask) == prefix) atomicAdd(&h[(k >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 256; t += blockDim.x)
+        if (h[t]) atomicAdd(&hist[t], h[t]);
+}
+
+__global__ void k_sel_emit(const uint32_t *key, int64_t n, uint32_t tau, uint32_t need_at_tau,
+                           int64_t *out, unsigned int *cnt, unsigned int *tie) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = key[x];
+        bool take = k > tau;
+        if (k == tau) take = atomicAdd(tie, 1u) < need_at_tau;
+        if (take) out[atomicAdd(cnt, 1u)] = x;
+    }
+}
+
+int select_grid_for(int64_t n) {
+    int64_t g = (n + 255) / 256;
+    return (int)(g < 4096 ? (g > 0 ? g : 1) : 4096);
+}
+
+// Indices (unordered) of the K largest keys.  out: device, K entries.
+cudaError_t select_top(const uint32_t *key, int64_t n, int64_t K, int64_t *out,
+                              unsigned int *scratch /* 258 */, cudaStream_t s) {
+    uint32_t prefix = 0, pmask = 0;
+    uint64_t need = (uint64_t)K;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 24 - 8 * pass;
+        cudaError_t e = cudaMemsetAsync(scratch, 0, 256 * 4, s);
+        if (e != cudaSuccess) return e;
+        k_sel_hist<<<select_grid_for(n), 256, 0, s>>>(key, n, prefix, pmask, shift, scratch);
+        unsigned int h[256];
+        e = cudaMemcpyAsync(h, scratch, sizeof h, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        uint64_t cum = 0;
+        int d = 255;
+        for (; d > 0; --d) {
+            if (cum + h[d] >= need) break;
+            cum += h[d];
+        }
+        need -= cum;
+        prefix |= (uint32_t)d << shift;
+        pmask |= 255u << shift;
+    }
+    cudaError_t e = cudaMemsetAsync(scratch + 256, 0, 8, s);
+    if (e != cudaSuccess) return e;
+    k_sel_emit<<<select_grid_for(n), 256, 0, s>>>(key, n, prefix, (uint32_t)need, out, scratch + 256,
+                                           scratch + 257);
+    return cudaGetLastError();
+}
+
+
+cudaError_t launch_item_counts(const int32_t *idx, int64_t nnz, int32_t n_items, unsigned int *cnt,
+                               cudaStream_t s) {
+    if (nnz <= 0) return cudaSuccess;
+    k_item_counts<<<select_grid_for(nnz), 256, 0, s>>>(idx, nnz, n_items, cnt);
+    return cudaGetLastError();
+}
+
+}  // namespace crp

@@ -61,6 +61,8 @@ CONFIGS = [
     dict(groups=2, flags=1 | 2),  # no warp match
     dict(flags=4 | 2), dict(groups=8, flags=4 | 2),  # direct HBM updates
     dict(flags=8 | 2), dict(groups=16, flags=8 | 2), dict(groups=64, flags=8 | 1 | 2),  # routed
+    dict(flags=4 | 2, hot_items=64), dict(flags=4 | 2, hot_items=1000),  # direct + hot block
+    dict(groups=16, flags=8 | 2, hot_items=128),                         # routed + hot block
 ]
 
 
@@ -129,13 +131,16 @@ def _random_case(seed, K, n_i, n_j, density, values):
     return A, B
 
 
-@pytest.mark.parametrize("seed,P,G,fl", [(0, 1, 1, 2), (1, 2, 2, 2), (2, 64, 8, 2),
-                                         (3, 1024, 32, 2), (4, 4096, 4096, 2), (5, 16, 1, 2),
-                                         (6, 256, 256, 8 | 2), (7, 1, 1, 8 | 2)])
-def test_random_edge_cases_int(crp, seed, P, G, fl):
+@pytest.mark.parametrize("seed,P,G,fl,hot", [(0, 1, 1, 2, 0), (1, 2, 2, 2, 0), (2, 64, 8, 2, 0),
+                                             (3, 1024, 32, 2, 0), (4, 4096, 4096, 2, 0),
+                                             (5, 16, 1, 2, 0), (6, 256, 256, 8 | 2, 0),
+                                             (7, 1, 1, 8 | 2, 0), (8, 64, 1, 4 | 2, 16),
+                                             (9, 16, 1, 4 | 2, 500)])
+def test_random_edge_cases_int(crp, seed, P, G, fl, hot):
     A, B = _random_case(seed, 700, 37 + seed * 50, 53 + seed * 30, 0.2, False)
     ref = O.exact_product(A, B, O.FULL)
-    plan = _run(crp, A, B, A.n_minor, B.n_minor, P, groups=G, tile_vectors=7, flags=fl)
+    plan = _run(crp, A, B, A.n_minor, B.n_minor, P, groups=G, tile_vectors=7, flags=fl,
+                hot_items=hot)
     _check_exact(crp, plan, ref, P)
     plan.close()
 
