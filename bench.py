@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--groups", type=int, default=1)
     ap.add_argument("--tile", type=int, default=64)
     ap.add_argument("--smem-slots", type=int, default=8192)
+    ap.add_argument("--hot", type=int, default=0, help="hot-block items (direct/routed)")
     ap.add_argument("--topk", type=int, default=1000)
     ap.add_argument("--no-match", action="store_true")
     ap.add_argument("--mode", choices=["direct", "smem", "routed"], default="direct",
@@ -121,7 +122,7 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("crp_accumulate.cu", "crp_device.cuh", "crp_internal.cuh"):
+    for f in ("crp_accumulate.cu", "crp_route.cu", "crp_device.cuh", "crp_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1210_0461_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -242,12 +243,13 @@ def main():
                  "seconds": round(time.time() - t0, 1)}
         args.P, args.groups, args.tile, args.smem_slots = (kw["P"], kw["groups"],
                                                            kw["tile_vectors"], kw["smem_slots"])
+        args.hot = kw["hot_items"]
         flags = kw["flags"] | (crp.CRP_PLAN_NO_WARP_MATCH if args.no_match else 0)
         args.mode = ("routed" if flags & crp.CRP_PLAN_ROUTED else
                      "direct" if flags & crp.CRP_PLAN_DIRECT else "smem")
     plan = crp.Plan(T.n_minor, T.n_minor, args.P, ci.SEED_A, ci.SEED_B, groups=args.groups,
                     tile_vectors=args.tile, smem_slots=args.smem_slots, flags=flags,
-                    stream=stream)
+                    hot_items=args.hot, stream=stream)
 
     def step():
         plan.reset()
@@ -344,7 +346,7 @@ def main():
                                    "exact int32 T^T T (all entries), top-1000 pairs",
                        "P": args.P, "groups": args.groups, "tile_vectors": args.tile,
                        "smem_slots": args.smem_slots, "warp_match": not args.no_match,
-                       "mode": args.mode, "autotune": tuned,
+                       "mode": args.mode, "hot_items": args.hot, "autotune": tuned,
                        "terms_per_step": terms_step, "entries": entries,
                        "nnz": int(T.nnz), "l2": "inputs (0.8 GB) and tables "
                        f"({st['table_slots'] * 16 / 1e9:.1f} GB) exceed L2; no flush",
@@ -353,7 +355,10 @@ def main():
                        "gen_seconds": round(gen_s, 2)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": "k_accumulate", "kernel_ms": acc,
+                         "kernel": {"direct": "k_accumulate", "smem": "k_accumulate",
+                                    "routed": "k_route+k_apply"}[args.mode]
+                                   + ("+k_hot_flush" if args.hot else ""),
+                         "kernel_ms": acc,
                          "bytes_model": f"{BYTES_PER_TERM_UPDATE:g} B/term + input + "
                                         f"{SLOT_BYTES:g} B/entry",
                          "peak_source": f"{peak_src} hbm_gbs"},

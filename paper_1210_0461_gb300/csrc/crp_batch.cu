@@ -261,7 +261,6 @@ static BatchArgs batch_args(crp_batch *b, Slot *slots, const unsigned long long 
     a.wait_ns = b->wait_ns;
     a.hp = b->hp;
     TableView tv;
-    memset(&tv, 0, sizeof tv);
     tv.slots = slots;
     tv.part_off = off;
     tv.part_mask = mask;

@@ -85,23 +85,25 @@ struct SpillRec {
 };
 
 // Everything a table-update kernel needs to reach the partition tables.
+// Every field has a default, so a view built field by field never carries
+// garbage into the update paths.
 struct TableView {
-    Slot *slots;
-    const unsigned long long *part_off;   // first slot of each partition
-    const unsigned long long *part_mask;  // capacity - 1 (capacity a power of two)
-    unsigned int *part_full;              // set once a partition had no free slot
-    SpillRec *spill;
-    unsigned long long spill_cap;
-    DevCounters *dc;
-    int value_type;
+    Slot *slots = nullptr;
+    const unsigned long long *part_off = nullptr;   // first slot of each partition
+    const unsigned long long *part_mask = nullptr;  // capacity - 1 (a power of two)
+    unsigned int *part_full = nullptr;              // set once a partition had no free slot
+    SpillRec *spill = nullptr;
+    unsigned long long spill_cap = 0;
+    DevCounters *dc = nullptr;
+    int value_type = 0;
     // summary mode (Space-Saving semantics per partition)
-    int summary;                          // 1: tables are counter summaries
-    unsigned int *live;                   // occupied slots per partition
-    const unsigned int *floor;            // current floor (min count) per partition
-    unsigned int hard_cap;                // max live slots before new keys spill
+    int summary = 0;                          // 1: tables are counter summaries
+    unsigned int *live = nullptr;             // occupied slots per partition
+    const unsigned int *floor = nullptr;      // current floor (min count) per partition
+    unsigned int hard_cap = 0;                // max live slots before new keys spill
     // reserved exact counters probed before the summaries (0 slots = none)
-    unsigned long long res_off, res_mask; // region [res_off, res_off + res_mask + 1)
-    int has_reserved;
+    unsigned long long res_off = 0, res_mask = 0;  // [res_off, res_off + res_mask + 1)
+    int has_reserved = 0;
 };
 
 struct AccumulateArgs {

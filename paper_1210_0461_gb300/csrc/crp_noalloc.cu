@@ -180,6 +180,8 @@ extern "C" crp_status crp_outer_product_noalloc(const crp_plan_desc *desc, const
         a.tv.spill_cap = 0;     // a full partition is reported, nothing is kept aside
         a.tv.dc = &sc->dc;
         a.tv.value_type = d.value_type;
+        a.tv.summary = 0;          // exact tables
+        a.tv.has_reserved = 0;
         const int per_sm = accumulate_max_blocks_per_sm(d.value_type, 4096, true);
         if (per_sm <= 0) return noalloc_fail(CRP_ECUDA, "accumulate kernel cannot be resident");
         NA_CUDA(launch_accumulate(a, nullptr, per_sm * sms, s));
