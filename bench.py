@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--tile", type=int, default=64)
     ap.add_argument("--smem-slots", type=int, default=8192)
     ap.add_argument("--hot", type=int, default=0, help="hot-block items (direct/routed)")
+    ap.add_argument("--load", type=int, default=0, help="target table load %% (0 = library default)")
     ap.add_argument("--topk", type=int, default=1000)
     ap.add_argument("--no-match", action="store_true")
     ap.add_argument("--mode", choices=["direct", "smem", "routed"], default="direct",
@@ -249,7 +250,8 @@ def main():
                      "direct" if flags & crp.CRP_PLAN_DIRECT else "smem")
     plan = crp.Plan(T.n_minor, T.n_minor, args.P, ci.SEED_A, ci.SEED_B, groups=args.groups,
                     tile_vectors=args.tile, smem_slots=args.smem_slots, flags=flags,
-                    hot_items=args.hot, stream=stream)
+                    hot_items=args.hot, target_load_pct=args.load, auto_grow=True,
+                    stream=stream)
 
     def step():
         plan.reset()
@@ -346,7 +348,8 @@ def main():
                                    "exact int32 T^T T (all entries), top-1000 pairs",
                        "P": args.P, "groups": args.groups, "tile_vectors": args.tile,
                        "smem_slots": args.smem_slots, "warp_match": not args.no_match,
-                       "mode": args.mode, "hot_items": args.hot, "autotune": tuned,
+                       "mode": args.mode, "hot_items": args.hot, "target_load_pct": args.load,
+                       "autotune": tuned,
                        "terms_per_step": terms_step, "entries": entries,
                        "nnz": int(T.nnz), "l2": "inputs (0.8 GB) and tables "
                        f"({st['table_slots'] * 16 / 1e9:.1f} GB) exceed L2; no flush",

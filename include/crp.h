@@ -125,6 +125,10 @@ typedef struct {
                                      first 1/64 of the outer products; their
                                      counts are added to the partition tables
                                      at the end of the call.  R <= 4096. */
+    uint32_t target_load_pct;     /* exact tables sized by the library: at most
+                                     this % of a partition's slots occupied per
+                                     the estimate (0 = 60; <= 90) */
+    uint32_t _pad2;
 } crp_plan_desc;
 
 typedef struct crp_plan crp_plan;

@@ -219,6 +219,7 @@ extern "C" crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc,
     if (d.value_type != CRP_I32 && d.value_type != CRP_F32_COMP)
         return fail(CRP_EINVAL, "unknown value_type");
     if (d.mode != CRP_FULL && d.mode != CRP_UPPER) return fail(CRP_EINVAL, "unknown mode");
+    if (d.target_load_pct > 90) return fail(CRP_EINVAL, "target_load_pct must be <= 90");
     if (d.smem_slots && (!is_pow2(d.smem_slots) || d.smem_slots < 4096 || d.smem_slots > 16384))
         return fail(CRP_EINVAL, "smem_slots must be a power of two in [4096, 16384]");
     if (d.groups && (!is_pow2(d.groups) || d.groups > d.P))
@@ -510,8 +511,9 @@ static crp_status estimate_and_allocate(crp_plan *pl, const crp_sparse *A, const
             distinct = std::max<uint64_t>((uint64_t)mx * P, (uint64_t)sum * Gs);
         }
     }
-    // target at most ~60% load per partition
-    uint64_t per = (uint64_t)((double)distinct / P / 0.6) + 64;
+    // target load per partition (default 60%)
+    const double load = pl->d.target_load_pct ? pl->d.target_load_pct / 100.0 : 0.6;
+    uint64_t per = (uint64_t)((double)distinct / P / load) + 64;
     return alloc_tables(pl, per);
 }
 
