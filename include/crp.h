@@ -128,6 +128,12 @@ typedef struct {
     uint32_t target_load_pct;     /* exact tables sized by the library: at most
                                      this % of a partition's slots occupied per
                                      the estimate (0 = 60; <= 90) */
+    uint32_t part_begin, part_end;/* the plan's interval [q, r) of partitions
+                                     (Figure 1, CRoP run on one interval;
+                                     Theorem 1's K instances use disjoint equal
+                                     intervals): only entries with h(i,j) in it
+                                     are accumulated and stored.  0, 0 = all.
+                                     Exact mode only. */
     uint32_t _pad2;
 } crp_plan_desc;
 

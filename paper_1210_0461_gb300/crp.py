@@ -48,6 +48,7 @@ class crp_plan_desc(ctypes.Structure):
                 ("groups", ctypes.c_uint32), ("tile_vectors", ctypes.c_uint32),
                 ("smem_slots", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("hot_items", ctypes.c_uint32), ("target_load_pct", ctypes.c_uint32),
+                ("part_begin", ctypes.c_uint32), ("part_end", ctypes.c_uint32),
                 ("_pad2", ctypes.c_uint32)]
 
 
@@ -213,7 +214,7 @@ class Plan:
                  tile_vectors: int = 0, smem_slots: int = 0, capacity_hint: int = 0,
                  auto_grow: bool = False, flags: int = 0, stream=None,
                  summary_counters: int = 0, reserved_counters: int = 0, hot_items: int = 0,
-                 target_load_pct: int = 0):
+                 target_load_pct: int = 0, part_begin: int = 0, part_end: int = 0):
         self._lib = lib()
         d = crp_plan_desc()
         d.n_rows, d.n_cols, d.P = n_rows, n_cols, P
@@ -223,6 +224,7 @@ class Plan:
         d.summary_counters, d.reserved_counters = summary_counters, reserved_counters
         d.hot_items = hot_items
         d.target_load_pct = target_load_pct
+        d.part_begin, d.part_end = part_begin, part_end
         d.auto_grow = 1 if auto_grow else 0
         d.groups, d.tile_vectors, d.smem_slots, d.flags = groups, tile_vectors, smem_slots, flags
         self.desc = d

@@ -99,6 +99,7 @@ struct crp_plan {
     uint64_t s_nnz_cap = 0, s_k_cap = 0;
     // launch configuration
     uint32_t G = 1, tile = 64, S = 8192;
+    uint32_t q = 0, r = 0;  // owned partition interval [q, r)
     int grid = 0, grid_direct = 0;
     bool tables_ready = false;
     float summary_ms = 0.f;
@@ -141,11 +142,15 @@ static crp_status alloc_tables(crp_plan *pl, uint64_t cap_per_partition) {
     cap_per_partition = next_pow2(std::max<uint64_t>(cap_per_partition, 64));
     pl->h_off.resize(P);
     pl->h_mask.resize(P);
+    // partitions outside the plan's interval get no slots (capacity 0: the
+    // mask sentinel ~0 makes mask + 1 == 0)
+    uint64_t total = 0;
     for (uint32_t p = 0; p < P; ++p) {
-        pl->h_off[p] = (unsigned long long)p * cap_per_partition;
-        pl->h_mask[p] = cap_per_partition - 1;
+        const bool own = p >= pl->q && p < pl->r;
+        pl->h_off[p] = total;
+        pl->h_mask[p] = own ? cap_per_partition - 1 : ~0ull;
+        if (own) total += cap_per_partition;
     }
-    uint64_t total = (uint64_t)P * cap_per_partition;
     if (pl->slots) cudaFree(pl->slots);
     pl->slots = nullptr;
     CRP_CUDA(cudaMalloc(&pl->slots, total * sizeof(Slot)));
@@ -220,6 +225,10 @@ extern "C" crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc,
         return fail(CRP_EINVAL, "unknown value_type");
     if (d.mode != CRP_FULL && d.mode != CRP_UPPER) return fail(CRP_EINVAL, "unknown mode");
     if (d.target_load_pct > 90) return fail(CRP_EINVAL, "target_load_pct must be <= 90");
+    if ((d.part_begin || d.part_end) &&
+        (d.part_begin >= d.part_end || d.part_end > d.P || d.summary_counters))
+        return fail(CRP_EINVAL, "partition interval must satisfy 0 <= begin < end <= P "
+                                "(exact mode only)");
     if (d.smem_slots && (!is_pow2(d.smem_slots) || d.smem_slots < 4096 || d.smem_slots > 16384))
         return fail(CRP_EINVAL, "smem_slots must be a power of two in [4096, 16384]");
     if (d.groups && (!is_pow2(d.groups) || d.groups > d.P))
@@ -249,6 +258,8 @@ extern "C" crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc,
     pl->hp.ha = make_side_hash(d.seed_a, pl->logP);
     pl->hp.hb = make_side_hash(d.seed_b, pl->logP);
     pl->G = d.groups ? d.groups : 1u;
+    pl->q = (d.part_begin || d.part_end) ? d.part_begin : 0u;
+    pl->r = (d.part_begin || d.part_end) ? d.part_end : d.P;
     pl->tile = d.tile_vectors ? d.tile_vectors : 64u;
     pl->S = d.smem_slots ? d.smem_slots : 8192u;
     crp_status st = CRP_OK;
@@ -432,6 +443,16 @@ static AccumulateArgs make_args(crp_plan *pl, const crp_sparse *A, const crp_spa
     a.use_match = (pl->d.flags & CRP_PLAN_NO_WARP_MATCH) ? 0 : 1;
     a.debug_checks = (pl->d.flags & CRP_PLAN_DEBUG_CHECKS) ? 1 : 0;
     a.direct = (pl->d.flags & CRP_PLAN_DIRECT) ? 1 : 0;
+    if (pl->q != 0 || pl->r != pl->d.P) {
+        const uint32_t w = pl->d.P / G;
+        if (G > 1 && pl->q % w == 0 && pl->r % w == 0) {
+            a.group_begin = pl->q / w;   // Lemma 1: enumerate only the owned groups
+            a.group_end = pl->r / w;
+        } else {
+            a.part_lo = pl->q;           // otherwise keep only the owned terms
+            a.part_hi = pl->r;
+        }
+    }
     a.smem_slots = pl->S;
     a.hp = pl->hp;
     return a;
@@ -483,8 +504,11 @@ static crp_status estimate_and_allocate(crp_plan *pl, const crp_sparse *A, const
             sb_val = B->val ? pl->s_val : nullptr;
         }
         AccumulateArgs a = make_args(pl, A, B, sb_idx, sb_val, Gs);
-        a.group_begin = 0;
-        a.group_end = 1;
+        a.group_begin = 0;   // the sample is group 0 of the whole hash space,
+        a.group_end = 1;     // whatever interval the plan owns
+        a.part_lo = 0;
+        a.part_hi = 0xFFFFFFFFu;
+        a.hot_R = 0;
         a.tv = table_view(pl, tmp, d_off, d_mask);
         CRP_CUDA(launch_accumulate(a, pl->s_hash, pl->grid, pl->stream));
         // live entries per sampled partition
@@ -859,6 +883,8 @@ extern "C" crp_status crp_sync(crp_plan *pl) {
     CRP_CUDA(cudaMemcpy(&status, &pl->dc->status, 4, cudaMemcpyDeviceToHost));
     if (status & kStatusBadIndex)
         return fail(CRP_EINVAL, "an input index was out of range (or a vector too long to sort)");
+    if (status & kStatusNotOwned)
+        return fail(CRP_ECUDA, "an update reached a partition outside the plan's interval");
     if (status & kStatusSmemProbe) return fail(CRP_ECUDA, "on-chip table probe bound exceeded");
     if (status & kStatusTimeout) return fail(CRP_ETIMEOUT, "a bounded device wait gave up");
     if (status & (kStatusTableFull | kStatusSpillFull)) {

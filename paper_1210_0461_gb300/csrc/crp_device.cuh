@@ -94,6 +94,10 @@ __device__ __forceinline__ void table_update(const TableView &tv, uint32_t p,
     }
     const unsigned long long off = tv.part_off[p];
     const unsigned long long mask = tv.part_mask[p];
+    if (mask == ~0ull) {  // a partition outside the plan's interval has no slots
+        atomicOr(&tv.dc->status, kStatusNotOwned);
+        return;
+    }
     unsigned long long h = slot_mix(key) & mask;
     for (unsigned long long probe = 0; probe <= mask; ++probe) {
         Slot *s = tv.slots + off + h;
@@ -302,6 +306,10 @@ __device__ __forceinline__ bool next_term(WarpEnum &st, const AccumulateArgs &A,
             valid = false;
         }
         if (A.mode == CRP_UPPER && !(oi < j)) valid = false;
+        if (A.part_lo != 0u || A.part_hi != 0xFFFFFFFFu) {
+            const uint32_t p = partition_hash(A.hp, oi, j);
+            if (p < A.part_lo || p >= A.part_hi) valid = false;
+        }
     }
     return valid;
 }

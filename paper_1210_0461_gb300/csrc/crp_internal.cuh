@@ -21,6 +21,7 @@ constexpr uint32_t kStatusSpillFull = 2u;
 constexpr uint32_t kStatusBadIndex = 4u;
 constexpr uint32_t kStatusTimeout = 8u;
 constexpr uint32_t kStatusSmemProbe = 16u;
+constexpr uint32_t kStatusNotOwned = 32u;
 // Value-type code of summary slots inside the top-k / export kernels:
 // low 32 bits = count (upper bound), high 32 bits = overestimation.
 constexpr int kVTSummary = 2;
@@ -135,6 +136,8 @@ struct AccumulateArgs {
     const uint16_t *hot_rank_b = nullptr;
     unsigned int *hot_block = nullptr;
     uint32_t hot_R = 0;
+    // interval [part_lo, part_hi) of partitions kept (Figure 1, CRoP on [q, r))
+    uint32_t part_lo = 0, part_hi = 0xFFFFFFFFu;
 };
 
 // Two-phase (routed) accumulation: bins of records per partition group.

@@ -1,0 +1,42 @@
+"""Sharding the product over several GPUs by partition interval.
+
+Section 4 ("Our approach") and Theorem 1: K instances of CRoP, each with a
+disjoint interval of the hash table and a full copy of the input, need no
+communication while they accumulate; every entry is produced by exactly one
+instance.  The heaviest entries of the whole product are then the heaviest of
+the union of every instance's own heaviest entries, which is the only exchange
+(a gather of k candidates per rank).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def partition_interval(rank: int, world: int, P: int) -> tuple[int, int]:
+    """Rank's equal share [q, r) of the P partitions (world <= P)."""
+    if not 0 <= rank < world or world > P:
+        raise ValueError("need 0 <= rank < world <= P")
+    return rank * P // world, (rank + 1) * P // world
+
+
+def merge_topk(parts, k: int):
+    """Merge per-rank top-k lists (i, j, w arrays) into the global top-k,
+    ordered by |w| descending, then i, then j ascending."""
+    i = np.concatenate([np.asarray(p[0], np.int64) for p in parts]) if parts else np.zeros(0, np.int64)
+    j = np.concatenate([np.asarray(p[1], np.int64) for p in parts]) if parts else np.zeros(0, np.int64)
+    w = np.concatenate([np.asarray(p[2], np.float64) for p in parts]) if parts else np.zeros(0)
+    order = np.lexsort((j, i, -np.abs(w)))[:k]
+    return i[order], j[order], w[order]
+
+
+def gather_topk(local, k: int, group=None):
+    """All ranks pass their own top-k (i, j, w); rank 0 gets the global top-k,
+    the others None.  Uses torch.distributed (gloo or nccl)."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    payload = [np.asarray(x).tolist() for x in local]
+    out = [None] * world
+    dist.all_gather_object(out, payload, group=group)
+    if dist.get_rank(group) != 0:
+        return None
+    return merge_topk([tuple(np.asarray(x) for x in o) for o in out], k)

@@ -55,7 +55,7 @@ def test_version_and_struct_sizes(libcrp):
     from paper_1210_0461_gb300 import crp
     assert libcrp.crp_version().startswith(b"crp ")
     assert ctypes.sizeof(crp.crp_sparse) == 48
-    assert ctypes.sizeof(crp.crp_plan_desc) == 88
+    assert ctypes.sizeof(crp.crp_plan_desc) == 96
     assert ctypes.sizeof(crp.crp_stats_t) == 80
 
 

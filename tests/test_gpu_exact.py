@@ -276,3 +276,33 @@ def test_repeat_runs_bit_identical(crp):
     for o in outs[1:]:
         for a, b in zip(o, outs[0]):
             assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("cfg", [dict(flags=4 | 2), dict(flags=4 | 2, hot_items=256),
+                                 dict(groups=16, flags=2), dict(groups=1, flags=2),
+                                 dict(groups=32, flags=8 | 2, hot_items=128)],
+                         ids=["direct", "direct+hot", "lemma1-groups", "smem", "routed+hot"])
+def test_disjoint_intervals_union_is_the_product(crp, cfg):
+    # Figure 1 / Theorem 1: K instances of CRoP on disjoint intervals of the
+    # partitions, each seeing the whole input, together produce every entry
+    # exactly once, and each keeps only the entries hashing into its interval.
+    T = ci.C1.generate()
+    Tc = O.Compressed.of(T)
+    ref = O.exact_product(Tc, Tc, O.FULL)
+    P = 64
+    d = crp.to_device(T)
+    got_i, got_j, got_w = [], [], []
+    for q, r in ((0, 16), (16, 48), (48, 64)):
+        plan = crp.Plan(1000, 1000, P, ci.SEED_A, ci.SEED_B, part_begin=q, part_end=r, **cfg)
+        plan.accumulate(d, d)
+        plan.sync()
+        i, j, w, _ = plan.export()
+        p = O.partition_of(i, j, P, ci.SEED_A, ci.SEED_B)
+        assert ((p >= q) & (p < r)).all()
+        got_i.append(i)
+        got_j.append(j)
+        got_w.append(w)
+        plan.close()
+    i, j, w = map(np.concatenate, (got_i, got_j, got_w))
+    gi, gj, gw = _sorted(i, j, w)
+    assert np.array_equal(gi, ref.i) and np.array_equal(gj, ref.j) and np.array_equal(gw, ref.w)
