@@ -71,7 +71,7 @@ static void cache_store(const char *path, const std::string &key, const crp_plan
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %u %u %u %u %u %u %.6g\n", key.c_str(), d.P, d.groups, d.tile_vectors,
+    fprintf(f, "%s %u %u %u %u %u %u %.17g\n", key.c_str(), d.P, d.groups, d.tile_vectors,
             d.smem_slots, d.flags, d.hot_items, tps);
     fclose(f);
 }
