@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5"], default="c2",
+                    help="c2 is the graded line; the others report the remaining workloads")
+    ap.add_argument("--c5-problems", type=int, default=4096)
+    ap.add_argument("--c5-mmax", type=int, default=200_000)
     return ap.parse_args()
 
 
@@ -202,10 +206,239 @@ def run_reference(args):
                 "d2h_bytes_per_step": 0}}), flush=True)
 
 
+def _timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / steps
+
+
+def _line(value, ms, args, dtype, config, extra=None):
+    out = {"metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config}
+    out.update(extra or {})
+    print(json.dumps(out), flush=True)
+
+
+def run_other(args):
+    """The remaining workloads, one JSON line each (not the graded line)."""
+    import numpy as np
+    import torch
+    import crp_inputs as ci
+    import paper_1210_0461_gb300 as pkg
+    pkg.build()
+    from paper_1210_0461_gb300 import crp
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    if args.workload == "c1":
+        T = ci.C1.generate()
+        d = crp.to_device(T)
+        terms = int((T.lengths().astype(np.int64) ** 2).sum())
+        plan = crp.Plan(T.n_minor, T.n_minor, 64, ci.SEED_A, ci.SEED_B, flags=crp.CRP_PLAN_DIRECT,
+                        stream=stream)
+
+        def step():
+            plan.reset()
+            plan.accumulate(d, d)
+            plan.sync()
+            plan.topk(1000, upper=True)
+        ms = _timed(step, args.steps, args.warmup, stream)
+        _line(terms / (ms / 1e3), ms, args, "i32",
+              {"workload": "c1: 20000 transactions x 1000 items, Poisson(10) in [2,40], "
+                           "Zipf(1.1); exact T^T T, P = 64, direct updates",
+               "terms_per_step": terms, "accumulate_ms": plan.timing()[0]})
+    elif args.workload == "c3":
+        A, At = ci.c3()
+        dA, dAt = crp.to_device(A), crp.to_device(At)
+        terms = int((A.lengths().astype(np.int64) * At.lengths().astype(np.int64)).sum())
+        kw, tps = crp.autotune(dA, dAt, A.n_minor, At.n_minor, ci.SEED_A, ci.SEED_B,
+                               value_type=crp.CRP_F32_COMP, stream=stream)
+        plan = crp.Plan(A.n_minor, At.n_minor, seed_a=ci.SEED_A, seed_b=ci.SEED_B,
+                        value_type=crp.CRP_F32_COMP, auto_grow=True, stream=stream, **kw)
+
+        def step():
+            plan.reset()
+            plan.accumulate(dA, dAt)
+            plan.sync()
+            plan.topk(1000)
+        ms = _timed(step, args.steps, args.warmup, stream)
+        st = plan.stats()
+        _line(terms / (ms / 1e3), ms, args, "f32/f64",
+              {"workload": "c3: C = A A, A 100000 x 100000 column-stochastic, column nnz ~ "
+                           "c^-2.1 on [5,2000], lognormal values; fp32 products, compensated "
+                           "fp32 on chip, fp64 entries",
+               "terms_per_step": terms, "entries": st["entries"], "autotune": kw,
+               "accumulate_ms": plan.timing()[0]})
+    elif args.workload == "c4":
+        run_c4(args, np, torch, crp, ci, stream)
+    else:
+        run_c5(args, np, torch, crp, ci, stream)
+
+
+def run_c4(args, np, torch, crp, ci, stream):
+    """Heavy-entry mode: per-partition summaries with 2^20 counters over P = 256
+    partitions (pairs i < j): plain, and with 2^16 reserved exact counters chosen
+    by the product of marginals or by the trained network.  Top-1000 weight
+    error against the GPU exact product (pinned bit-exact to the oracle by the
+    tests)."""
+    w4 = ci.C4
+    T = w4.generate()
+    n = T.n_minor
+    d = crp.to_device(T)
+    m_pre = T.n_major // 100
+    pre = crp.to_device(ci.Sparse(T.ptr[:m_pre + 1], T.idx[:T.ptr[m_pre]], None, n))
+    L = T.lengths().astype(np.int64)
+    terms = int((L * (L - 1) // 2).sum())
+    ex = crp.Plan(n, n, 1024, ci.SEED_A, ci.SEED_B, mode=crp.CRP_UPPER, flags=crp.CRP_PLAN_ROUTED,
+                  groups=128, hot_items=4096, auto_grow=True, stream=stream)
+    ex.accumulate(d, d)
+    ex.sync()
+    exact_ms = ex.timing()[0]
+    ri, rj, rw, _ = ex.topk(1000, upper=True)
+    truth = dict(zip((ri.astype(np.int64) * n + rj).tolist(), rw.tolist()))
+    top_sum = rw.sum()
+
+    def true_weight(ti, tj):
+        # weights of returned pairs outside the exact top-1000 come from the
+        # exact tables (export of their partitions)
+        out = 0.0
+        miss = {}
+        for a, b in zip(ti.tolist(), tj.tolist()):
+            k = a * n + b
+            if k in truth:
+                out += truth[k]
+            else:
+                miss.setdefault(ex.partition_of(a, b), []).append(k)
+        for p, ks in miss.items():
+            i, j, w, _ = ex.export(p, p + 1)
+            look = dict(zip((i.astype(np.int64) * n + j).tolist(), w.tolist()))
+            out += sum(look.get(k, 0.0) for k in ks)
+        return out
+
+    # network trained on a separate stream of the same recipe; labels are the
+    # exact pair counts of that stream (GPU exact product)
+    tr = ci.transactions(w4.seed + 17, 1_000_000, n, w4.lam, w4.lmin, w4.lmax, w4.zipf_s)
+    dtr = crp.to_device(tr)
+    ep = crp.Plan(n, n, 256, ci.SEED_A, ci.SEED_B, mode=crp.CRP_UPPER, flags=crp.CRP_PLAN_DIRECT,
+                  auto_grow=True, stream=stream)
+    ep.accumulate(dtr, dtr)
+    ep.sync()
+    ei, ej, ew, _ = ep.export()
+    ep.close()
+    keys = ei.astype(np.int64) * n + ej
+    o = np.argsort(keys)
+    keys, ew = keys[o], ew[o]
+    R = 2048
+    m_tp = tr.n_major // 100
+    cpre = crp.to_device(ci.Sparse(tr.ptr[:m_tp + 1], tr.idx[:tr.ptr[m_tp]], None, n))
+    cI, cJ, X = crp.candidate_pairs(cpre, n, R)
+    ck = cI.cpu().numpy().astype(np.int64) * n + cJ.cpu().numpy()
+    pos = np.minimum(np.searchsorted(keys, ck), len(keys) - 1)
+    y = np.log1p(np.where(keys[pos] == ck, ew[pos], 0.0))
+    Y = torch.tensor(y / max(y.max(), 1e-9), dtype=torch.float32, device="cuda")
+    params = crp.mlp_init(7)
+    trainer = crp.MLPTrainer(params, lr=3e-3)
+    t0 = time.time()
+    losses = [trainer.step(X, Y) for _ in range(300)]
+    train_s = time.time() - t0
+    results = {}
+    for name, prm, reserve in (("plain", None, False), ("product_of_marginals", None, True),
+                               ("predictor", params, True)):
+        plan = crp.Plan(n, n, 256, ci.SEED_A, ci.SEED_B, mode=crp.CRP_UPPER,
+                        summary_counters=1 << 20, reserved_counters=(1 << 16) if reserve else 0,
+                        stream=stream)
+        t0 = time.time()
+        if reserve:
+            crp.predict_reserve(plan, pre, n, prm, R, 1 << 16)
+        predict_s = time.time() - t0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.accumulate(d, d)
+        plan.sync()
+        ti, tj, tw, tl = plan.topk(1000, upper=True)
+        wall = time.perf_counter() - t0
+        err = 1.0 - true_weight(ti, tj) / top_sum
+        results[name] = {"terms_per_s": terms / wall, "seconds": wall,
+                         "accumulate_kernel_ms": plan.timing()[0], "top1000_weight_err": err,
+                         "predict_reserve_s": predict_s}
+        plan.close()
+    best = results["predictor"]
+    _line(best["terms_per_s"], best["seconds"] * 1e3, args, "u32 counters",
+          {"workload": "c4: 50M transactions x 1M items, Poisson(15), Zipf(1.2); pairs i < j; "
+                       "2^20 counters per partition, P = 256, 2^16 reserved counters",
+           "terms_per_step": terms, "exact_reference_ms": exact_ms,
+           "training": {"samples": int(len(y)), "steps": 300, "first_loss": losses[0],
+                        "last_loss": losses[-1], "seconds": train_s},
+           "variants": results})
+    ex.close()
+
+
+def run_c5(args, np, torch, crp, ci, stream):
+    """Batched: many independent co-occurrence problems in one persistent,
+    graph-captured launch, against one launch per problem."""
+    ws = ci.c5_params(args.c5_problems, m_range=(100, args.c5_mmax))
+    t0 = time.time()
+    Ts = [w.generate() for w in ws]
+    gen_s = time.time() - t0
+    dev = [crp.to_device(T) for T in Ts]
+    terms = sum(int((T.lengths().astype(np.int64) ** 2).sum()) for T in Ts)
+    batch = crp.Batch([(x, x) for x in dev], 256, ci.SEED_A, ci.SEED_B, tile_vectors=32,
+                      stream=stream)
+    info = batch.info()
+
+    def step():
+        batch.run()
+        batch.sync()
+    ms = _timed(step, args.steps, args.warmup, stream)
+    ev_ms, ev_terms = batch.sync()
+    entries = [batch.count(q) for q in range(len(Ts))]
+    batch.close()
+    del batch
+    # baseline: one plan per problem, launched back to back (plans built first,
+    # each sized from its problem's entry count)
+    plans = [crp.Plan(T.n_minor, T.n_minor, 256, ci.SEED_A, ci.SEED_B, flags=crp.CRP_PLAN_DIRECT,
+                      capacity_hint=int(e / 0.6) + 256 * 64, stream=stream)
+             for T, e in zip(Ts, entries)]
+    for p, x in zip(plans, dev):
+        p.accumulate(x, x)
+    for p in plans:
+        p.sync()
+
+    def per_problem():
+        for p, x in zip(plans, dev):
+            p.reset()
+            p.accumulate(x, x)
+        for p in plans:
+            p.sync()
+    ms_pp = _timed(per_problem, max(1, args.steps // 2), 1, stream)
+    for p in plans:
+        p.close()
+    _line(terms / (ms / 1e3), ms, args, "i32",
+          {"workload": f"c5: {len(ws)} problems, transactions log-U[100,{args.c5_mmax}], items "
+                       "log-U[1e3,1e5], Zipf s ~ U[0.8,1.3], Poisson(12); exact T^T T each, "
+                       "one persistent graph-captured launch",
+           "terms_per_step": terms, "table_slots": info["table_slots"],
+           "entries": int(sum(entries)), "generation_s": gen_s},
+          {"one_launch_per_problem": {"terms_per_s": terms / (ms_pp / 1e3), "ms": ms_pp},
+           "speedup_vs_per_problem": ms_pp / ms})
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "c2":
+        run_other(args)
         return
     import numpy as np
     import torch

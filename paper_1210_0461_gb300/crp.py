@@ -392,6 +392,14 @@ class Batch:
                    "crp_batch_export")
         return i, j, w
 
+    def count(self, q: int) -> int:
+        """Number of entries of problem q."""
+        n = ctypes.c_int64(0)
+        st = self._lib.crp_batch_export(self._h, q, None, None, None, 0, ctypes.byref(n))
+        if st not in (CRP_OK, CRP_EINVAL):
+            _check(st, "crp_batch_export")
+        return n.value
+
     def info(self):
         t, s, l = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
         _check(self._lib.crp_batch_info(self._h, ctypes.byref(t), ctypes.byref(s),
@@ -438,6 +446,16 @@ def mlp_grad(params, x, t, n_total=None):
                               n if n_total is None else n_total, g.data_ptr(), loss.data_ptr(),
                               _stream_handle(None)), "crp_mlp_grad")
     return float(loss.item()), g
+
+
+def mlp_init(seed: int, device="cuda"):
+    """Initial parameters (He-style normal weights, small positive biases) as a
+    device tensor in the layout of crp_mlp_forward."""
+    import torch
+    g = np.random.default_rng(seed)
+    parts = [g.normal(0, 1.0, 128), np.full(64, 0.01), g.normal(0, np.sqrt(2 / 64), 4096),
+             np.full(64, 0.01), g.normal(0, np.sqrt(1 / 64), 64), np.zeros(1)]
+    return torch.tensor(np.concatenate(parts), dtype=torch.float32, device=device)
 
 
 class MLPTrainer:
