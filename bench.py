@@ -298,7 +298,8 @@ def run_c4(args, np, torch, crp, ci, stream):
     pre = crp.to_device(ci.Sparse(T.ptr[:m_pre + 1], T.idx[:T.ptr[m_pre]], None, n))
     L = T.lengths().astype(np.int64)
     terms = int((L * (L - 1) // 2).sum())
-    ex = crp.Plan(n, n, 1024, ci.SEED_A, ci.SEED_B, mode=crp.CRP_UPPER, flags=crp.CRP_PLAN_ROUTED,
+    ex = crp.Plan(n, n, 1024, ci.SEED_A, ci.SEED_B, mode=crp.CRP_UPPER,
+                  flags=crp.CRP_PLAN_ROUTED | crp.CRP_PLAN_SORTED_ROWS,
                   groups=128, hot_items=4096, auto_grow=True, stream=stream)
     ex.accumulate(d, d)
     ex.sync()
@@ -355,7 +356,7 @@ def run_c4(args, np, torch, crp, ci, stream):
                                ("predictor", params, True)):
         plan = crp.Plan(n, n, 256, ci.SEED_A, ci.SEED_B, mode=crp.CRP_UPPER,
                         summary_counters=1 << 20, reserved_counters=(1 << 16) if reserve else 0,
-                        stream=stream)
+                        flags=crp.CRP_PLAN_SORTED_ROWS, stream=stream)
         t0 = time.time()
         if reserve:
             crp.predict_reserve(plan, pre, n, prm, R, 1 << 16)

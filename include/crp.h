@@ -68,6 +68,10 @@ enum { CRP_PLAN_NO_WARP_MATCH = 1,  /* skip __match_any_sync pre-combining */
        CRP_PLAN_DIRECT = 4,         /* no on-chip combining table: every
                                        (warp-combined) term updates its
                                        partition table in HBM directly */
+       CRP_PLAN_SORTED_ROWS = 16,   /* the caller guarantees every vector's
+                                       indices are distinct and ascending: with
+                                       CRP_UPPER and A, B the same arrays (T^T T)
+                                       only the pairs i < j are enumerated */
        CRP_PLAN_ROUTED = 8 };       /* two phases: enumerate every term once
                                        into per-partition-group bins, then
                                        apply the bins group by group so each

@@ -24,6 +24,7 @@ CRP_I32, CRP_F32_COMP = 0, 1
 CRP_FULL, CRP_UPPER = 0, 1
 CRP_TOPK_UPPER = 1
 CRP_PLAN_NO_WARP_MATCH, CRP_PLAN_DEBUG_CHECKS, CRP_PLAN_DIRECT, CRP_PLAN_ROUTED = 1, 2, 4, 8
+CRP_PLAN_SORTED_ROWS = 16
 
 
 class CrpError(RuntimeError):

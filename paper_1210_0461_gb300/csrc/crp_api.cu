@@ -112,6 +112,7 @@ struct crp_plan {
     SpillRec *d_spill2 = nullptr;
     unsigned long long res_off = 0, res_mask = 0;
     unsigned long long *d_res_keys = nullptr;
+    unsigned int *d_res_bits = nullptr;  // row bits then column bits
     int32_t n_res = 0;
     // hot block (direct mode)
     uint32_t hot_R = 0;
@@ -208,8 +209,12 @@ static crp_status alloc_summary(crp_plan *pl) {
     CRP_CUDA(cudaMalloc(&pl->d_spill2, pl->spill_cap * sizeof(SpillRec)));
     pl->ctmp_grid = (int)std::min<uint32_t>(P, (uint32_t)pl->sm_count);
     CRP_CUDA(cudaMalloc(&pl->d_ctmp, (size_t)pl->ctmp_grid * pl->ell * sizeof(Slot)));
-    if (pl->d.reserved_counters)
+    if (pl->d.reserved_counters) {
         CRP_CUDA(cudaMalloc(&pl->d_res_keys, (size_t)pl->d.reserved_counters * 8));
+        const size_t words = (size_t)(pl->d.n_rows + 31) / 32 + (size_t)(pl->d.n_cols + 31) / 32;
+        CRP_CUDA(cudaMalloc(&pl->d_res_bits, words * 4));
+        CRP_CUDA(cudaMemsetAsync(pl->d_res_bits, 0, words * 4, pl->stream));
+    }
     pl->tables_ready = true;
     return CRP_OK;
 }
@@ -328,6 +333,7 @@ extern "C" void crp_plan_destroy(crp_plan *pl) {
     cudaFree(pl->d_ctmp);
     cudaFree(pl->d_spill2);
     cudaFree(pl->d_res_keys);
+    cudaFree(pl->d_res_bits);
     cudaFree(pl->bins);
     cudaFree(pl->d_bin_off);
     cudaFree(pl->d_bin_cap);
@@ -419,6 +425,10 @@ static TableView table_view(crp_plan *pl, Slot *slots, const unsigned long long 
     tv.res_off = pl->res_off;
     tv.res_mask = pl->res_mask;
     tv.has_reserved = (pl->summary && pl->n_res > 0) ? 1 : 0;
+    if (pl->d_res_bits) {
+        tv.res_bits_a = pl->d_res_bits;
+        tv.res_bits_b = pl->d_res_bits + (pl->d.n_rows + 31) / 32;
+    }
     return tv;
 }
 
@@ -443,6 +453,10 @@ static AccumulateArgs make_args(crp_plan *pl, const crp_sparse *A, const crp_spa
     a.use_match = (pl->d.flags & CRP_PLAN_NO_WARP_MATCH) ? 0 : 1;
     a.debug_checks = (pl->d.flags & CRP_PLAN_DEBUG_CHECKS) ? 1 : 0;
     a.direct = (pl->d.flags & CRP_PLAN_DIRECT) ? 1 : 0;
+    // T^T T above the diagonal with A and B the same sorted lists: enumerate
+    // only j after i (rows must hold distinct ascending indices)
+    a.sym_upper = (pl->d.mode == CRP_UPPER && G == 1 && A->ptr == B->ptr && A->idx == B->idx &&
+                   b_idx == B->idx && (pl->d.flags & CRP_PLAN_SORTED_ROWS)) ? 1 : 0;
     if (pl->q != 0 || pl->r != pl->d.P) {
         const uint32_t w = pl->d.P / G;
         if (G > 1 && pl->q % w == 0 && pl->r % w == 0) {
@@ -545,12 +559,13 @@ static crp_status select_hot_items(crp_plan *pl, const crp_sparse *A, const crp_
 
 // Compact every partition holding more than ell keys, then re-insert spilled
 // updates (each re-insert may spill again when a partition refills; repeat).
-static crp_status summary_settle(crp_plan *pl) {
+static crp_status summary_settle(crp_plan *pl, bool final) {
     const uint32_t P = pl->d.P;
+    const uint32_t trigger = final ? pl->ell : pl->ell + (3u * pl->ell) / 4u;
     for (int round = 0; round < 256; ++round) {
         CRP_CUDA(launch_summary_compact(pl->slots, pl->d_off, pl->d_mask, pl->d_live, pl->d_floor,
-                                        nullptr, P, pl->ell, pl->d_ctmp, pl->ctmp_grid,
-                                        pl->stream));
+                                        nullptr, P, pl->ell, round == 0 ? trigger : pl->ell,
+                                        pl->d_ctmp, pl->ctmp_grid, pl->stream));
         pl->launches += 1;
         unsigned long long n_spill = 0;
         CRP_CUDA(cudaMemcpyAsync(&n_spill, &pl->dc->spill_n, 8, cudaMemcpyDeviceToHost, pl->stream));
@@ -577,7 +592,9 @@ static crp_status summary_accumulate(crp_plan *pl, const crp_sparse *A, const cr
     CRP_CUDA(cudaMemcpyAsync(&terms, pl->d_scratch64, 8, cudaMemcpyDeviceToHost, pl->stream));
     CRP_CUDA(cudaStreamSynchronize(pl->stream));
     pl->launches += 1;
-    const uint64_t chunk_terms = std::max<uint64_t>((uint64_t)P * pl->ell, 1);
+    // about ell / 4 new keys per partition per chunk at most, within the
+    // headroom between the compaction trigger (7/4 ell) and the cap (2 ell)
+    const uint64_t chunk_terms = std::max<uint64_t>((uint64_t)P * pl->ell / 4, 1);
     const uint64_t n_chunks = std::max<uint64_t>((terms + chunk_terms - 1) / chunk_terms, 1);
     const int64_t K = A->n_major;
     const int64_t kstep = (K + (int64_t)n_chunks - 1) / (int64_t)n_chunks;
@@ -597,7 +614,7 @@ static crp_status summary_accumulate(crp_plan *pl, const crp_sparse *A, const cr
         CRP_CUDA(launch_accumulate(a, nullptr, pl->grid_direct, pl->stream));
         CRP_CUDA(cudaEventRecord(pl->ev1, pl->stream));
         pl->launches += 1;
-        crp_status st = summary_settle(pl);
+        crp_status st = summary_settle(pl, k1 == K);
         if (st != CRP_OK) return st;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, pl->ev0, pl->ev1) == cudaSuccess) total_ms += ms;
@@ -1148,7 +1165,9 @@ extern "C" crp_status crp_reserve(crp_plan *pl, const uint64_t *keys, int32_t n)
                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, pl->stream));
     CRP_CUDA(launch_reserve_insert(pl->slots, pl->res_off, pl->res_mask, pl->d_res_keys + pl->n_res,
                                    n, pl->stream));
-    pl->launches += 1;
+    CRP_CUDA(launch_reserve_bits(pl->d_res_keys + pl->n_res, n, pl->d_res_bits,
+                                 pl->d_res_bits + (pl->d.n_rows + 31) / 32, pl->stream));
+    pl->launches += 2;
     pl->n_res += n;
     CRP_CUDA(cudaStreamSynchronize(pl->stream));
     return CRP_OK;

@@ -40,7 +40,9 @@ __device__ __forceinline__ void spill_update(const TableView &tv, unsigned long 
 // Reserved keys (exact counters) are looked up first.
 __device__ __forceinline__ void summary_update(const TableView &tv, uint32_t p,
                                                unsigned long long key, unsigned long long v) {
-    if (tv.has_reserved) {
+    if (tv.has_reserved &&
+        ((tv.res_bits_a[(uint32_t)(key >> 32) >> 5] >> ((uint32_t)(key >> 32) & 31)) & 1u) &&
+        ((tv.res_bits_b[(uint32_t)key >> 5] >> ((uint32_t)key & 31)) & 1u)) {
         unsigned long long h = slot_mix(key) & tv.res_mask;
         for (unsigned long long probe = 0; probe <= tv.res_mask; ++probe) {
             const Slot *s = tv.slots + tv.res_off + h;
@@ -178,7 +180,7 @@ __device__ __forceinline__ void smem_add_comp(unsigned long long *cell, float p,
 
 struct WarpEnum {
     int64_t k, k_hi;
-    int64_t a_cur, a_end;
+    int64_t a_cur, a_end, a_beg;
     int64_t b_beg;
     int32_t b_len;
     // this lane's a entry of the current batch of 32
@@ -213,7 +215,11 @@ __device__ __forceinline__ void load_batch(WarpEnum &st, const AccumulateArgs &A
         st.my_i = (uint32_t)__ldg(A.a_idx + idx);
         if (A.hot_rank_a) st.my_rank = __ldg(A.hot_rank_a + st.my_i);
         if (A.a_val) st.my_wa = __ldg(A.a_val + idx);
-        if (A.groups == 1) {
+        if (A.sym_upper) {
+            st.lo1 = (int32_t)(idx - st.a_beg) + 1;
+            st.n1 = st.b_len - st.lo1;
+            c = st.n1 > 0 ? st.n1 : 0;
+        } else if (A.groups == 1) {
             st.n1 = st.b_len;
             c = st.b_len;
         } else {
@@ -266,6 +272,7 @@ __device__ __forceinline__ bool advance(WarpEnum &st, const AccumulateArgs &A,
         int64_t b0 = __ldg(A.b_ptr + st.k), b1 = __ldg(A.b_ptr + st.k + 1);
         if (a1 == a0 || b1 == b0) continue;
         st.a_cur = a0;
+        st.a_beg = a0;
         st.a_end = a1;
         st.b_beg = b0;
         st.b_len = (int32_t)(b1 - b0);

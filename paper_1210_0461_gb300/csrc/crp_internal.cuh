@@ -105,6 +105,8 @@ struct TableView {
     // reserved exact counters probed before the summaries (0 slots = none)
     unsigned long long res_off = 0, res_mask = 0;  // [res_off, res_off + res_mask + 1)
     int has_reserved = 0;
+    // items that occur in a reserved key (bit per index): other pairs skip the probe
+    const unsigned int *res_bits_a = nullptr, *res_bits_b = nullptr;
 };
 
 struct AccumulateArgs {
@@ -138,6 +140,9 @@ struct AccumulateArgs {
     uint32_t hot_R = 0;
     // interval [part_lo, part_hi) of partitions kept (Figure 1, CRoP on [q, r))
     uint32_t part_lo = 0, part_hi = 0xFFFFFFFFu;
+    // pairs i < j of T^T T with a_k == b_k (same sorted list): the window of
+    // the a entry at position x starts at position x + 1 of b_k
+    int sym_upper = 0;
 };
 
 // Two-phase (routed) accumulation: bins of records per partition group.
@@ -157,7 +162,10 @@ size_t route_smem_bytes(int value_type, uint32_t B, uint32_t R_s);
 cudaError_t launch_summary_compact(Slot *slots, const unsigned long long *part_off,
                                    const unsigned long long *part_mask, unsigned int *live,
                                    unsigned int *floor, const unsigned int *todo, uint32_t n_todo,
-                                   uint32_t ell, Slot *tmp, int grid, cudaStream_t s);
+                                   uint32_t ell, uint32_t trigger, Slot *tmp, int grid,
+                                   cudaStream_t s);
+cudaError_t launch_reserve_bits(const unsigned long long *keys, int32_t n, unsigned int *bits_a,
+                                unsigned int *bits_b, cudaStream_t s);
 cudaError_t launch_reserve_insert(Slot *slots, unsigned long long res_off,
                                   unsigned long long res_mask, const unsigned long long *keys,
                                   int32_t n, cudaStream_t s);

@@ -10,6 +10,9 @@
 //     floor bounds the weight of every unrecorded key of the partition;
 //   * k_summary_compact keeps the ell keys of largest count, raises the
 //     floor to the ell-th largest count and rebuilds the table.
+// Between compactions a partition may hold up to 2*ell keys (more counters
+// only sharpen the estimates); it is compacted once it holds more than
+// 7/4 ell, and every partition is compacted to ell at the end of each call.
 // Each compaction drops at least as many keys as were added since the last
 // one, each with count >= the old floor, so the sum of kept counts never
 // exceeds the partition's stream weight W; hence floor <= W / ell, every
@@ -30,13 +33,14 @@ __device__ __forceinline__ unsigned int slot_count(const Slot &s) { return (unsi
 __global__ void __launch_bounds__(kCompactThreads)
 k_summary_compact(Slot *slots, const unsigned long long *part_off,
                   const unsigned long long *part_mask, unsigned int *live, unsigned int *floor,
-                  const unsigned int *todo, uint32_t n_todo, uint32_t ell, Slot *tmp) {
+                  const unsigned int *todo, uint32_t n_todo, uint32_t ell, uint32_t trigger,
+                  Slot *tmp) {
     __shared__ unsigned int hist[2048];
     __shared__ unsigned int sel_digit, need_s, kept_n, tie_n;
     Slot *mine = tmp + (size_t)blockIdx.x * ell;
     for (uint32_t t = blockIdx.x; t < n_todo; t += gridDim.x) {
         const uint32_t p = todo ? todo[t] : t;
-        if (live[p] <= ell) continue;
+        if (live[p] <= trigger) continue;
         const unsigned long long off = part_off[p], cap = part_mask[p] + 1ull;
         // radix select of the ell-th largest count: digits of 11, 11, 10 bits
         unsigned int prefix = 0, pmask = 0;
@@ -112,10 +116,11 @@ k_summary_compact(Slot *slots, const unsigned long long *part_off,
 cudaError_t launch_summary_compact(Slot *slots, const unsigned long long *part_off,
                                    const unsigned long long *part_mask, unsigned int *live,
                                    unsigned int *floor, const unsigned int *todo, uint32_t n_todo,
-                                   uint32_t ell, Slot *tmp, int grid, cudaStream_t s) {
+                                   uint32_t ell, uint32_t trigger, Slot *tmp, int grid,
+                                   cudaStream_t s) {
     if (n_todo == 0) return cudaSuccess;
     k_summary_compact<<<grid, kCompactThreads, 0, s>>>(slots, part_off, part_mask, live, floor,
-                                                       todo, n_todo, ell, tmp);
+                                                       todo, n_todo, ell, trigger, tmp);
     return cudaGetLastError();
 }
 
@@ -139,6 +144,23 @@ cudaError_t launch_reserve_insert(Slot *slots, unsigned long long res_off,
                                   int32_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_reserve_insert<<<(n + 255) / 256, 256, 0, s>>>(slots, res_off, res_mask, keys, n);
+    return cudaGetLastError();
+}
+
+// Mark the row and column indices that occur in reserved keys.
+__global__ void k_reserve_bits(const unsigned long long *keys, int32_t n, unsigned int *bits_a,
+                               unsigned int *bits_b) {
+    for (int32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        const uint32_t i = (uint32_t)(keys[x] >> 32), j = (uint32_t)keys[x];
+        atomicOr(&bits_a[i >> 5], 1u << (i & 31));
+        atomicOr(&bits_b[j >> 5], 1u << (j & 31));
+    }
+}
+
+cudaError_t launch_reserve_bits(const unsigned long long *keys, int32_t n, unsigned int *bits_a,
+                                unsigned int *bits_b, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_reserve_bits<<<(n + 255) / 256, 256, 0, s>>>(keys, n, bits_a, bits_b);
     return cudaGetLastError();
 }
 

@@ -80,11 +80,14 @@ def test_c1_cooccurrence_full_bit_exact(crp, cfg):
     plan.close()
 
 
-def test_c1_upper_and_topk(crp):
+@pytest.mark.parametrize("cfg", [dict(groups=8), dict(flags=4 | 16 | 2), dict(flags=8 | 16 | 2,
+                                                                           hot_items=64)],
+                         ids=["groups", "direct-sorted-rows", "routed-sorted-rows"])
+def test_c1_upper_and_topk(crp, cfg):
     T = ci.C1.generate()
     Tc = O.Compressed.of(T)
     ref = O.exact_product(Tc, Tc, O.UPPER)
-    plan = _run(crp, T, T, 1000, 1000, 64, mode=O.UPPER, groups=8)
+    plan = _run(crp, T, T, 1000, 1000, 64, mode=O.UPPER, **cfg)
     _check_exact(crp, plan, ref, 64)
     assert ref.terms == int((T.lengths() * (T.lengths() - 1) // 2).sum())
     for k in (1, 10, 1000, 5000):

@@ -34,10 +34,10 @@ def _truth(T, P, mode=O.FULL):
     return ref, true, W
 
 
-def _summary_plan(crp, T, P, ell, reserved=0, mode=O.FULL):
+def _summary_plan(crp, T, P, ell, reserved=0, mode=O.FULL, flags=0):
     d = crp.to_device(T)
     plan = crp.Plan(T.n_minor, T.n_minor, P, ci.SEED_A, ci.SEED_B, mode=mode,
-                    summary_counters=ell, reserved_counters=reserved)
+                    summary_counters=ell, reserved_counters=reserved, flags=flags)
     return plan, d
 
 
@@ -148,4 +148,23 @@ def test_summary_streaming_chunks_keep_guarantees(crp):
     p = O.partition_of(i, j, P, ci.SEED_A, ci.SEED_B)
     assert (lo_ <= tv).all() and (tv <= up).all()
     assert ((up - lo_) <= W[p] / ell + 1e-9).all()
+    plan.close()
+
+
+def test_summary_upper_sorted_rows_guarantees(crp):
+    # pairs above the diagonal, enumerated only as j after i (sorted rows)
+    T = ci.C1.generate()
+    P, ell = 16, 128
+    ref, true, W = _truth(T, P, O.UPPER)
+    plan, d = _summary_plan(crp, T, P, ell, mode=O.UPPER, flags=crp.CRP_PLAN_SORTED_ROWS)
+    plan.accumulate(d, d)
+    plan.sync()
+    i, j, up, lo = plan.export()
+    assert (i < j).all()
+    keys = (i.astype(np.int64) * T.n_minor + j).tolist()
+    tv = np.array([true[k] for k in keys])
+    p = O.partition_of(i, j, P, ci.SEED_A, ci.SEED_B)
+    assert (lo <= tv).all() and (tv <= up).all()
+    assert ((up - lo) <= W[p] / ell + 1e-9).all()
+    assert plan.stats()["terms"] == ref.terms
     plan.close()
