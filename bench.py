@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--tile", type=int, default=64)
     ap.add_argument("--smem-slots", type=int, default=8192)
     ap.add_argument("--hot", type=int, default=0, help="hot-block items (direct/routed)")
+    ap.add_argument("--warm", type=int, default=0, help="warm-stripe items (direct/routed)")
     ap.add_argument("--load", type=int, default=0, help="target table load %% (0 = library default)")
     ap.add_argument("--topk", type=int, default=1000)
     ap.add_argument("--no-match", action="store_true")
@@ -484,6 +485,7 @@ def main():
         args.P, args.groups, args.tile, args.smem_slots = (kw["P"], kw["groups"],
                                                            kw["tile_vectors"], kw["smem_slots"])
         args.hot = kw["hot_items"]
+        args.warm = kw.get("warm_items", 0)
         flags = kw["flags"] | (crp.CRP_PLAN_NO_WARP_MATCH if args.no_match else 0)
         args.mode = ("routed" if flags & crp.CRP_PLAN_ROUTED else
                      "direct" if flags & crp.CRP_PLAN_DIRECT else "smem")
@@ -496,8 +498,8 @@ def main():
         q, r = partition_interval(rank, world, args.P)
     plan = crp.Plan(T.n_minor, T.n_minor, args.P, ci.SEED_A, ci.SEED_B, groups=args.groups,
                     tile_vectors=args.tile, smem_slots=args.smem_slots, flags=flags,
-                    hot_items=args.hot, target_load_pct=args.load, auto_grow=True,
-                    part_begin=q, part_end=r, stream=stream)
+                    hot_items=args.hot, warm_items=args.warm, target_load_pct=args.load,
+                    auto_grow=True, part_begin=q, part_end=r, stream=stream)
 
     def step():
         plan.reset()
@@ -600,7 +602,8 @@ def main():
                                    "exact int32 T^T T (all entries), top-1000 pairs",
                        "P": args.P, "groups": args.groups, "tile_vectors": args.tile,
                        "smem_slots": args.smem_slots, "warp_match": not args.no_match,
-                       "mode": args.mode, "hot_items": args.hot, "target_load_pct": args.load,
+                       "mode": args.mode, "hot_items": args.hot, "warm_items": args.warm,
+                       "target_load_pct": args.load,
                        "autotune": tuned,
                        "terms_per_step": terms_step, "entries": entries,
                        "nnz": int(T.nnz), "l2": "inputs (0.8 GB) and tables "
@@ -615,7 +618,8 @@ def main():
                          "frac": achieved / hbm, "traffic": traffic,
                          "kernel": {"direct": "k_accumulate", "smem": "k_accumulate",
                                     "routed": "k_route+k_apply"}[args.mode]
-                                   + ("+k_hot_flush" if args.hot else ""),
+                                   + ("+k_hot_flush" if args.hot else "")
+                                   + ("+k_warm_flush" if args.warm else ""),
                          "kernel_ms": acc,
                          "bytes_model": f"{BYTES_PER_TERM_UPDATE:g} B/term + input + "
                                         f"{SLOT_BYTES:g} B/entry",

@@ -138,7 +138,14 @@ typedef struct {
                                      intervals): only entries with h(i,j) in it
                                      are accumulated and stored.  0, 0 = all.
                                      Exact mode only. */
-    uint32_t _pad2;
+    uint32_t warm_items;          /* CRP_PLAN_DIRECT or CRP_PLAN_ROUTED with
+                                     CRP_I32 only: W > 0 keeps exact dense
+                                     counters for every pair whose row (or
+                                     else column) is among the W most frequent
+                                     (W x n_cols and W x n_rows, in L2),
+                                     after the hot block; W is lowered so the
+                                     stripes fit 64 MB.  Same selection and
+                                     flush as hot_items. */
 } crp_plan_desc;
 
 typedef struct crp_plan crp_plan;

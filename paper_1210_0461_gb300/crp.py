@@ -50,7 +50,7 @@ class crp_plan_desc(ctypes.Structure):
                 ("smem_slots", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("hot_items", ctypes.c_uint32), ("target_load_pct", ctypes.c_uint32),
                 ("part_begin", ctypes.c_uint32), ("part_end", ctypes.c_uint32),
-                ("_pad2", ctypes.c_uint32)]
+                ("warm_items", ctypes.c_uint32)]
 
 
 class crp_stats_t(ctypes.Structure):
@@ -215,7 +215,8 @@ class Plan:
                  tile_vectors: int = 0, smem_slots: int = 0, capacity_hint: int = 0,
                  auto_grow: bool = False, flags: int = 0, stream=None,
                  summary_counters: int = 0, reserved_counters: int = 0, hot_items: int = 0,
-                 target_load_pct: int = 0, part_begin: int = 0, part_end: int = 0):
+                 target_load_pct: int = 0, part_begin: int = 0, part_end: int = 0,
+                 warm_items: int = 0):
         self._lib = lib()
         d = crp_plan_desc()
         d.n_rows, d.n_cols, d.P = n_rows, n_cols, P
@@ -226,6 +227,7 @@ class Plan:
         d.hot_items = hot_items
         d.target_load_pct = target_load_pct
         d.part_begin, d.part_end = part_begin, part_end
+        d.warm_items = warm_items
         d.auto_grow = 1 if auto_grow else 0
         d.groups, d.tile_vectors, d.smem_slots, d.flags = groups, tile_vectors, smem_slots, flags
         self.desc = d
@@ -520,5 +522,6 @@ def autotune(A: DeviceSparse, B: DeviceSparse, n_rows: int, n_cols: int, seed_a:
                               cache_path.encode() if cache_path else None, ctypes.byref(best),
                               ctypes.byref(tps), _stream_handle(stream)), "crp_autotune")
     kw = dict(P=best.P, groups=best.groups, tile_vectors=best.tile_vectors,
-              smem_slots=best.smem_slots, flags=best.flags, hot_items=best.hot_items)
+              smem_slots=best.smem_slots, flags=best.flags, hot_items=best.hot_items,
+              warm_items=best.warm_items)
     return kw, tps.value

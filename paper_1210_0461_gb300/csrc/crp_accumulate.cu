@@ -109,6 +109,7 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
                 int owner;
                 const bool valid = next_term(st, A, lane, VT, oi, j, owa, wb, &owner);
                 const uint32_t orank = __shfl_sync(kFull, st.my_rank, owner);
+                const uint32_t owrank = __shfl_sync(kFull, st.my_wrank, owner);
                 const unsigned long long key = make_key(oi, j);
                 const unsigned act = __ballot_sync(kFull, valid);
                 my_terms += valid ? 1 : 0;
@@ -121,18 +122,9 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
                             lead = lane == __ffs(peers) - 1;
                             cnt = __popc(peers);
                         }
-                        uint32_t hot_slot = 0xFFFFFFFFu;
-                        if (orank < A.hot_R) {
-                            const uint32_t rb = __ldg(A.hot_rank_b + j);
-                            if (rb < A.hot_R) hot_slot = orank * A.hot_R + rb;
-                        }
-                        if (lead) {
-                            if (hot_slot != 0xFFFFFFFFu) {
-                                atomicAdd(&A.hot_block[hot_slot], cnt);
-                            } else {
-                                table_update(A.tv, partition_hash(A.hp, oi, j), key, cnt);
-                                ++flushed;
-                            }
+                        if (lead && !dense_tiers(A, orank, owrank, oi, j, cnt)) {
+                            table_update(A.tv, partition_hash(A.hp, oi, j), key, cnt);
+                            ++flushed;
                         }
                     } else {
                         const float p = __fmul_rn(owa, wb);
@@ -538,6 +530,37 @@ cudaError_t launch_validate_sparse(const int64_t *ptr, const int32_t *idx, int64
     if (e != cudaSuccess || nnz == 0) return e;
     int64_t b2 = (nnz + 255) / 256;
     k_validate_idx<<<(int)(b2 < 4096 ? b2 : 4096), 256, 0, s>>>(idx, nnz, n_minor, bad);
+    return cudaGetLastError();
+}
+
+// Add a warm stripe's counts to the partition tables and clear it.  Row
+// stripe (rows = 1): entry (items[r], x); column stripe: (x, items[r]).
+__global__ void k_warm_flush(unsigned int *stripe, uint32_t W, int32_t n_other,
+                             const int64_t *items, int rows, HashPair hp, TableView tv,
+                             unsigned long long *flushed) {
+    unsigned long long n = 0;
+    const uint64_t total = (uint64_t)W * (uint64_t)n_other;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned int c = stripe[x];
+        if (!c) continue;
+        stripe[x] = 0u;
+        const uint32_t w = (uint32_t)items[x / (uint64_t)n_other];
+        const uint32_t o = (uint32_t)(x % (uint64_t)n_other);
+        const uint32_t i = rows ? w : o, j = rows ? o : w;
+        table_update(tv, partition_hash(hp, i, j), make_key(i, j), c);
+        ++n;
+    }
+    if (n) atomicAdd(flushed, n);
+}
+
+cudaError_t launch_warm_flush(unsigned int *stripe, uint32_t W, int32_t n_other,
+                              const int64_t *items, int rows, HashPair hp, TableView tv,
+                              unsigned long long *flushed, cudaStream_t s) {
+    const uint64_t n = (uint64_t)W * (uint64_t)n_other;
+    if (n == 0) return cudaSuccess;
+    k_warm_flush<<<(int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192), 256, 0, s>>>(
+        stripe, W, n_other, items, rows, hp, tv, flushed);
     return cudaGetLastError();
 }
 

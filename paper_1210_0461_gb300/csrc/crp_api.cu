@@ -119,6 +119,10 @@ struct crp_plan {
     unsigned int *d_hot = nullptr, *d_cnt_a = nullptr, *d_cnt_b = nullptr, *d_sel = nullptr;
     uint16_t *d_rank_a = nullptr, *d_rank_b = nullptr;
     int64_t *d_items_a = nullptr, *d_items_b = nullptr;
+    uint32_t warm_W = 0;
+    unsigned int *d_warm_a = nullptr, *d_warm_b = nullptr;
+    uint16_t *d_wrank_a = nullptr, *d_wrank_b = nullptr;
+    int64_t *d_witems_a = nullptr, *d_witems_b = nullptr;
     // routed mode: per-group bins
     void *bins = nullptr;
     uint64_t bins_bytes = 0;
@@ -238,10 +242,11 @@ extern "C" crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc,
         return fail(CRP_EINVAL, "smem_slots must be a power of two in [4096, 16384]");
     if (d.groups && (!is_pow2(d.groups) || d.groups > d.P))
         return fail(CRP_EINVAL, "groups must be a power of two <= P");
-    if (d.hot_items && (d.hot_items > 4096 || d.value_type != CRP_I32 ||
-                        !(d.flags & (CRP_PLAN_DIRECT | CRP_PLAN_ROUTED)) || d.summary_counters))
-        return fail(CRP_EINVAL, "hot_items needs CRP_PLAN_DIRECT or CRP_PLAN_ROUTED, CRP_I32, "
-                                "exact mode, <= 4096");
+    if ((d.hot_items || d.warm_items) &&
+        (d.hot_items > 4096 || d.warm_items > 4096 || d.value_type != CRP_I32 ||
+         !(d.flags & (CRP_PLAN_DIRECT | CRP_PLAN_ROUTED)) || d.summary_counters))
+        return fail(CRP_EINVAL, "hot_items / warm_items need CRP_PLAN_DIRECT or CRP_PLAN_ROUTED, "
+                                "CRP_I32, exact mode, <= 4096");
     if (d.summary_counters && d.value_type != CRP_I32)
         return fail(CRP_EUNSUPPORTED, "summaries count {0,1} inputs (CRP_I32) only");
     if (d.summary_counters > (1u << 24))
@@ -328,6 +333,12 @@ extern "C" void crp_plan_destroy(crp_plan *pl) {
     cudaFree(pl->d_rank_b);
     cudaFree(pl->d_items_a);
     cudaFree(pl->d_items_b);
+    cudaFree(pl->d_warm_a);
+    cudaFree(pl->d_warm_b);
+    cudaFree(pl->d_wrank_a);
+    cudaFree(pl->d_wrank_b);
+    cudaFree(pl->d_witems_a);
+    cudaFree(pl->d_witems_b);
     cudaFree(pl->d_live);
     cudaFree(pl->d_floor);
     cudaFree(pl->d_ctmp);
@@ -523,6 +534,7 @@ static crp_status estimate_and_allocate(crp_plan *pl, const crp_sparse *A, const
         a.part_lo = 0;
         a.part_hi = 0xFFFFFFFFu;
         a.hot_R = 0;
+        a.warm_W = 0;
         a.tv = table_view(pl, tmp, d_off, d_mask);
         CRP_CUDA(launch_accumulate(a, pl->s_hash, pl->grid, pl->stream));
         // live entries per sampled partition
@@ -556,6 +568,8 @@ static crp_status estimate_and_allocate(crp_plan *pl, const crp_sparse *A, const
 }
 
 static crp_status select_hot_items(crp_plan *pl, const crp_sparse *A, const crp_sparse *B);
+static void set_dense_args(crp_plan *pl, AccumulateArgs &a);
+static crp_status flush_dense(crp_plan *pl, const TableView &tv);
 
 // Compact every partition holding more than ell keys, then re-insert spilled
 // updates (each re-insert may spill again when a partition refills; repeat).
@@ -672,13 +686,10 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
     RouteArgs RA;
     RA.acc = make_args(pl, A, B, B->idx, B->val, 1);
     RA.acc.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
-    if (pl->d.hot_items) {
+    if (pl->d.hot_items || pl->d.warm_items) {
         crp_status hs = select_hot_items(pl, A, B);
         if (hs != CRP_OK) return hs;
-        RA.acc.hot_rank_a = pl->d_rank_a;
-        RA.acc.hot_rank_b = pl->d_rank_b;
-        RA.acc.hot_block = pl->d_hot;
-        RA.acc.hot_R = pl->hot_R;
+        set_dense_args(pl, RA.acc);
     }
     RA.bins = pl->bins;
     RA.bin_off = pl->d_bin_off;
@@ -697,10 +708,9 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
     CRP_CUDA(launch_route(RA, 2 * pl->sm_count, pl->stream));
     CRP_CUDA(cudaEventRecord(pl->evm, pl->stream));
     CRP_CUDA(launch_apply(RA, pl->d_chunk_prefix, 2048, 2 * pl->sm_count, pl->stream));
-    if (RA.acc.hot_R) {
-        CRP_CUDA(launch_hot_flush(pl->d_hot, pl->hot_R, pl->d_items_a, pl->d_items_b, pl->hp,
-                                  RA.acc.tv, &pl->dc->flushed, pl->stream));
-        pl->launches += 1;
+    {
+        crp_status fs = flush_dense(pl, RA.acc.tv);
+        if (fs != CRP_OK) return fs;
     }
     CRP_CUDA(cudaEventRecord(pl->ev1, pl->stream));
     pl->timed = true;
@@ -709,24 +719,41 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
     return CRP_OK;
 }
 
-// Hot items of this call: the R most frequent row indices of A and column
-// indices of B over the first 1/64 of the outer products (at least 4096);
-// ranks map an item to its row / column of the hot block.
+// Dense tiers of this call: the R (hot) and W (warm) most frequent row
+// indices of A and column indices of B over the first 1/64 of the outer
+// products (at least 4096); ranks map an item to its row / column of the hot
+// block or of a warm stripe.
 static crp_status select_hot_items(crp_plan *pl, const crp_sparse *A, const crp_sparse *B) {
-    const uint32_t R = std::min<uint32_t>(pl->d.hot_items,
-                                          (uint32_t)std::min(pl->d.n_rows, pl->d.n_cols));
+    const uint32_t nmin = (uint32_t)std::min(pl->d.n_rows, pl->d.n_cols);
+    const uint32_t R = std::min<uint32_t>(pl->d.hot_items, nmin);
+    uint32_t W = std::min<uint32_t>(pl->d.warm_items, nmin);
+    const uint64_t stripe_cols = (uint64_t)pl->d.n_rows + pl->d.n_cols;
+    while (W && (uint64_t)W * stripe_cols * 4 > (64ull << 20)) W >>= 1;
     cudaStream_t s = pl->stream;
-    if (!pl->d_hot) {
-        CRP_CUDA(cudaMalloc(&pl->d_hot, (size_t)R * R * 4));
-        CRP_CUDA(cudaMemsetAsync(pl->d_hot, 0, (size_t)R * R * 4, s));
+    if (!pl->d_cnt_a) {
         CRP_CUDA(cudaMalloc(&pl->d_cnt_a, (size_t)pl->d.n_rows * 4));
         CRP_CUDA(cudaMalloc(&pl->d_cnt_b, (size_t)pl->d.n_cols * 4));
-        CRP_CUDA(cudaMalloc(&pl->d_rank_a, (size_t)pl->d.n_rows * 2));
-        CRP_CUDA(cudaMalloc(&pl->d_rank_b, (size_t)pl->d.n_cols * 2));
-        CRP_CUDA(cudaMalloc(&pl->d_items_a, (size_t)R * 8));
-        CRP_CUDA(cudaMalloc(&pl->d_items_b, (size_t)R * 8));
         CRP_CUDA(cudaMalloc(&pl->d_sel, 260 * 4));
+        if (R) {
+            CRP_CUDA(cudaMalloc(&pl->d_hot, (size_t)R * R * 4));
+            CRP_CUDA(cudaMemsetAsync(pl->d_hot, 0, (size_t)R * R * 4, s));
+            CRP_CUDA(cudaMalloc(&pl->d_rank_a, (size_t)pl->d.n_rows * 2));
+            CRP_CUDA(cudaMalloc(&pl->d_rank_b, (size_t)pl->d.n_cols * 2));
+            CRP_CUDA(cudaMalloc(&pl->d_items_a, (size_t)R * 8));
+            CRP_CUDA(cudaMalloc(&pl->d_items_b, (size_t)R * 8));
+        }
+        if (W) {
+            CRP_CUDA(cudaMalloc(&pl->d_warm_a, (size_t)W * pl->d.n_cols * 4));
+            CRP_CUDA(cudaMalloc(&pl->d_warm_b, (size_t)W * pl->d.n_rows * 4));
+            CRP_CUDA(cudaMemsetAsync(pl->d_warm_a, 0, (size_t)W * pl->d.n_cols * 4, s));
+            CRP_CUDA(cudaMemsetAsync(pl->d_warm_b, 0, (size_t)W * pl->d.n_rows * 4, s));
+            CRP_CUDA(cudaMalloc(&pl->d_wrank_a, (size_t)pl->d.n_rows * 2));
+            CRP_CUDA(cudaMalloc(&pl->d_wrank_b, (size_t)pl->d.n_cols * 2));
+            CRP_CUDA(cudaMalloc(&pl->d_witems_a, (size_t)W * 8));
+            CRP_CUDA(cudaMalloc(&pl->d_witems_b, (size_t)W * 8));
+        }
         pl->hot_R = R;
+        pl->warm_W = W;
     }
     const int64_t K = A->n_major;
     const int64_t S = std::min<int64_t>(K, std::max<int64_t>(4096, K / 64));
@@ -738,11 +765,53 @@ static crp_status select_hot_items(crp_plan *pl, const crp_sparse *A, const crp_
     CRP_CUDA(cudaStreamSynchronize(s));
     CRP_CUDA(launch_item_counts(A->idx, ea, pl->d.n_rows, pl->d_cnt_a, s));
     CRP_CUDA(launch_item_counts(B->idx, eb, pl->d.n_cols, pl->d_cnt_b, s));
-    CRP_CUDA(select_top(pl->d_cnt_a, pl->d.n_rows, R, pl->d_items_a, pl->d_sel, s));
-    CRP_CUDA(select_top(pl->d_cnt_b, pl->d.n_cols, R, pl->d_items_b, pl->d_sel, s));
-    CRP_CUDA(launch_hot_ranks(pl->d_rank_a, pl->d.n_rows, pl->d_items_a, R, s));
-    CRP_CUDA(launch_hot_ranks(pl->d_rank_b, pl->d.n_cols, pl->d_items_b, R, s));
-    pl->launches += 2 + 2 * 5 + 4;
+    pl->launches += 2;
+    if (pl->hot_R) {
+        CRP_CUDA(select_top(pl->d_cnt_a, pl->d.n_rows, pl->hot_R, pl->d_items_a, pl->d_sel, s));
+        CRP_CUDA(select_top(pl->d_cnt_b, pl->d.n_cols, pl->hot_R, pl->d_items_b, pl->d_sel, s));
+        CRP_CUDA(launch_hot_ranks(pl->d_rank_a, pl->d.n_rows, pl->d_items_a, pl->hot_R, s));
+        CRP_CUDA(launch_hot_ranks(pl->d_rank_b, pl->d.n_cols, pl->d_items_b, pl->hot_R, s));
+        pl->launches += 2 * 5 + 4;
+    }
+    if (pl->warm_W) {
+        CRP_CUDA(select_top(pl->d_cnt_a, pl->d.n_rows, pl->warm_W, pl->d_witems_a, pl->d_sel, s));
+        CRP_CUDA(select_top(pl->d_cnt_b, pl->d.n_cols, pl->warm_W, pl->d_witems_b, pl->d_sel, s));
+        CRP_CUDA(launch_hot_ranks(pl->d_wrank_a, pl->d.n_rows, pl->d_witems_a, pl->warm_W, s));
+        CRP_CUDA(launch_hot_ranks(pl->d_wrank_b, pl->d.n_cols, pl->d_witems_b, pl->warm_W, s));
+        pl->launches += 2 * 5 + 4;
+    }
+    return CRP_OK;
+}
+
+static void set_dense_args(crp_plan *pl, AccumulateArgs &a) {
+    if (pl->hot_R) {
+        a.hot_rank_a = pl->d_rank_a;
+        a.hot_rank_b = pl->d_rank_b;
+        a.hot_block = pl->d_hot;
+        a.hot_R = pl->hot_R;
+    }
+    if (pl->warm_W) {
+        a.warm_rank_a = pl->d_wrank_a;
+        a.warm_rank_b = pl->d_wrank_b;
+        a.warm_a = pl->d_warm_a;
+        a.warm_b = pl->d_warm_b;
+        a.warm_W = pl->warm_W;
+    }
+}
+
+static crp_status flush_dense(crp_plan *pl, const TableView &tv) {
+    if (pl->hot_R) {
+        CRP_CUDA(launch_hot_flush(pl->d_hot, pl->hot_R, pl->d_items_a, pl->d_items_b, pl->hp, tv,
+                                  &pl->dc->flushed, pl->stream));
+        pl->launches += 1;
+    }
+    if (pl->warm_W) {
+        CRP_CUDA(launch_warm_flush(pl->d_warm_a, pl->warm_W, pl->d.n_cols, pl->d_witems_a, 1,
+                                   pl->hp, tv, &pl->dc->flushed, pl->stream));
+        CRP_CUDA(launch_warm_flush(pl->d_warm_b, pl->warm_W, pl->d.n_rows, pl->d_witems_b, 0,
+                                   pl->hp, tv, &pl->dc->flushed, pl->stream));
+        pl->launches += 2;
+    }
     return CRP_OK;
 }
 
@@ -795,22 +864,16 @@ extern "C" crp_status crp_outer_accumulate(crp_plan *pl, const crp_sparse *A, co
     if (pl->d.flags & CRP_PLAN_ROUTED) return routed_accumulate(pl, A, B);
     AccumulateArgs a = make_args(pl, A, B, b_idx, b_val, pl->G);
     a.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
-    if (pl->d.hot_items) {
+    if (pl->d.hot_items || pl->d.warm_items) {
         st = select_hot_items(pl, A, B);
         if (st != CRP_OK) return st;
-        a.hot_rank_a = pl->d_rank_a;
-        a.hot_rank_b = pl->d_rank_b;
-        a.hot_block = pl->d_hot;
-        a.hot_R = pl->hot_R;
+        set_dense_args(pl, a);
     }
     CRP_CUDA(cudaMemsetAsync(&pl->dc->work_next, 0, sizeof(unsigned int), pl->stream));
     CRP_CUDA(cudaEventRecord(pl->ev0, pl->stream));
     CRP_CUDA(launch_accumulate(a, b_hash, pl->grid, pl->stream));
-    if (a.hot_R) {
-        CRP_CUDA(launch_hot_flush(pl->d_hot, pl->hot_R, pl->d_items_a, pl->d_items_b, pl->hp, a.tv,
-                                  &pl->dc->flushed, pl->stream));
-        pl->launches += 1;
-    }
+    st = flush_dense(pl, a.tv);
+    if (st != CRP_OK) return st;
     CRP_CUDA(cudaEventRecord(pl->ev1, pl->stream));
     pl->timed = true;
     pl->timed_mid = false;

@@ -1,11 +1,12 @@
 // Launch-configuration autotuner.  It times candidate configurations of the
 // exact product (partition count P, variant: on-chip combining table / direct
-// HBM updates / routed two-phase with 128, 256 or size-derived bins, hot
-// blocks of 1024 or 4096 items, tile of outer products per work item) on a
-// prefix of the caller's outer products, and keeps the fastest.  Results are
-// cached in a text file keyed by device name and a shape class of the input
-// (log2 buckets of K, n_rows, n_cols and of the mean terms per outer
-// product, plus value type and mode), one "key value..." line per entry.
+// HBM updates / routed two-phase with 128, 256 or size-derived bins, dense
+// tiers: hot blocks of 1024 or 4096 items, or 2048 items plus warm stripes of
+// 64 items, tile of outer products per work item) on a prefix of the caller's
+// outer products, and keeps the fastest.  Results are cached in a text file
+// keyed by device name and a shape class of the input (log2 buckets of K,
+// n_rows, n_cols and of the mean terms per outer product, plus value type and
+// mode), one "key value..." line per entry.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -48,12 +49,13 @@ static bool cache_lookup(const char *path, const std::string &key, crp_plan_desc
     bool found = false;
     while (fgets(line, sizeof line, f)) {
         char k[256];
-        unsigned P, groups, tile, slots, flags, hot;
+        unsigned P, groups, tile, slots, flags, hot, warm;
         double v;
-        if (sscanf(line, "%255s %u %u %u %u %u %u %lf", k, &P, &groups, &tile, &slots, &flags, &hot,
-                   &v) == 8 && key == k) {
+        if (sscanf(line, "%255s %u %u %u %u %u %u %u %lf", k, &P, &groups, &tile, &slots, &flags,
+                   &hot, &warm, &v) == 9 && key == k) {
             out->P = P;
             out->hot_items = hot;
+            out->warm_items = warm;
             out->groups = groups;
             out->tile_vectors = tile;
             out->smem_slots = slots;
@@ -71,8 +73,8 @@ static void cache_store(const char *path, const std::string &key, const crp_plan
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %u %u %u %u %u %u %.17g\n", key.c_str(), d.P, d.groups, d.tile_vectors,
-            d.smem_slots, d.flags, d.hot_items, tps);
+    fprintf(f, "%s %u %u %u %u %u %u %u %.17g\n", key.c_str(), d.P, d.groups, d.tile_vectors,
+            d.smem_slots, d.flags, d.hot_items, d.warm_items, tps);
     fclose(f);
 }
 
@@ -110,21 +112,23 @@ extern "C" crp_status crp_autotune(const crp_plan_desc *base, const crp_sparse *
     const std::string key = shape_key(*base, K, Ks ? (double)terms / (double)Ks : 0.0);
     if (cache_lookup(cache_path, key, best, best_terms_per_s)) return CRP_OK;
 
-    struct Cand { uint32_t P, groups, tile, slots, flags, hot; };
+    struct Cand { uint32_t P, groups, tile, slots, flags, hot, warm; };
     std::vector<Cand> cands;
     const uint32_t Ps[] = {256, 1024, 4096};
     const uint32_t tiles[] = {32, 64, 256};
     const bool ints = base->value_type == CRP_I32;
     for (uint32_t P : Ps) {
-        for (uint32_t t : tiles) cands.push_back({P, 1, t, 8192, CRP_PLAN_DIRECT, 0});
-        cands.push_back({P, 1, 64, 8192, 0u, 0});
-        cands.push_back({P, 1, 64, 16384, 0u, 0});
-        cands.push_back({P, 0, 64, 8192, CRP_PLAN_ROUTED, 0});
+        for (uint32_t t : tiles) cands.push_back({P, 1, t, 8192, CRP_PLAN_DIRECT, 0, 0});
+        cands.push_back({P, 1, 64, 8192, 0u, 0, 0});
+        cands.push_back({P, 1, 64, 16384, 0u, 0, 0});
+        cands.push_back({P, 0, 64, 8192, CRP_PLAN_ROUTED, 0, 0});
         if (ints) {
-            for (uint32_t h : {1024u, 4096u}) {
-                cands.push_back({P, 1, 64, 8192, CRP_PLAN_DIRECT, h});
+            // hot block alone, and a smaller hot block with warm stripes
+            const uint32_t tiers[3][2] = {{1024u, 0u}, {4096u, 0u}, {2048u, 64u}};
+            for (const auto &hw : tiers) {
+                cands.push_back({P, 1, 64, 8192, CRP_PLAN_DIRECT, hw[0], hw[1]});
                 for (uint32_t g : {0u, 128u, 256u})
-                    if (g <= P) cands.push_back({P, g, 64, 8192, CRP_PLAN_ROUTED, h});
+                    if (g <= P) cands.push_back({P, g, 64, 8192, CRP_PLAN_ROUTED, hw[0], hw[1]});
             }
         }
     }
@@ -138,6 +142,7 @@ extern "C" crp_status crp_autotune(const crp_plan_desc *base, const crp_sparse *
         d.smem_slots = c.slots;
         d.flags = (base->flags & ~(CRP_PLAN_DIRECT | CRP_PLAN_ROUTED)) | c.flags;
         d.hot_items = c.hot;
+        d.warm_items = c.warm;
         d.table_capacity_hint = 0;
         d.auto_grow = 1;
         crp_plan *pl = nullptr;

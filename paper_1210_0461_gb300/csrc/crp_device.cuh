@@ -186,6 +186,7 @@ struct WarpEnum {
     // this lane's a entry of the current batch of 32
     uint32_t my_i;
     uint32_t my_rank;          // row of my_i in the hot block, or 0xFFFF
+    uint32_t my_wrank;         // row of my_i in the warm stripe, or 0xFFFF
     float my_wa;
     int32_t lo1, n1, lo2, excl;
     int32_t total, pos;
@@ -209,11 +210,13 @@ __device__ __forceinline__ void load_batch(WarpEnum &st, const AccumulateArgs &A
     int32_t c = 0;
     st.my_i = 0;
     st.my_rank = 0xFFFFu;
+    st.my_wrank = 0xFFFFu;
     st.my_wa = 1.0f;
     st.lo1 = 0; st.n1 = 0; st.lo2 = 0;
     if (va) {
         st.my_i = (uint32_t)__ldg(A.a_idx + idx);
         if (A.hot_rank_a) st.my_rank = __ldg(A.hot_rank_a + st.my_i);
+        if (A.warm_rank_a) st.my_wrank = __ldg(A.warm_rank_a + st.my_i);
         if (A.a_val) st.my_wa = __ldg(A.a_val + idx);
         if (A.sym_upper) {
             st.lo1 = (int32_t)(idx - st.a_beg) + 1;
@@ -319,6 +322,33 @@ __device__ __forceinline__ bool next_term(WarpEnum &st, const AccumulateArgs &A,
         }
     }
     return valid;
+}
+
+// The dense on-chip tiers of an int term: the hot block (both items hot),
+// then the warm stripes (row warm, else column warm).  Returns true when the
+// term was counted there.
+__device__ __forceinline__ bool dense_tiers(const AccumulateArgs &A, uint32_t orank,
+                                            uint32_t owrank, uint32_t i, uint32_t j,
+                                            unsigned cnt) {
+    if (orank < A.hot_R) {
+        const uint32_t rb = __ldg(A.hot_rank_b + j);
+        if (rb < A.hot_R) {
+            atomicAdd(&A.hot_block[orank * A.hot_R + rb], cnt);
+            return true;
+        }
+    }
+    if (A.warm_W) {
+        if (owrank < A.warm_W) {
+            atomicAdd(&A.warm_a[(size_t)owrank * A.n_cols + j], cnt);
+            return true;
+        }
+        const uint32_t wb = __ldg(A.warm_rank_b + j);
+        if (wb < A.warm_W) {
+            atomicAdd(&A.warm_b[(size_t)wb * A.n_rows + i], cnt);
+            return true;
+        }
+    }
+    return false;
 }
 
 }  // namespace crp

@@ -138,6 +138,13 @@ struct AccumulateArgs {
     const uint16_t *hot_rank_b = nullptr;
     unsigned int *hot_block = nullptr;
     uint32_t hot_R = 0;
+    // warm stripes: dense counters for the pairs (warm row, any column) and
+    // (any row, warm column) outside the hot block
+    const uint16_t *warm_rank_a = nullptr;
+    const uint16_t *warm_rank_b = nullptr;
+    unsigned int *warm_a = nullptr;   // [warm_W][n_cols]
+    unsigned int *warm_b = nullptr;   // [warm_W][n_rows]
+    uint32_t warm_W = 0;
     // interval [part_lo, part_hi) of partitions kept (Figure 1, CRoP on [q, r))
     uint32_t part_lo = 0, part_hi = 0xFFFFFFFFu;
     // pairs i < j of T^T T with a_k == b_k (same sorted list): the window of
@@ -176,6 +183,9 @@ cudaError_t launch_hot_flush(unsigned int *hot, uint32_t R, const int64_t *items
                              unsigned long long *flushed, cudaStream_t s);
 cudaError_t launch_hot_ranks(uint16_t *rank, int32_t n, const int64_t *items, uint32_t R,
                              cudaStream_t s);
+cudaError_t launch_warm_flush(unsigned int *stripe, uint32_t W, int32_t n_other,
+                              const int64_t *items, int rows, HashPair hp, TableView tv,
+                              unsigned long long *flushed, cudaStream_t s);
 
 // Selections (crp_select.cu)
 int select_grid_for(int64_t n);

@@ -136,14 +136,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_route(RouteArgs RA) {
                 int owner;
                 bool valid = next_term(st, A, lane, VT, oi, j, owa, wb, &owner);
                 const uint32_t orank = __shfl_sync(kFull, st.my_rank, owner);
+                const uint32_t owrank = __shfl_sync(kFull, st.my_wrank, owner);
                 my_terms += valid ? 1 : 0;
-                if (VT == CRP_I32 && valid && orank < A.hot_R) {
-                    const uint32_t rb = __ldg(A.hot_rank_b + j);
-                    if (rb < A.hot_R) {
-                        atomicAdd(&A.hot_block[orank * A.hot_R + rb], 1u);
-                        valid = false;
-                    }
-                }
+                if (VT == CRP_I32 && valid && dense_tiers(A, orank, owrank, oi, j, 1u))
+                    valid = false;
                 if (valid) {
                     const unsigned long long key = make_key(oi, j);
                     const uint32_t b = partition_hash(A.hp, oi, j) >> RA.B_shift;

@@ -63,6 +63,9 @@ CONFIGS = [
     dict(flags=8 | 2), dict(groups=16, flags=8 | 2), dict(groups=64, flags=8 | 1 | 2),  # routed
     dict(flags=4 | 2, hot_items=64), dict(flags=4 | 2, hot_items=1000),  # direct + hot block
     dict(groups=16, flags=8 | 2, hot_items=128),                         # routed + hot block
+    dict(flags=4 | 2, hot_items=64, warm_items=16),                      # direct + hot + warm
+    dict(flags=4 | 2, warm_items=100),                                   # direct + warm only
+    dict(groups=16, flags=8 | 2, hot_items=32, warm_items=128),          # routed, warm > hot
 ]
 
 
@@ -80,9 +83,11 @@ def test_c1_cooccurrence_full_bit_exact(crp, cfg):
     plan.close()
 
 
-@pytest.mark.parametrize("cfg", [dict(groups=8), dict(flags=4 | 16 | 2), dict(flags=8 | 16 | 2,
-                                                                           hot_items=64)],
-                         ids=["groups", "direct-sorted-rows", "routed-sorted-rows"])
+@pytest.mark.parametrize("cfg", [dict(groups=8), dict(flags=4 | 16 | 2),
+                                 dict(flags=8 | 16 | 2, hot_items=64),
+                                 dict(flags=8 | 16 | 2, hot_items=64, warm_items=32)],
+                         ids=["groups", "direct-sorted-rows", "routed-sorted-rows",
+                              "routed-sorted-rows-warm"])
 def test_c1_upper_and_topk(crp, cfg):
     T = ci.C1.generate()
     Tc = O.Compressed.of(T)
@@ -134,16 +139,17 @@ def _random_case(seed, K, n_i, n_j, density, values):
     return A, B
 
 
-@pytest.mark.parametrize("seed,P,G,fl,hot", [(0, 1, 1, 2, 0), (1, 2, 2, 2, 0), (2, 64, 8, 2, 0),
-                                             (3, 1024, 32, 2, 0), (4, 4096, 4096, 2, 0),
-                                             (5, 16, 1, 2, 0), (6, 256, 256, 8 | 2, 0),
-                                             (7, 1, 1, 8 | 2, 0), (8, 64, 1, 4 | 2, 16),
-                                             (9, 16, 1, 4 | 2, 500)])
-def test_random_edge_cases_int(crp, seed, P, G, fl, hot):
+@pytest.mark.parametrize("seed,P,G,fl,hot,warm", [
+    (0, 1, 1, 2, 0, 0), (1, 2, 2, 2, 0, 0), (2, 64, 8, 2, 0, 0), (3, 1024, 32, 2, 0, 0),
+    (4, 4096, 4096, 2, 0, 0), (5, 16, 1, 2, 0, 0), (6, 256, 256, 8 | 2, 0, 0),
+    (7, 1, 1, 8 | 2, 0, 0), (8, 64, 1, 4 | 2, 16, 0), (9, 16, 1, 4 | 2, 500, 0),
+    (14, 64, 1, 4 | 2, 8, 40), (15, 32, 4, 8 | 2, 0, 4000), (16, 1, 1, 8 | 2, 3, 3)])
+def test_random_edge_cases_int(crp, seed, P, G, fl, hot, warm):
+    # warm=4000 exceeds both dimensions (the plan clamps it to min(n_rows, n_cols))
     A, B = _random_case(seed, 700, 37 + seed * 50, 53 + seed * 30, 0.2, False)
     ref = O.exact_product(A, B, O.FULL)
     plan = _run(crp, A, B, A.n_minor, B.n_minor, P, groups=G, tile_vectors=7, flags=fl,
-                hot_items=hot)
+                hot_items=hot, warm_items=warm)
     _check_exact(crp, plan, ref, P)
     plan.close()
 
@@ -198,12 +204,16 @@ def test_c3_markov_expansion_scaled(crp, fl):
     plan.close()
 
 
-def test_streaming_chunks_are_additive(crp):
+@pytest.mark.parametrize("cfg", [dict(groups=4, flags=2),
+                                 dict(groups=16, flags=8 | 2, hot_items=64, warm_items=32),
+                                 dict(flags=4 | 2, warm_items=48)],
+                         ids=["groups", "routed+hot+warm", "direct+warm"])
+def test_streaming_chunks_are_additive(crp, cfg):
+    # each call picks its own hot / warm items and leaves the dense tiers clear
     T = ci.C1.scaled(m=9000).generate()
     Tc = O.Compressed.of(T)
     ref = O.exact_product(Tc, Tc, O.FULL)
-    plan = crp.Plan(1000, 1000, 64, ci.SEED_A, ci.SEED_B, groups=4,
-                    flags=crp.CRP_PLAN_DEBUG_CHECKS)
+    plan = crp.Plan(1000, 1000, 64, ci.SEED_A, ci.SEED_B, **cfg)
     for lo, hi in ((0, 1000), (1000, 1001), (1001, 6000), (6000, 9000)):
         ptr = T.ptr[lo:hi + 1] - T.ptr[lo]
         part = ci.Sparse(ptr, T.idx[T.ptr[lo]:T.ptr[hi]], None, 1000)
@@ -283,8 +293,10 @@ def test_repeat_runs_bit_identical(crp):
 
 @pytest.mark.parametrize("cfg", [dict(flags=4 | 2), dict(flags=4 | 2, hot_items=256),
                                  dict(groups=16, flags=2), dict(groups=1, flags=2),
-                                 dict(groups=32, flags=8 | 2, hot_items=128)],
-                         ids=["direct", "direct+hot", "lemma1-groups", "smem", "routed+hot"])
+                                 dict(groups=32, flags=8 | 2, hot_items=128),
+                                 dict(groups=32, flags=8 | 2, hot_items=64, warm_items=64)],
+                         ids=["direct", "direct+hot", "lemma1-groups", "smem", "routed+hot",
+                              "routed+hot+warm"])
 def test_disjoint_intervals_union_is_the_product(crp, cfg):
     # Figure 1 / Theorem 1: K instances of CRoP on disjoint intervals of the
     # partitions, each seeing the whole input, together produce every entry
