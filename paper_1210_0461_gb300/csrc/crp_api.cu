@@ -123,12 +123,12 @@ struct crp_plan {
     unsigned int *d_warm_a = nullptr, *d_warm_b = nullptr;
     uint16_t *d_wrank_a = nullptr, *d_wrank_b = nullptr;
     int64_t *d_witems_a = nullptr, *d_witems_b = nullptr;
-    // routed mode: per-group bins
-    void *bins = nullptr;
-    uint64_t bins_bytes = 0;
-    uint32_t B = 0;
-    unsigned long long *d_bin_off = nullptr, *d_bin_cap = nullptr, *d_bin_cnt = nullptr;
-    unsigned int *d_chunk_prefix = nullptr;
+    // routed mode: pool of record chunks, their bins and the grouping by bin
+    void *pool = nullptr;
+    uint64_t pool_bytes = 0;
+    uint32_t pool_chunks = 0, B = 0;
+    unsigned int *d_chunk_bin = nullptr, *d_order = nullptr;
+    unsigned int *d_route_ctl = nullptr;   // chunk counter, count[B], fill[B], start[B + 1]
     // timing of the enumeration kernel and a count of our launches
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;
     bool timed = false, timed_mid = false;
@@ -345,11 +345,10 @@ extern "C" void crp_plan_destroy(crp_plan *pl) {
     cudaFree(pl->d_spill2);
     cudaFree(pl->d_res_keys);
     cudaFree(pl->d_res_bits);
-    cudaFree(pl->bins);
-    cudaFree(pl->d_bin_off);
-    cudaFree(pl->d_bin_cap);
-    cudaFree(pl->d_bin_cnt);
-    cudaFree(pl->d_chunk_prefix);
+    cudaFree(pl->pool);
+    cudaFree(pl->d_chunk_bin);
+    cudaFree(pl->d_order);
+    cudaFree(pl->d_route_ctl);
     if (pl->ev0) cudaEventDestroy(pl->ev0);
     if (pl->ev1) cudaEventDestroy(pl->ev1);
     if (pl->evm) cudaEventDestroy(pl->evm);
@@ -653,36 +652,44 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
     uint32_t Bn = 1;
     while (Bn < want && Bn < P) Bn <<= 1;
     if (pl->d.groups) Bn = pl->G;  // explicit partition groups = bins
-    const int rec = pl->d.value_type == CRP_I32 ? 8 : 16;
-    const uint64_t per_bin = (uint64_t)((double)terms / Bn * 1.25) + 8192;
-    const uint64_t need = per_bin * Bn * rec;
+    Bn = std::min<uint32_t>(Bn, 8192);   // per-CTA chunk state lives in shared memory
+    const int grid = 2 * pl->sm_count;
+    const uint64_t rec = pl->d.value_type == CRP_I32 ? 8 : 16;
+    // every term may become a record; each CTA also holds a partly filled
+    // chunk and a spare per bin
+    const uint64_t chunks_needed = (terms + kChunkRecs - 1) / kChunkRecs + 2ull * Bn * grid + 1;
+    const uint32_t chunks = (uint32_t)std::min<uint64_t>(chunks_needed, 0xFFFFFFF0ull);
     if (Bn != pl->B) {
-        cudaFree(pl->d_bin_off);
-        cudaFree(pl->d_bin_cap);
-        cudaFree(pl->d_bin_cnt);
-        cudaFree(pl->d_chunk_prefix);
-        pl->d_bin_off = pl->d_bin_cap = pl->d_bin_cnt = nullptr;
-        pl->d_chunk_prefix = nullptr;
-        CRP_CUDA(cudaMalloc(&pl->d_bin_off, Bn * 8));
-        CRP_CUDA(cudaMalloc(&pl->d_bin_cap, Bn * 8));
-        CRP_CUDA(cudaMalloc(&pl->d_bin_cnt, Bn * 8));
-        CRP_CUDA(cudaMalloc(&pl->d_chunk_prefix, (Bn + 1) * 4));
+        cudaFree(pl->d_route_ctl);
+        pl->d_route_ctl = nullptr;
+        pl->B = 0;
+        CRP_CUDA(cudaMalloc(&pl->d_route_ctl, (3 * (size_t)Bn + 2) * 4));
         pl->B = Bn;
     }
-    if (need > pl->bins_bytes) {
-        cudaFree(pl->bins);
-        pl->bins = nullptr;
-        pl->bins_bytes = 0;
-        CRP_CUDA(cudaMalloc(&pl->bins, need));
-        pl->bins_bytes = need;
+    if (chunks > pl->pool_chunks) {
+        cudaFree(pl->pool);
+        cudaFree(pl->d_chunk_bin);
+        cudaFree(pl->d_order);
+        pl->pool = nullptr;
+        pl->d_chunk_bin = pl->d_order = nullptr;
+        pl->pool_chunks = 0;
+        pl->pool_bytes = 0;
+        // a smaller pool only sends the overflow straight to the tables
+        uint32_t c = chunks;
+        while (true) {
+            if (cudaMalloc(&pl->pool, (size_t)c * kChunkRecs * rec) == cudaSuccess) break;
+            cudaGetLastError();
+            pl->pool = nullptr;
+            if (c <= chunks / 16 || c <= 2u * Bn * grid + 1) return fail(CRP_ENOMEM, "routed pool");
+            c /= 2;
+        }
+        CRP_CUDA(cudaMalloc(&pl->d_chunk_bin, (size_t)c * 4));
+        CRP_CUDA(cudaMalloc(&pl->d_order, (size_t)c * 4));
+        pl->pool_chunks = c;
+        pl->pool_bytes = (uint64_t)c * kChunkRecs * rec;
     }
-    const uint64_t cap = pl->bins_bytes / rec / Bn;
-    std::vector<unsigned long long> off(Bn), capv(Bn, cap);
-    for (uint32_t b = 0; b < Bn; ++b) off[b] = (unsigned long long)b * cap;
-    CRP_CUDA(cudaMemcpyAsync(pl->d_bin_off, off.data(), Bn * 8, cudaMemcpyHostToDevice, pl->stream));
-    CRP_CUDA(cudaMemcpyAsync(pl->d_bin_cap, capv.data(), Bn * 8, cudaMemcpyHostToDevice,
-                             pl->stream));
-    CRP_CUDA(cudaMemsetAsync(pl->d_bin_cnt, 0, Bn * 8, pl->stream));
+    CRP_CUDA(cudaMemsetAsync(pl->d_chunk_bin, 0xFF, (size_t)pl->pool_chunks * 4, pl->stream));
+    CRP_CUDA(cudaMemsetAsync(pl->d_route_ctl, 0, (2 * (size_t)Bn + 1) * 4, pl->stream));
     RouteArgs RA;
     RA.acc = make_args(pl, A, B, B->idx, B->val, 1);
     RA.acc.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
@@ -691,23 +698,23 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
         if (hs != CRP_OK) return hs;
         set_dense_args(pl, RA.acc);
     }
-    RA.bins = pl->bins;
-    RA.bin_off = pl->d_bin_off;
-    RA.bin_cap = pl->d_bin_cap;
-    RA.bin_cnt = pl->d_bin_cnt;
+    unsigned int *ctl = pl->d_route_ctl;
+    RA.pool = pl->pool;
+    RA.chunk_bin = pl->d_chunk_bin;
+    RA.chunk_next = ctl;
+    RA.order = pl->d_order;
+    RA.start = ctl + 1 + 2 * Bn;
+    RA.n_chunks = pl->pool_chunks;
     RA.B = Bn;
     uint32_t lgB = 0;
     while ((1u << lgB) < Bn) ++lgB;
     RA.B_shift = pl->logP - lgB;
-    const size_t budget = 96u << 10;
-    uint64_t rs = (budget - (size_t)Bn * 12 - 16) / ((size_t)Bn * rec);
-    RA.R_s = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(rs, 1), 256);
-    RA.pad = 0;
+    RA.core_H = std::min<uint32_t>(RA.acc.hot_R, 128);
     CRP_CUDA(cudaMemsetAsync(&pl->dc->work_next, 0, sizeof(unsigned int), pl->stream));
     CRP_CUDA(cudaEventRecord(pl->ev0, pl->stream));
-    CRP_CUDA(launch_route(RA, 2 * pl->sm_count, pl->stream));
+    CRP_CUDA(launch_route(RA, grid, pl->stream));
     CRP_CUDA(cudaEventRecord(pl->evm, pl->stream));
-    CRP_CUDA(launch_apply(RA, pl->d_chunk_prefix, 2048, 2 * pl->sm_count, pl->stream));
+    CRP_CUDA(launch_apply(RA, ctl + 1, ctl + 1 + Bn, grid, pl->stream));
     {
         crp_status fs = flush_dense(pl, RA.acc.tv);
         if (fs != CRP_OK) return fs;
@@ -715,7 +722,7 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
     CRP_CUDA(cudaEventRecord(pl->ev1, pl->stream));
     pl->timed = true;
     pl->timed_mid = true;
-    pl->launches += 3;
+    pl->launches += 5;
     return CRP_OK;
 }
 
@@ -769,9 +776,12 @@ static crp_status select_hot_items(crp_plan *pl, const crp_sparse *A, const crp_
     if (pl->hot_R) {
         CRP_CUDA(select_top(pl->d_cnt_a, pl->d.n_rows, pl->hot_R, pl->d_items_a, pl->d_sel, s));
         CRP_CUDA(select_top(pl->d_cnt_b, pl->d.n_cols, pl->hot_R, pl->d_items_b, pl->d_sel, s));
+        // ranks in order of frequency: the lowest ranks are the heaviest items
+        CRP_CUDA(order_by_count(pl->d_items_a, pl->d_cnt_a, pl->hot_R, s));
+        CRP_CUDA(order_by_count(pl->d_items_b, pl->d_cnt_b, pl->hot_R, s));
         CRP_CUDA(launch_hot_ranks(pl->d_rank_a, pl->d.n_rows, pl->d_items_a, pl->hot_R, s));
         CRP_CUDA(launch_hot_ranks(pl->d_rank_b, pl->d.n_cols, pl->d_items_b, pl->hot_R, s));
-        pl->launches += 2 * 5 + 4;
+        pl->launches += 2 * 5 + 6;
     }
     if (pl->warm_W) {
         CRP_CUDA(select_top(pl->d_cnt_a, pl->d.n_rows, pl->warm_W, pl->d_witems_a, pl->d_sel, s));

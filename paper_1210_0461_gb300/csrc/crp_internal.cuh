@@ -153,17 +153,23 @@ struct AccumulateArgs {
 };
 
 // Two-phase (routed) accumulation: bins of records per partition group.
+constexpr uint32_t kChunkRecs = 256;   // records per chunk of the routed pool
 struct RouteArgs {
     AccumulateArgs acc;        // enumeration inputs, hash and table view
-    void *bins;                // records: u64 keys (int) or {key, p, e} (real)
-    const unsigned long long *bin_off, *bin_cap;
-    unsigned long long *bin_cnt;
-    uint32_t B, B_shift, R_s, pad;
+    void *pool;                // n_chunks chunks of kChunkRecs records: u64 keys (int)
+                               // or {key, p, e} (real); unused tails hold kEmptyKey
+    unsigned int *chunk_bin;   // bin of each installed chunk, ~0u for none
+    unsigned int *chunk_next;  // chunks handed out (may pass n_chunks)
+    unsigned int *order;       // installed chunk ids grouped by bin
+    unsigned int *start;       // B + 1: first entry of each bin in order[]
+    uint32_t n_chunks;
+    uint32_t B, B_shift;
+    uint32_t core_H;           // ranks < core_H of the hot block count in shared memory first
 };
 cudaError_t launch_route(const RouteArgs &RA, int grid, cudaStream_t s);
-cudaError_t launch_apply(const RouteArgs &RA, unsigned int *chunk_prefix, uint32_t CH, int grid,
+cudaError_t launch_apply(const RouteArgs &RA, unsigned int *count, unsigned int *fill, int grid,
                          cudaStream_t s);
-size_t route_smem_bytes(int value_type, uint32_t B, uint32_t R_s);
+size_t route_smem_bytes(uint32_t B, uint32_t core_H);
 
 // Summary mode (crp_summary.cu)
 cudaError_t launch_summary_compact(Slot *slots, const unsigned long long *part_off,
@@ -189,6 +195,7 @@ cudaError_t launch_warm_flush(unsigned int *stripe, uint32_t W, int32_t n_other,
 
 // Selections (crp_select.cu)
 int select_grid_for(int64_t n);
+cudaError_t order_by_count(int64_t *items, const unsigned int *cnt, uint32_t R, cudaStream_t s);
 cudaError_t select_top(const uint32_t *key, int64_t n, int64_t K, int64_t *out,
                        unsigned int *scratch /* 258 */, cudaStream_t s);
 cudaError_t launch_item_counts(const int32_t *idx, int64_t nnz, int32_t n_items, unsigned int *cnt,

@@ -4,17 +4,25 @@
 // method runs fastest when that interval fits the processor's cache (Section
 // 6, scalability on the Xeon E5570 and the Mac Pro).  On GB300 the cache that
 // matters is the 126 MB L2, shared by all SMs: random atomics into an
-// L2-resident region run ~8x faster than into HBM.  So:
+// L2-resident region run several times faster than into HBM.  So:
 //
-//  1. k_route enumerates every term once (Lemma 1 with one interval) and
-//     appends it to the bin of its partition group b = h(i,j) >> shift; the
-//     appends are staged per bin in shared memory and written out in runs.
-//  2. k_apply walks the bins in order, all CTAs on one bin at a time, adding
-//     each record into its partition table; a group's table region (P/B
-//     partitions, sized to a few tens of MB) stays in L2 while it is updated.
+//  1. k_route enumerates every term once (one row of a_k per lane, the
+//     columns of b_k in turn).  Terms of hot and warm items go to the dense
+//     counters; every other term becomes a record appended to the bin of its
+//     partition group b = h(i,j) >> shift.  (Pairs of the most frequent
+//     items count first in per-CTA shared-memory counters, added into the
+//     hot block at the end: their few cache lines would otherwise take the
+//     bulk of the L2 atomics.)  A CTA appends to a bin through
+//     its own current chunk of kChunkRecs records, taken from a shared pool:
+//     one shared-memory 64-bit atomic returns (chunk, position) together, the
+//     lane that receives position kChunkRecs installs the next chunk, and no
+//     CTA-wide barrier is needed while enumerating.
+//  2. k_apply walks the chunks sorted by bin, all warps on one bin at a
+//     time, adding each record into its partition table; a group's table
+//     region stays in L2 while it is updated.
 //
-// A bin that runs out of room sends its extra records straight to the tables
-// (correct, only slower).
+// Appends that arrive while a chunk is being replaced, or when the pool is
+// exhausted, go straight to the tables (correct, only slower).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -23,7 +31,7 @@
 
 namespace crp {
 
-constexpr int kRouteChunks = 8;   // chunks of 32 terms per warp between CTA barriers
+constexpr uint32_t kNoChunk = 0xFFFFFFFFu;
 
 struct Rec16 {
     unsigned long long key;
@@ -67,124 +75,285 @@ __device__ __forceinline__ void apply_record(const RouteArgs &RA, const R &r) {
     table_update(RA.acc.tv, partition_hash(RA.acc.hp, i, j), key, rec_val(r));
 }
 
-template <typename R>
-__device__ __forceinline__ void bin_append(const RouteArgs &RA, uint32_t b, const R &r) {
-    R *bins = (R *)RA.bins;
-    const unsigned long long at = atomicAdd(&RA.bin_cnt[b], 1ull);
-    if (at < RA.bin_cap[b]) bins[RA.bin_off[b] + at] = r;
-    else apply_record(RA, r);
+__device__ __forceinline__ void store_rec(unsigned long long *p, unsigned long long v) { *p = v; }
+__device__ __forceinline__ void store_rec(Rec16 *p, const Rec16 &v) {
+    *(ulonglong2 *)p = *(const ulonglong2 *)&v;
+}
+__device__ __forceinline__ void set_empty(unsigned long long *p) { *p = kEmptyKey; }
+__device__ __forceinline__ void set_empty(Rec16 *p) { p->key = kEmptyKey; }
+
+// A chunk id from the pool, or kNoChunk when it is exhausted.  The counter is
+// read first so that it grows past the pool by at most the lanes in flight.
+__device__ __forceinline__ uint32_t reserve_chunk(const RouteArgs &RA) {
+    if (*(volatile unsigned int *)RA.chunk_next >= RA.n_chunks) return kNoChunk;
+    const uint32_t n = atomicAdd(RA.chunk_next, 1u);
+    return n < RA.n_chunks ? n : kNoChunk;
 }
 
-// Write bin b's staged records out (all of them; the count is reset).
-template <int VT>
-__device__ __forceinline__ void flush_bin(const RouteArgs &RA, typename RecT<VT>::type *stage,
-                                          unsigned int *scnt, uint32_t b, int lane) {
-    typedef typename RecT<VT>::type R;
-    R *bins = (R *)RA.bins;
-    const uint32_t c = scnt[b];
-    const uint32_t n = c < RA.R_s ? c : RA.R_s;
-    if (n == 0) return;
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&RA.bin_cnt[b], (unsigned long long)n);
-    base = __shfl_sync(kFull, base, 0);
-    const unsigned long long cap = RA.bin_cap[b], off = RA.bin_off[b];
-    for (uint32_t t = lane; t < n; t += 32) {
-        const R r = stage[(size_t)b * RA.R_s + t];
-        if (base + t < cap) store_stream(bins + off + base + t, r);
-        else apply_record(RA, r);
+// Append record r to bin b through this CTA's current chunk of the bin.
+// cur[b] = (chunk << 32) | next position; nxt[b] = a chunk reserved ahead.
+template <typename R>
+__device__ __forceinline__ void bin_append(const RouteArgs &RA, unsigned long long *cur,
+                                           unsigned int *nxt, uint32_t b, const R &r) {
+    R *pool = (R *)RA.pool;
+    const unsigned long long old = atomicAdd(&cur[b], 1ull);
+    const uint32_t c = (uint32_t)(old >> 32), pos = (uint32_t)old;
+    if (pos < kChunkRecs) {
+        store_rec(pool + (size_t)c * kChunkRecs + pos, r);
+        if (pos == kChunkRecs / 2) {            // reserve the successor ahead of need
+            const uint32_t n = reserve_chunk(RA);
+            if (n != kNoChunk) atomicCAS(&nxt[b], kNoChunk, n);   // a spare stays unused
+        }
+        return;
     }
-    __syncwarp();
-    if (lane == 0) scnt[b] = 0;
+    if (pos == kChunkRecs) {                    // this lane installs the next chunk
+        uint32_t n = atomicExch(&nxt[b], kNoChunk);
+        if (n == kNoChunk) n = reserve_chunk(RA);
+        if (n != kNoChunk) {
+            RA.chunk_bin[n] = b;
+            store_rec(pool + (size_t)n * kChunkRecs, r);
+            atomicExch(&cur[b], ((unsigned long long)n << 32) | 1ull);
+            return;
+        }
+        atomicExch(&cur[b], ((unsigned long long)kNoChunk << 32) | kChunkRecs);
+    }
+    apply_record(RA, r);
+}
+
+// Row-per-lane enumeration of the terms of a_k b_k.  A warp holds a batch of
+// up to 32 entries of a_k (one per lane; a batch of L < 32 rows is held
+// G = 32 / L times, so G columns run per step) and a batch of up to 32
+// entries of b_k, each with its side hash and dense-tier ranks.  A step
+// pairs every row with column m + sub of the batch, taking the column's
+// values from its lane by shuffle.  The warp takes tiles of outer products
+// from a global counter, so warps never wait on each other for work.
+struct RowLane {
+    int64_t k;                    // current outer product
+    int64_t a0, b0;               // first entries of a_k and b_k
+    int32_t left;                 // outer products left in the tile after k
+    int32_t na, nb;               // lengths of a_k and b_k
+    int32_t abase, bbase;         // first row / column of the batches (offsets in a_k, b_k)
+    int32_t m, mcount, G;         // next column of the batch, its size, columns per step
+    bool done;
+    // this lane's row of the batch
+    uint32_t i, ha, rank, wrank;
+    float wa;
+    int32_t sub, rpos;            // column offset within a step; row position in a_k
+    bool va;
+    // this lane's entry of the column batch (j = ~0u: none)
+    uint32_t jl, hbl, rbl, wbl;
+    float bl;
+};
+
+__device__ __forceinline__ void rl_load_rows(RowLane &st, const AccumulateArgs &A, int lane) {
+    const int32_t L = min(32, st.na - st.abase);
+    st.G = 32 / L;
+    st.sub = lane / L;
+    st.rpos = st.abase + (lane - st.sub * L);
+    const int64_t x = st.a0 + st.rpos;
+    st.va = false;
+    st.i = 0;
+    st.ha = 0;
+    st.rank = st.wrank = 0xFFFFu;
+    st.wa = 1.0f;
+    if (st.sub < st.G) {
+        const uint32_t i = (uint32_t)__ldg(A.a_idx + x);
+        if (i < (uint32_t)A.n_rows) {
+            st.va = true;
+            st.i = i;
+            st.ha = side_hash(A.hp.ha, i);
+            if (A.hot_rank_a) st.rank = __ldg(A.hot_rank_a + i);
+            if (A.warm_rank_a) st.wrank = __ldg(A.warm_rank_a + i);
+            if (A.a_val) st.wa = __ldg(A.a_val + x);
+        } else if (A.debug_checks) {
+            atomicOr(&A.tv.dc->status, kStatusBadIndex);
+        }
+    }
+}
+
+__device__ __forceinline__ void rl_load_cols(RowLane &st, const AccumulateArgs &A, int lane) {
+    st.mcount = min(32, st.nb - st.bbase);
+    st.m = 0;
+    st.jl = ~0u;
+    st.hbl = 0;
+    st.rbl = st.wbl = 0xFFFFu;
+    st.bl = 1.0f;
+    if (lane < st.mcount) {
+        const int64_t y = st.b0 + st.bbase + lane;
+        const uint32_t j = (uint32_t)__ldg(A.b_idx + y);
+        if (j < (uint32_t)A.n_cols) {
+            st.jl = j;
+            st.hbl = side_hash(A.hp.hb, j);
+            if (A.hot_rank_b) st.rbl = __ldg(A.hot_rank_b + j);
+            if (A.warm_rank_b) st.wbl = __ldg(A.warm_rank_b + j);
+            if (A.b_val) st.bl = __ldg(A.b_val + y);
+        } else if (A.debug_checks) {
+            atomicOr(&A.tv.dc->status, kStatusBadIndex);
+        }
+    }
+}
+
+// First column of the batch for the current row batch: with T^T T above the
+// diagonal on sorted lists, only columns after the batch's first row.
+__device__ __forceinline__ int32_t rl_col_start(const RowLane &st, const AccumulateArgs &A) {
+    return A.sym_upper ? st.abase + 1 : 0;
+}
+
+// Make (m < mcount) hold for a loaded row and column batch; false when the
+// warp's work is exhausted.  Warp-uniform.
+__device__ __forceinline__ bool rl_advance(RowLane &st, const AccumulateArgs &A, int lane) {
+    while (true) {
+        if (st.m < st.mcount) return true;
+        if (st.abase < st.na) {
+            st.bbase += 32;
+            if (st.bbase >= st.nb) {
+                st.abase += 32;
+                if (st.abase >= st.na) continue;
+                rl_load_rows(st, A, lane);
+                st.bbase = rl_col_start(st, A);
+                if (st.bbase >= st.nb) { st.mcount = 0; st.m = 0; continue; }
+            }
+            rl_load_cols(st, A, lane);
+            continue;
+        }
+        if (st.left > 0) {
+            ++st.k;
+            --st.left;
+        } else {
+            unsigned int item = 0;
+            if (lane == 0) item = atomicAdd(&A.tv.dc->work_next, 1u);
+            item = __shfl_sync(kFull, item, 0);
+            if (item >= A.n_tiles) { st.done = true; return false; }
+            st.k = (int64_t)item * A.tile;
+            st.left = (int32_t)(min((int64_t)A.K, st.k + (int64_t)A.tile) - st.k) - 1;
+        }
+        st.a0 = __ldg(A.a_ptr + st.k);
+        st.na = (int32_t)(__ldg(A.a_ptr + st.k + 1) - st.a0);
+        st.b0 = __ldg(A.b_ptr + st.k);
+        st.nb = (int32_t)(__ldg(A.b_ptr + st.k + 1) - st.b0);
+        st.abase = st.na;                       // inactive until both sides are non-empty
+        st.mcount = st.m = 0;
+        if (st.na == 0 || st.nb == 0) continue;
+        st.abase = 0;
+        rl_load_rows(st, A, lane);
+        st.bbase = rl_col_start(st, A);
+        if (st.bbase >= st.nb) continue;
+        rl_load_cols(st, A, lane);
+    }
 }
 
 template <int VT>
 __global__ void __launch_bounds__(kThreads, 2) k_route(RouteArgs RA) {
     typedef typename RecT<VT>::type R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *stage = (R *)smem_raw;
-    unsigned int *scnt = (unsigned int *)(stage + (size_t)RA.B * RA.R_s);
-    unsigned int *ready = scnt + RA.B;          // two lists of bins that reached the threshold
-    unsigned int *ctrl = ready + 2 * RA.B;      // ctrl[0] work item, ctrl[1..2] list counts
+    unsigned long long *cur = (unsigned long long *)smem_raw;
+    unsigned int *nxt = (unsigned int *)(cur + RA.B);
+    unsigned int *core = nxt + RA.B;            // core_H x (core_H + 1) counters (padded rows)
     const AccumulateArgs &A = RA.acc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t b = threadIdx.x; b < RA.B; b += kThreads) scnt[b] = 0;
-    if (threadIdx.x == 0) ctrl[1] = ctrl[2] = 0;
+    const uint32_t H = RA.core_H, Hp = RA.core_H + 1;
+    for (uint32_t b = threadIdx.x; b < RA.B; b += kThreads) {
+        cur[b] = ((unsigned long long)kNoChunk << 32) | kChunkRecs;   // full: first append installs
+        nxt[b] = kNoChunk;
+    }
+    for (uint32_t x = threadIdx.x; x < H * Hp; x += kThreads) core[x] = 0u;
     __syncthreads();
-    uint32_t parity = 0;
-    const uint32_t thr = RA.R_s / 2 > 0 ? RA.R_s / 2 : 1;
+    const uint32_t pmask = A.hp.ha.mask;
+    const bool filter = A.part_lo != 0u || A.part_hi != 0xFFFFFFFFu;
     unsigned long long my_terms = 0;
-    while (true) {
-        if (threadIdx.x == 0) ctrl[0] = atomicAdd(&A.tv.dc->work_next, 1u);
-        __syncthreads();
-        const unsigned int item = ctrl[0];
-        __syncthreads();
-        if (item >= A.n_tiles) break;
-        WarpEnum st;
-        st.k = (int64_t)item * A.tile + warp - kWarps;
-        st.k_hi = min((int64_t)A.K, (int64_t)(item + 1) * A.tile);
-        st.has_batch = false;
-        st.done = false;
-        st.total = 0;
-        st.pos = 0;
-        while (true) {
-            unsigned int *rlist = ready + parity * RA.B;
-            unsigned int *rcount = &ctrl[1 + parity];
-            for (int r = 0; r < kRouteChunks; ++r) {
-                if (st.done || !advance(st, A, nullptr, 0u, A.hp.ha.mask + 1u, lane)) break;
-                uint32_t oi, j;
-                float owa, wb;
-                int owner;
-                bool valid = next_term(st, A, lane, VT, oi, j, owa, wb, &owner);
-                const uint32_t orank = __shfl_sync(kFull, st.my_rank, owner);
-                const uint32_t owrank = __shfl_sync(kFull, st.my_wrank, owner);
-                my_terms += valid ? 1 : 0;
-                if (VT == CRP_I32 && valid && dense_tiers(A, orank, owrank, oi, j, 1u))
-                    valid = false;
-                if (valid) {
-                    const unsigned long long key = make_key(oi, j);
-                    const uint32_t b = partition_hash(A.hp, oi, j) >> RA.B_shift;
-                    R rec;
-                    if constexpr (VT == CRP_I32) {
-                        rec = key;
-                    } else {
-                        rec.key = key;
-                        rec.p = __fmul_rn(owa, wb);
-                        rec.e = __fmaf_rn(owa, wb, -rec.p);
-                    }
-                    const unsigned int pos = atomicAdd(&scnt[b], 1u);
-                    if (pos < RA.R_s) stage[(size_t)b * RA.R_s + pos] = rec;
-                    else bin_append(RA, b, rec);
-                    if (pos == thr - 1) rlist[atomicAdd(rcount, 1u)] = b;
-                }
+    RowLane st;
+    st.k = st.a0 = st.b0 = 0;
+    st.left = st.na = st.nb = st.abase = st.bbase = 0;
+    st.m = st.mcount = 0;
+    st.G = 1;
+    st.done = false;
+    while (rl_advance(st, A, lane)) {
+        const int32_t c = st.m + st.sub;
+        const int src = c & 31;
+        const uint32_t j = __shfl_sync(kFull, st.jl, src);
+        const uint32_t hb = __shfl_sync(kFull, st.hbl, src);
+        const uint32_t rb = __shfl_sync(kFull, st.rbl, src);
+        const uint32_t wbk = __shfl_sync(kFull, st.wbl, src);
+        const float bv = __shfl_sync(kFull, st.bl, src);
+        const int32_t cpos = st.bbase + c;
+        st.m += st.G;
+        bool valid = st.va && c < st.mcount && j != ~0u;
+        if (A.mode == CRP_UPPER && !(st.i < j)) valid = false;
+        if (A.sym_upper && cpos <= st.rpos) valid = false;
+        const uint32_t p = (st.ha + hb) & pmask;
+        if (filter && (p < A.part_lo || p >= A.part_hi)) valid = false;
+        my_terms += valid ? 1 : 0;
+        if (VT == CRP_I32 && valid) {
+            if (st.rank < A.hot_R && rb < A.hot_R) {
+                if (st.rank < H && rb < H) atomicAdd(&core[st.rank * Hp + rb], 1u);
+                else atomicAdd(&A.hot_block[st.rank * A.hot_R + rb], 1u);
+                valid = false;
+            } else if (st.wrank < A.warm_W) {
+                atomicAdd(&A.warm_a[(size_t)st.wrank * A.n_cols + j], 1u);
+                valid = false;
+            } else if (wbk < A.warm_W) {
+                atomicAdd(&A.warm_b[(size_t)wbk * A.n_rows + st.i], 1u);
+                valid = false;
             }
-            const int more = __syncthreads_or(st.done ? 0 : 1);
-            const unsigned int nready = *rcount;
-            for (unsigned int q = warp; q < nready; q += kWarps)
-                flush_bin<VT>(RA, stage, scnt, rlist[q], lane);
-            if (threadIdx.x == 0) ctrl[2 - parity] = 0;   // the other list, for the next round
-            parity ^= 1u;
-            __syncthreads();
-            if (!more) break;
+        }
+        if (valid) {
+            R rec;
+            if constexpr (VT == CRP_I32) {
+                rec = make_key(st.i, j);
+            } else {
+                rec.key = make_key(st.i, j);
+                rec.p = __fmul_rn(st.wa, bv);
+                rec.e = __fmaf_rn(st.wa, bv, -rec.p);
+            }
+            bin_append(RA, cur, nxt, p >> RA.B_shift, rec);
         }
     }
-    for (uint32_t b = warp; b < RA.B; b += kWarps) flush_bin<VT>(RA, stage, scnt, b, lane);
+    // close this CTA's chunks: mark the unused tail of each current chunk;
+    // add the core counters into the hot block
+    __syncthreads();
+    for (uint32_t x = threadIdx.x; x < H * H; x += kThreads) {
+        const uint32_t ri = x / H, rj = x - ri * H;
+        const unsigned int v = core[ri * Hp + rj];
+        if (v) atomicAdd(&A.hot_block[ri * A.hot_R + rj], v);
+    }
+    R *pool = (R *)RA.pool;
+    for (uint32_t b = warp; b < RA.B; b += kWarps) {
+        const unsigned long long w = cur[b];
+        const uint32_t c = (uint32_t)(w >> 32), pos = (uint32_t)w;
+        if (c == kNoChunk) continue;
+        for (uint32_t x = pos + lane; x < kChunkRecs; x += 32)
+            set_empty(pool + (size_t)c * kChunkRecs + x);
+    }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) my_terms += __shfl_down_sync(kFull, my_terms, d);
     if (lane == 0 && my_terms) atomicAdd(&A.tv.dc->terms, my_terms);
 }
 
-// chunk_prefix[b] = number of CH-record chunks in bins [0, b); one CTA.
+// Chunks per bin: count[b] over the installed chunks (chunk_bin != ~0u).
+__global__ void k_chunk_count(const unsigned int *chunk_bin, const unsigned int *chunk_next,
+                              uint32_t n_chunks, uint32_t B, unsigned int *count) {
+    extern __shared__ unsigned int hist[];
+    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const uint32_t used = min(*chunk_next, n_chunks);
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < used; c += gridDim.x * blockDim.x) {
+        const unsigned int b = chunk_bin[c];
+        if (b != kNoChunk) atomicAdd(&hist[b], 1u);
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x)
+        if (hist[b]) atomicAdd(&count[b], hist[b]);
+}
+
+// start[b] = chunks in bins [0, b) (exclusive scan of count, B + 1 entries);
+// fill[b] = start[b].  One CTA of 1024 threads.
 __global__ void __launch_bounds__(1024)
-k_bin_chunks(const unsigned long long *bin_cnt, const unsigned long long *bin_cap, uint32_t B,
-             uint32_t CH, unsigned int *chunk_prefix) {
+k_chunk_scan(const unsigned int *count, uint32_t B, unsigned int *start, unsigned int *fill) {
     __shared__ unsigned int part[1024];
     const uint32_t per = (B + 1023) / 1024;
     const uint32_t b0 = threadIdx.x * per;
     unsigned int local = 0;
-    for (uint32_t b = b0; b < b0 + per && b < B; ++b) {
-        unsigned long long n = bin_cnt[b] < bin_cap[b] ? bin_cnt[b] : bin_cap[b];
-        local += (unsigned int)((n + CH - 1) / CH);
-    }
+    for (uint32_t b = b0; b < b0 + per && b < B; ++b) local += count[b];
     part[threadIdx.x] = local;
     __syncthreads();
     for (int d = 1; d < 1024; d <<= 1) {
@@ -195,22 +364,32 @@ k_bin_chunks(const unsigned long long *bin_cnt, const unsigned long long *bin_ca
     }
     unsigned int run = part[threadIdx.x] - local;
     for (uint32_t b = b0; b < b0 + per && b < B; ++b) {
-        chunk_prefix[b] = run;
-        unsigned long long n = bin_cnt[b] < bin_cap[b] ? bin_cnt[b] : bin_cap[b];
-        run += (unsigned int)((n + CH - 1) / CH);
+        start[b] = run;
+        fill[b] = run;
+        run += count[b];
     }
-    if (threadIdx.x == 1023) chunk_prefix[B] = part[1023];
+    if (threadIdx.x == 1023) start[B] = part[1023];
 }
 
-// Each warp takes chunks of CH records (bins in order, so all warps work on
-// one or two groups' table regions at a time) and applies them; no CTA-wide
-// barriers.
+// order[] = installed chunk ids grouped by bin.
+__global__ void k_chunk_scatter(const unsigned int *chunk_bin, const unsigned int *chunk_next,
+                                uint32_t n_chunks, unsigned int *fill, unsigned int *order) {
+    const uint32_t used = min(*chunk_next, n_chunks);
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < used; c += gridDim.x * blockDim.x) {
+        const unsigned int b = chunk_bin[c];
+        if (b != kNoChunk) order[atomicAdd(&fill[b], 1u)] = c;
+    }
+}
+
+// Each warp takes one chunk at a time, in bin order (so all warps work on
+// one or two groups' table regions at a time), and applies its records; no
+// CTA-wide barriers.
 template <int VT>
 __global__ void __launch_bounds__(kThreads, 2)
-k_apply(RouteArgs RA, const unsigned int *__restrict__ chunk_prefix, uint32_t CH) {
+k_apply(RouteArgs RA) {
     typedef typename RecT<VT>::type R;
-    const R *bins = (const R *)RA.bins;
-    const unsigned int total = chunk_prefix[RA.B];
+    const R *pool = (const R *)RA.pool;
+    const unsigned int total = RA.start[RA.B];
     const int lane = threadIdx.x & 31;
     unsigned long long applied = 0;
     while (true) {
@@ -218,18 +397,12 @@ k_apply(RouteArgs RA, const unsigned int *__restrict__ chunk_prefix, uint32_t CH
         if (lane == 0) item = atomicAdd(&RA.acc.tv.dc->work_next, 1u);
         item = __shfl_sync(kFull, item, 0);
         if (item >= total) break;
-        uint32_t lo = 0, hi = RA.B;
-        while (hi - lo > 1) {
-            uint32_t mid = (lo + hi) >> 1;
-            if (chunk_prefix[mid] <= item) lo = mid; else hi = mid;
-        }
-        const uint32_t b = lo;
-        const unsigned long long n = RA.bin_cnt[b] < RA.bin_cap[b] ? RA.bin_cnt[b] : RA.bin_cap[b];
-        const unsigned long long start = (unsigned long long)(item - chunk_prefix[b]) * CH;
-        const unsigned long long end = start + CH < n ? start + CH : n;
-        const unsigned long long off = RA.bin_off[b];
-        for (unsigned long long x = start + lane; x < end; x += 32) {
-            apply_record(RA, load_stream(bins + off + x));
+        const R *chunk = pool + (size_t)RA.order[item] * kChunkRecs;
+#pragma unroll 2
+        for (uint32_t x = lane; x < kChunkRecs; x += 32) {
+            const R r = load_stream(chunk + x);
+            if (rec_key(r) == kEmptyKey) continue;
+            apply_record(RA, r);
             ++applied;
         }
     }
@@ -238,13 +411,12 @@ k_apply(RouteArgs RA, const unsigned int *__restrict__ chunk_prefix, uint32_t CH
     if (lane == 0 && applied) atomicAdd(&RA.acc.tv.dc->flushed, applied);
 }
 
-size_t route_smem_bytes(int value_type, uint32_t B, uint32_t R_s) {
-    const size_t rec = value_type == CRP_I32 ? 8 : 16;
-    return (size_t)B * R_s * rec + (size_t)B * 12 + 16;
+size_t route_smem_bytes(uint32_t B, uint32_t core_H) {
+    return (size_t)B * 12 + (size_t)core_H * (core_H + 1) * 4;
 }
 
 cudaError_t launch_route(const RouteArgs &RA, int grid, cudaStream_t s) {
-    const size_t smem = route_smem_bytes(RA.acc.tv.value_type, RA.B, RA.R_s);
+    const size_t smem = route_smem_bytes(RA.B, RA.core_H);
     cudaError_t e;
     if (RA.acc.tv.value_type == CRP_I32) {
         e = cudaFuncSetAttribute(k_route<CRP_I32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -260,17 +432,28 @@ cudaError_t launch_route(const RouteArgs &RA, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_apply(const RouteArgs &RA, unsigned int *chunk_prefix, uint32_t CH, int grid,
+// Group the installed chunks by bin (count, scan, scatter), then apply them.
+// count must hold B zeroed words; start B + 1, fill B.
+cudaError_t launch_apply(const RouteArgs &RA, unsigned int *count, unsigned int *fill, int grid,
                          cudaStream_t s) {
-    k_bin_chunks<<<1, 1024, 0, s>>>(RA.bin_cnt, RA.bin_cap, RA.B, CH, chunk_prefix);
+    const int cgrid = grid > 0 ? grid : 1;
+    k_chunk_count<<<cgrid, 1024, RA.B * sizeof(unsigned int), s>>>(
+        RA.chunk_bin, RA.chunk_next, RA.n_chunks, RA.B, count);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_chunk_scan<<<1, 1024, 0, s>>>(count, RA.B, RA.start, fill);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_chunk_scatter<<<cgrid, 1024, 0, s>>>(RA.chunk_bin, RA.chunk_next, RA.n_chunks, fill,
+                                           RA.order);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(&RA.acc.tv.dc->work_next, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     if (RA.acc.tv.value_type == CRP_I32)
-        k_apply<CRP_I32><<<grid, kThreads, 0, s>>>(RA, chunk_prefix, CH);
+        k_apply<CRP_I32><<<grid, kThreads, 0, s>>>(RA);
     else
-        k_apply<CRP_F32_COMP><<<grid, kThreads, 0, s>>>(RA, chunk_prefix, CH);
+        k_apply<CRP_F32_COMP><<<grid, kThreads, 0, s>>>(RA);
     return cudaGetLastError();
 }
 

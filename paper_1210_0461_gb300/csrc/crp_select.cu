@@ -79,6 +79,41 @@ cudaError_t select_top(const uint32_t *key, int64_t n, int64_t K, int64_t *out,
 }
 
 
+// Reorder items[0, R) by descending cnt[item] (ties in any order): one CTA,
+// bitonic sort of R <= 4096 keys (cnt << 32 | 1 << 31 | item) in shared memory.
+__global__ void __launch_bounds__(1024) k_order_by_count(int64_t *items, const unsigned int *cnt,
+                                                         uint32_t R) {
+    __shared__ unsigned long long key[4096];
+    uint32_t n = 1;
+    while (n < R) n <<= 1;
+    for (uint32_t t = threadIdx.x; t < n; t += blockDim.x)
+        key[t] = t < R ? ((unsigned long long)cnt[items[t]] << 32) | (1ull << 31) |
+                             (unsigned long long)items[t]
+                       : 0ull;
+    __syncthreads();
+    for (uint32_t size = 2; size <= n; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
+                const uint32_t u = t ^ stride;
+                if (u > t) {
+                    const bool desc = (t & size) == 0;
+                    const unsigned long long a = key[t], b = key[u];
+                    if (desc ? a < b : a > b) { key[t] = b; key[u] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (uint32_t t = threadIdx.x; t < R; t += blockDim.x)
+        items[t] = (int64_t)(key[t] & 0x7FFFFFFFull);
+}
+
+cudaError_t order_by_count(int64_t *items, const unsigned int *cnt, uint32_t R, cudaStream_t s) {
+    if (R == 0 || R > 4096) return R == 0 ? cudaSuccess : cudaErrorInvalidValue;
+    k_order_by_count<<<1, 1024, 0, s>>>(items, cnt, R);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_item_counts(const int32_t *idx, int64_t nnz, int32_t n_items, unsigned int *cnt,
                                cudaStream_t s) {
     if (nnz <= 0) return cudaSuccess;
