@@ -482,7 +482,8 @@ __global__ void k_rehash(const Slot *old_slots, uint64_t old_off, uint64_t old_c
          x += (uint64_t)gridDim.x * blockDim.x) {
         Slot s = old_slots[old_off + x];
         if (s.key == kEmptyKey) continue;
-        unsigned long long h = slot_mix(s.key) & new_mask;
+        // same probe order as table_update: linear from the 4-slot bucket
+        unsigned long long h = slot_mix(s.key) & new_mask & ~3ull;
         for (unsigned long long probe = 0; probe <= new_mask; ++probe) {
             Slot *d = tv.slots + new_off + h;
             unsigned long long prev = atomicCAS(&d->key, kEmptyKey, s.key);

@@ -646,11 +646,13 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
     CRP_CUDA(cudaMemcpyAsync(&terms, pl->d_scratch64, 8, cudaMemcpyDeviceToHost, pl->stream));
     CRP_CUDA(cudaStreamSynchronize(pl->stream));
     pl->launches += 1;
-    // groups of partitions whose table region is ~48 MB or less
+    // groups of partitions whose table region is about 96 MB or more (the
+    // record chunks of every CTA stay open in L2 for each group, so more
+    // groups cost the enumeration more than they save the apply phase)
     const uint64_t table_bytes = pl->n_slots * sizeof(Slot);
-    uint64_t want = (table_bytes + (48ull << 20) - 1) / (48ull << 20);
+    const uint64_t want = std::max<uint64_t>(table_bytes / (96ull << 20), 1);
     uint32_t Bn = 1;
-    while (Bn < want && Bn < P) Bn <<= 1;
+    while (2ull * Bn <= want && Bn < P) Bn <<= 1;
     if (pl->d.groups) Bn = pl->G;  // explicit partition groups = bins
     Bn = std::min<uint32_t>(Bn, 8192);   // per-CTA chunk state lives in shared memory
     const int grid = 2 * pl->sm_count;

@@ -2,7 +2,7 @@
 // exact product (partition count P, variant: on-chip combining table / direct
 // HBM updates / routed two-phase with 128, 256 or size-derived bins, dense
 // tiers: hot blocks of 1024 or 4096 items, or 2048 items plus warm stripes of
-// 64 items, tile of outer products per work item) on a prefix of the caller's
+// 32 or 64 items, tile of outer products per work item) on a prefix of the caller's
 // outer products, and keeps the fastest.  Results are cached in a text file
 // keyed by device name and a shape class of the input (log2 buckets of K,
 // n_rows, n_cols and of the mean terms per outer product, plus value type and
@@ -124,7 +124,7 @@ extern "C" crp_status crp_autotune(const crp_plan_desc *base, const crp_sparse *
         cands.push_back({P, 0, 64, 8192, CRP_PLAN_ROUTED, 0, 0});
         if (ints) {
             // hot block alone, and a smaller hot block with warm stripes
-            const uint32_t tiers[3][2] = {{1024u, 0u}, {4096u, 0u}, {2048u, 64u}};
+            const uint32_t tiers[4][2] = {{1024u, 0u}, {4096u, 0u}, {2048u, 32u}, {2048u, 64u}};
             for (const auto &hw : tiers) {
                 cands.push_back({P, 1, 64, 8192, CRP_PLAN_DIRECT, hw[0], hw[1]});
                 for (uint32_t g : {0u, 128u, 256u})

@@ -100,22 +100,32 @@ __device__ __forceinline__ void table_update(const TableView &tv, uint32_t p,
         atomicOr(&tv.dc->status, kStatusNotOwned);
         return;
     }
-    unsigned long long h = slot_mix(key) & mask;
-    for (unsigned long long probe = 0; probe <= mask; ++probe) {
+    // Linear probing from the 4-slot bucket holding slot_mix(key): the four
+    // keys of a bucket (64 bytes) are loaded together, so most updates take
+    // one round trip even at high load.  Partition capacities are powers of
+    // two >= 64.
+    unsigned long long h = slot_mix(key) & mask & ~3ull;
+    for (unsigned long long probe = 0; probe <= mask; probe += 4) {
         Slot *s = tv.slots + off + h;
-        unsigned long long k = s->key;
-        if (k == kEmptyKey) {
-            k = atomicCAS(&s->key, kEmptyKey, key);
-            if (k == kEmptyKey) k = key;
+        unsigned long long k4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) k4[q] = s[q].key;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            unsigned long long k = k4[q];
+            if (k == kEmptyKey) {
+                k = atomicCAS(&s[q].key, kEmptyKey, key);
+                if (k == kEmptyKey) k = key;
+            }
+            if (k == key) {
+                if (tv.value_type == CRP_I32)
+                    atomicAdd((unsigned int *)&s[q].val, (unsigned int)v);
+                else
+                    atomicAdd((double *)&s[q].val, __longlong_as_double((long long)v));
+                return;
+            }
         }
-        if (k == key) {
-            if (tv.value_type == CRP_I32)
-                atomicAdd((unsigned int *)&s->val, (unsigned int)v);
-            else
-                atomicAdd((double *)&s->val, __longlong_as_double((long long)v));
-            return;
-        }
-        h = (h + 1) & mask;
+        h = (h + 4) & mask;
     }
     atomicOr(&tv.part_full[p], 1u);
     atomicOr(&tv.dc->status, kStatusTableFull);
