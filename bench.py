@@ -550,7 +550,8 @@ def main():
     entries = st["entries"]
     alg_bytes = (terms_step * BYTES_PER_TERM_UPDATE + dT.nbytes() + entries * SLOT_BYTES)
     achieved = alg_bytes / (acc / 1e3) / 1e9
-    tr = profiled_traffic(f"c2:{args.mode}:P{args.P}:G{args.groups}:S{args.smem_slots}")
+    tr = profiled_traffic(f"c2:{args.mode}:P{args.P}:G{args.groups}:S{args.smem_slots}"
+                          f":H{args.hot}:W{args.warm}")
     traffic = tr * terms_step if tr is not None else None
 
     # ---- end to end through the C ABI from pinned host buffers ----

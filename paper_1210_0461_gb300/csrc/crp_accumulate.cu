@@ -552,7 +552,10 @@ __global__ void k_warm_flush(unsigned int *stripe, uint32_t W, int32_t n_other,
         table_update(tv, partition_hash(hp, i, j), make_key(i, j), c);
         ++n;
     }
-    if (n) atomicAdd(flushed, n);
+    // one atomic per warp: a counter taken by every thread serialises on one address
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) n += __shfl_down_sync(0xffffffffu, n, d);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(flushed, n);
 }
 
 cudaError_t launch_warm_flush(unsigned int *stripe, uint32_t W, int32_t n_other,
@@ -579,7 +582,10 @@ __global__ void k_hot_flush(unsigned int *hot, uint32_t R, const int64_t *items_
         table_update(tv, partition_hash(hp, i, j), make_key(i, j), c);
         ++n;
     }
-    if (n) atomicAdd(flushed, n);
+    // one atomic per warp: a counter taken by every thread serialises on one address
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) n += __shfl_down_sync(0xffffffffu, n, d);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(flushed, n);
 }
 
 __global__ void k_hot_ranks(uint16_t *rank, int32_t n, const int64_t *items, uint32_t R) {

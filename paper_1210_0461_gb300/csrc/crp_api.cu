@@ -1014,24 +1014,6 @@ extern "C" crp_status crp_topk(crp_plan *pl, int32_t k, uint32_t flags, int32_t 
     const int upper = (flags & CRP_TOPK_UPPER) ? 1 : 0;
     cudaStream_t s = pl->stream;
     const int vt = pl->summary ? kVTSummary : pl->d.value_type;
-    CRP_CUDA(launch_topk_hist(pl->slots, pl->n_slots, vt, upper, pl->d_topk_hist, s));
-    pl->launches += 1;
-    std::vector<unsigned int> hist(kTopkBuckets);
-    CRP_CUDA(cudaMemcpyAsync(hist.data(), pl->d_topk_hist, kTopkBuckets * 4, cudaMemcpyDeviceToHost,
-                             s));
-    CRP_CUDA(cudaStreamSynchronize(s));
-    uint64_t cum = 0;
-    int b = kTopkBuckets - 1;
-    for (; b >= 0; --b) {
-        cum += hist[b];
-        if (cum >= (uint64_t)k) break;
-    }
-    if (b < 0) b = 0;
-    const uint64_t n_c = cum;
-    if (n_c == 0) return CRP_OK;
-    if (n_c > 0xffffffffull) return fail(CRP_EUNSUPPORTED, "too many top-k candidates");
-    TopkCand *cand = nullptr, *sel = nullptr, *keep = nullptr;
-    CRP_CUDA(cudaMalloc(&cand, n_c * sizeof(TopkCand)));
     unsigned int *cnt = pl->d_topk_hist + kTopkBuckets;  // 3 counters + 256-bin hist after
     unsigned int *dhist = cnt + 4;
     crp_status st = CRP_OK;
@@ -1040,9 +1022,52 @@ extern "C" crp_status crp_topk(crp_plan *pl, int32_t k, uint32_t flags, int32_t 
             st = fail(CRP_ECUDA, std::string("topk: ") + cudaGetErrorString(e));
         return st == CRP_OK;
     };
-    cuda_ok(launch_topk_collect(pl->slots, pl->n_slots, vt, upper, (unsigned)b, cand,
-                                cnt, (unsigned)n_c, s));
-    pl->launches += 1;
+    // candidates: the slots at or above a histogram bucket.  A large table is
+    // first tried with a 1/32 sample histogram and a bucket expected to hold
+    // about 2k + 256 slots; k or more collected slots at or above a bucket
+    // contain the top k, otherwise the exact histogram decides.
+    const int shift = pl->n_slots >= (1ull << 26) ? 5 : 0;
+    TopkCand *cand = nullptr, *sel = nullptr, *keep = nullptr;
+    uint64_t n_c = 0;
+    std::vector<unsigned int> hist(kTopkBuckets);
+    for (int sh : {shift, 0}) {
+        CRP_CUDA(launch_topk_hist(pl->slots, pl->n_slots, vt, upper, sh, pl->d_topk_hist, s));
+        pl->launches += 1;
+        CRP_CUDA(cudaMemcpyAsync(hist.data(), pl->d_topk_hist, kTopkBuckets * 4,
+                                 cudaMemcpyDeviceToHost, s));
+        CRP_CUDA(cudaStreamSynchronize(s));
+        const uint64_t want = sh ? (((uint64_t)2 * k + 256) >> sh) + 1 : (uint64_t)k;
+        uint64_t cum = 0;
+        int b = kTopkBuckets - 1;
+        for (; b >= 0; --b) {
+            cum += hist[b];
+            if (cum >= want) break;
+        }
+        if (b < 0) {
+            if (sh) continue;   // the sample holds too few slots: take the exact histogram
+            b = 0;
+        }
+        if (cum == 0) break;
+        // capacity: the exact count, or twice the sampled estimate plus slack
+        const uint64_t cap = sh ? (cum << sh) * 2 + 4 * (uint64_t)k + 1024 : cum;
+        cudaFree(cand);
+        if (cap > 0xffffffffull) return fail(CRP_EUNSUPPORTED, "too many top-k candidates");
+        cand = nullptr;
+        CRP_CUDA(cudaMalloc(&cand, cap * sizeof(TopkCand)));
+        CRP_CUDA(launch_topk_collect(pl->slots, pl->n_slots, vt, upper, (unsigned)b, cand, cnt,
+                                     (unsigned)cap, s));
+        pl->launches += 1;
+        unsigned int got = 0;
+        CRP_CUDA(cudaMemcpyAsync(&got, cnt, 4, cudaMemcpyDeviceToHost, s));
+        CRP_CUDA(cudaStreamSynchronize(s));
+        n_c = got;
+        if (sh == 0 || (got >= (unsigned)k && got <= cap)) break;
+        n_c = 0;
+    }
+    if (n_c == 0) {
+        cudaFree(cand);
+        return CRP_OK;
+    }
     const TopkCand *final_c = cand;
     unsigned int final_sort = (unsigned int)n_c;  // candidates to sort
     unsigned int final_n = (unsigned int)std::min<uint64_t>(n_c, (uint64_t)k);

@@ -237,7 +237,7 @@ struct TopkCand {
     double wl;
 };
 cudaError_t launch_topk_hist(const Slot *slots, uint64_t n, int value_type, int upper_only,
-                             unsigned int *hist, cudaStream_t s);
+                             int sample_shift, unsigned int *hist, cudaStream_t s);
 cudaError_t launch_topk_collect(const Slot *slots, uint64_t n, int value_type, int upper_only,
                                 unsigned int bucket_lo, TopkCand *out, unsigned int *count,
                                 unsigned int cap, cudaStream_t s);

@@ -372,12 +372,37 @@ k_chunk_scan(const unsigned int *count, uint32_t B, unsigned int *start, unsigne
 }
 
 // order[] = installed chunk ids grouped by bin.
-__global__ void k_chunk_scatter(const unsigned int *chunk_bin, const unsigned int *chunk_next,
-                                uint32_t n_chunks, unsigned int *fill, unsigned int *order) {
+// order[] = installed chunk ids grouped by bin.  Each CTA takes spans of
+// kScatterSpan chunk ids, ranks them within their bins in shared memory and
+// reserves one run per bin with a single global atomic.
+constexpr uint32_t kScatterSpan = 4096;
+__global__ void __launch_bounds__(1024)
+k_chunk_scatter(const unsigned int *chunk_bin, const unsigned int *chunk_next, uint32_t n_chunks,
+                uint32_t B, unsigned int *fill, unsigned int *order) {
+    extern __shared__ unsigned int sm[];
+    unsigned int *hist = sm, *base = sm + B, *pk = sm + 2 * B;   // pk: bin | rank << 13
     const uint32_t used = min(*chunk_next, n_chunks);
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < used; c += gridDim.x * blockDim.x) {
-        const unsigned int b = chunk_bin[c];
-        if (b != kNoChunk) order[atomicAdd(&fill[b], 1u)] = c;
+    for (uint32_t c0 = blockIdx.x * kScatterSpan; c0 < used; c0 += gridDim.x * kScatterSpan) {
+        for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) hist[b] = 0u;
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < kScatterSpan; t += blockDim.x) {
+            const uint32_t c = c0 + t;
+            unsigned int v = ~0u;
+            if (c < used) {
+                const unsigned int b = chunk_bin[c];
+                if (b != kNoChunk) v = b | (atomicAdd(&hist[b], 1u) << 13);
+            }
+            pk[t] = v;
+        }
+        __syncthreads();
+        for (uint32_t b = threadIdx.x; b < B; b += blockDim.x)
+            if (hist[b]) base[b] = atomicAdd(&fill[b], hist[b]);
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < kScatterSpan; t += blockDim.x) {
+            const unsigned int v = pk[t];
+            if (v != ~0u) order[base[v & 0x1FFFu] + (v >> 13)] = c0 + t;
+        }
+        __syncthreads();
     }
 }
 
@@ -444,8 +469,12 @@ cudaError_t launch_apply(const RouteArgs &RA, unsigned int *count, unsigned int 
     k_chunk_scan<<<1, 1024, 0, s>>>(count, RA.B, RA.start, fill);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_chunk_scatter<<<cgrid, 1024, 0, s>>>(RA.chunk_bin, RA.chunk_next, RA.n_chunks, fill,
-                                           RA.order);
+    const size_t ssm = (2 * (size_t)RA.B + kScatterSpan) * sizeof(unsigned int);   // B <= 8192
+    e = cudaFuncSetAttribute(k_chunk_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ssm);
+    if (e != cudaSuccess) return e;
+    k_chunk_scatter<<<cgrid, 1024, ssm, s>>>(RA.chunk_bin, RA.chunk_next, RA.n_chunks, RA.B, fill,
+                                             RA.order);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(&RA.acc.tv.dc->work_next, 0, sizeof(unsigned int), s);

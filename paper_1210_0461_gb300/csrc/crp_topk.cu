@@ -1,9 +1,13 @@
 // Heaviest entries of the partition tables (Section 6: the task is to find
 // the largest entries of the product) and table export.
 //
-// crp_topk runs:  (1) one pass over all slots building a log-linear histogram
-// of the weights, (2) one pass collecting the slots at or above the bucket
-// that holds the k-th largest weight, (3) when that candidate set is still
+// crp_topk runs:  (1) a log-linear histogram of the weights, over a 1/32
+// sample of the slots for a large table, (2) one pass collecting the slots at
+// or above the bucket that the histogram puts at or below the k-th largest
+// weight (with a sample, a bucket expected to hold several times k; if fewer
+// than k slots come back, the full histogram is taken and the pass redone:
+// k collected slots at or above a bucket contain every slot of the top k),
+// (3) when that candidate set is still
 // larger than one CTA can sort, an MSD radix select over the 128-bit order
 // key (weight descending, then (i, j) ascending) on the candidates only, and
 // (4) a single-CTA bitonic sort of the k survivors that writes the output.
@@ -52,13 +56,17 @@ __host__ __device__ __forceinline__ unsigned int bucket_of(unsigned long long u)
 
 unsigned int topk_bucket_host(unsigned long long u) { return bucket_of(u); }
 
+// Histogram of the weights of all slots, or (sample_shift = s > 0) of the
+// first 32 slots of every 32 << s: a 2^-s sample read in whole 512-byte runs.
 __global__ void k_topk_hist(const Slot *__restrict__ slots, uint64_t n, int value_type,
-                            int upper_only, unsigned int *__restrict__ hist) {
+                            int upper_only, int sample_shift, unsigned int *__restrict__ hist) {
     __shared__ unsigned int h[kTopkBuckets];
     for (int t = threadIdx.x; t < kTopkBuckets; t += blockDim.x) h[t] = 0;
     __syncthreads();
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-         x += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t m = sample_shift ? ((n >> 5) >> sample_shift) << 5 : n;
+    for (uint64_t y = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; y < m;
+         y += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = sample_shift ? ((y >> 5) << (5 + sample_shift)) + (y & 31) : y;
         Slot s = slots[x];
         if (s.key == kEmptyKey) continue;
         if (upper_only && !((uint32_t)(s.key >> 32) < (uint32_t)s.key)) continue;
@@ -71,12 +79,12 @@ __global__ void k_topk_hist(const Slot *__restrict__ slots, uint64_t n, int valu
 }
 
 cudaError_t launch_topk_hist(const Slot *slots, uint64_t n, int value_type, int upper_only,
-                             unsigned int *hist, cudaStream_t s) {
+                             int sample_shift, unsigned int *hist, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * kTopkBuckets, s);
     if (e != cudaSuccess || n == 0) return e;
-    uint64_t blocks = (n + 511) / 512;
-    int grid = (int)(blocks < 4096 ? blocks : 4096);
-    k_topk_hist<<<grid, 512, 0, s>>>(slots, n, value_type, upper_only, hist);
+    uint64_t blocks = ((sample_shift ? n >> sample_shift : n) + 511) / 512;
+    int grid = (int)(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096);
+    k_topk_hist<<<grid, 512, 0, s>>>(slots, n, value_type, upper_only, sample_shift, hist);
     return cudaGetLastError();
 }
 

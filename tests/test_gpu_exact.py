@@ -119,6 +119,23 @@ def test_topk_full_mode_upper_flag_and_large_k(crp):
     plan.close()
 
 
+@pytest.mark.parametrize("cap", [1 << 21, 1 << 27])
+def test_topk_sampled_histogram_on_large_tables(crp, cap):
+    # tables of 2^26 slots or more take the top-k threshold from a 1/32 sample
+    # histogram (falling back to the exact one when the sample is too thin);
+    # the result must be the exact top k either way
+    T = ci.C1.generate()
+    Tc = O.Compressed.of(T)
+    ref = O.exact_product(Tc, Tc, O.FULL)
+    plan = _run(crp, T, T, 1000, 1000, 64, groups=1, flags=4 | 2, capacity_hint=cap)
+    assert plan.stats()["table_slots"] >= cap
+    for k, up in ((1, True), (10, False), (1000, True), (5000, False), (8192, True)):
+        ti, tj, tw, _ = plan.topk(k, upper=up)
+        ri, rj, rw = O.topk(ref.i, ref.j, ref.w, k, upper_only=up)
+        assert np.array_equal(ti, ri) and np.array_equal(tj, rj) and np.array_equal(tw, rw)
+    plan.close()
+
+
 def _random_case(seed, K, n_i, n_j, density, values):
     rng = np.random.default_rng(seed)
     ptrs, idxs = [], []
