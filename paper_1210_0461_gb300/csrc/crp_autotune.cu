@@ -1,6 +1,6 @@
 // Launch-configuration autotuner.  It times candidate configurations of the
 // exact product (partition count P, variant: on-chip combining table / direct
-// HBM updates / routed two-phase with 128, 256 or size-derived bins, dense
+// HBM updates / routed two-phase with bins derived from the table size, dense
 // tiers: hot blocks of 1024 or 4096 items, or 2048 items plus warm stripes of
 // 32 or 64 items, tile of outer products per work item) on a prefix of the caller's
 // outer products, and keeps the fastest.  Results are cached in a text file
@@ -125,10 +125,12 @@ extern "C" crp_status crp_autotune(const crp_plan_desc *base, const crp_sparse *
         if (ints) {
             // hot block alone, and a smaller hot block with warm stripes
             const uint32_t tiers[4][2] = {{1024u, 0u}, {4096u, 0u}, {2048u, 32u}, {2048u, 64u}};
+            // routed bins are left to the plan (groups = 0): it sizes them by
+            // the table, which grows with the input, so a choice made on a
+            // prefix carries over to the whole input
             for (const auto &hw : tiers) {
                 cands.push_back({P, 1, 64, 8192, CRP_PLAN_DIRECT, hw[0], hw[1]});
-                for (uint32_t g : {0u, 128u, 256u})
-                    if (g <= P) cands.push_back({P, g, 64, 8192, CRP_PLAN_ROUTED, hw[0], hw[1]});
+                cands.push_back({P, 0, 64, 8192, CRP_PLAN_ROUTED, hw[0], hw[1]});
             }
         }
     }
