@@ -648,9 +648,11 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
     pl->launches += 1;
     // groups of partitions whose table region is about 96 MB or more (the
     // record chunks of every CTA stay open in L2 for each group, so more
-    // groups cost the enumeration more than they save the apply phase)
+    // groups cost the enumeration more than they save the apply phase), but
+    // at least 256 groups: a CTA's appends to one group share one
+    // shared-memory word, and fewer groups make those atomics contend
     const uint64_t table_bytes = pl->n_slots * sizeof(Slot);
-    const uint64_t want = std::max<uint64_t>(table_bytes / (96ull << 20), 1);
+    const uint64_t want = std::max<uint64_t>(table_bytes / (96ull << 20), 256);
     uint32_t Bn = 1;
     while (2ull * Bn <= want && Bn < P) Bn <<= 1;
     if (pl->d.groups) Bn = pl->G;  // explicit partition groups = bins
@@ -714,7 +716,7 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
     RA.core_H = std::min<uint32_t>(RA.acc.hot_R, 128);
     CRP_CUDA(cudaMemsetAsync(&pl->dc->work_next, 0, sizeof(unsigned int), pl->stream));
     CRP_CUDA(cudaEventRecord(pl->ev0, pl->stream));
-    CRP_CUDA(launch_route(RA, grid, pl->stream));
+    CRP_CUDA(launch_route(RA, pl->sm_count, pl->stream));
     CRP_CUDA(cudaEventRecord(pl->evm, pl->stream));
     CRP_CUDA(launch_apply(RA, ctl + 1, ctl + 1 + Bn, grid, pl->stream));
     {
@@ -1057,11 +1059,15 @@ extern "C" crp_status crp_topk(crp_plan *pl, int32_t k, uint32_t flags, int32_t 
         CRP_CUDA(launch_topk_collect(pl->slots, pl->n_slots, vt, upper, (unsigned)b, cand, cnt,
                                      (unsigned)cap, s));
         pl->launches += 1;
+        if (sh == 0) {   // the exact histogram already counted the candidates
+            n_c = cum;
+            break;
+        }
         unsigned int got = 0;
         CRP_CUDA(cudaMemcpyAsync(&got, cnt, 4, cudaMemcpyDeviceToHost, s));
         CRP_CUDA(cudaStreamSynchronize(s));
         n_c = got;
-        if (sh == 0 || (got >= (unsigned)k && got <= cap)) break;
+        if (got >= (unsigned)k && got <= cap) break;
         n_c = 0;
     }
     if (n_c == 0) {

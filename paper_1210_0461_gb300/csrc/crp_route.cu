@@ -32,6 +32,10 @@
 namespace crp {
 
 constexpr uint32_t kNoChunk = 0xFFFFFFFFu;
+// k_route runs one CTA of 1024 threads per SM: the chunks a CTA keeps open
+// (one per bin) and the shared-memory core are shared by all its warps.
+constexpr int kRouteThreads = 1024;
+constexpr int kRouteWarps = kRouteThreads / 32;
 
 struct Rec16 {
     unsigned long long key;
@@ -243,7 +247,7 @@ __device__ __forceinline__ bool rl_advance(RowLane &st, const AccumulateArgs &A,
 }
 
 template <int VT>
-__global__ void __launch_bounds__(kThreads, 2) k_route(RouteArgs RA) {
+__global__ void __launch_bounds__(kRouteThreads, 1) k_route(RouteArgs RA) {
     typedef typename RecT<VT>::type R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long *cur = (unsigned long long *)smem_raw;
@@ -252,11 +256,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_route(RouteArgs RA) {
     const AccumulateArgs &A = RA.acc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t H = RA.core_H, Hp = RA.core_H + 1;
-    for (uint32_t b = threadIdx.x; b < RA.B; b += kThreads) {
+    for (uint32_t b = threadIdx.x; b < RA.B; b += kRouteThreads) {
         cur[b] = ((unsigned long long)kNoChunk << 32) | kChunkRecs;   // full: first append installs
         nxt[b] = kNoChunk;
     }
-    for (uint32_t x = threadIdx.x; x < H * Hp; x += kThreads) core[x] = 0u;
+    for (uint32_t x = threadIdx.x; x < H * Hp; x += kRouteThreads) core[x] = 0u;
     __syncthreads();
     const uint32_t pmask = A.hp.ha.mask;
     const bool filter = A.part_lo != 0u || A.part_hi != 0xFFFFFFFFu;
@@ -311,13 +315,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_route(RouteArgs RA) {
     // close this CTA's chunks: mark the unused tail of each current chunk;
     // add the core counters into the hot block
     __syncthreads();
-    for (uint32_t x = threadIdx.x; x < H * H; x += kThreads) {
+    for (uint32_t x = threadIdx.x; x < H * H; x += kRouteThreads) {
         const uint32_t ri = x / H, rj = x - ri * H;
         const unsigned int v = core[ri * Hp + rj];
         if (v) atomicAdd(&A.hot_block[ri * A.hot_R + rj], v);
     }
     R *pool = (R *)RA.pool;
-    for (uint32_t b = warp; b < RA.B; b += kWarps) {
+    for (uint32_t b = warp; b < RA.B; b += kRouteWarps) {
         const unsigned long long w = cur[b];
         const uint32_t c = (uint32_t)(w >> 32), pos = (uint32_t)w;
         if (c == kNoChunk) continue;
@@ -447,12 +451,12 @@ cudaError_t launch_route(const RouteArgs &RA, int grid, cudaStream_t s) {
         e = cudaFuncSetAttribute(k_route<CRP_I32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        k_route<CRP_I32><<<grid, kThreads, smem, s>>>(RA);
+        k_route<CRP_I32><<<grid, kRouteThreads, smem, s>>>(RA);
     } else {
         e = cudaFuncSetAttribute(k_route<CRP_F32_COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
-        k_route<CRP_F32_COMP><<<grid, kThreads, smem, s>>>(RA);
+        k_route<CRP_F32_COMP><<<grid, kRouteThreads, smem, s>>>(RA);
     }
     return cudaGetLastError();
 }
