@@ -80,6 +80,19 @@ __device__ __forceinline__ void summary_update(const TableView &tv, uint32_t p,
     spill_update(tv, key, v);
 }
 
+// The keys of the 4-slot bucket at s (64 bytes, 64-byte aligned: partition
+// capacities are powers of two >= 64 and tables start 256-byte aligned), in
+// two 32-byte loads.
+__device__ __forceinline__ void load_bucket_keys(const Slot *s, unsigned long long *k4) {
+    unsigned long long v0, v1;
+    asm volatile("ld.global.v4.u64 {%0, %1, %2, %3}, [%4];"
+                 : "=l"(k4[0]), "=l"(v0), "=l"(k4[1]), "=l"(v1)
+                 : "l"(s));
+    asm volatile("ld.global.v4.u64 {%0, %1, %2, %3}, [%4];"
+                 : "=l"(k4[2]), "=l"(v0), "=l"(k4[3]), "=l"(v1)
+                 : "l"(s + 2));
+}
+
 // Add v (u32 count, or the bits of a double) to entry `key` of partition p.
 __device__ __forceinline__ void table_update(const TableView &tv, uint32_t p,
                                              unsigned long long key, unsigned long long v) {
@@ -102,14 +115,12 @@ __device__ __forceinline__ void table_update(const TableView &tv, uint32_t p,
     }
     // Linear probing from the 4-slot bucket holding slot_mix(key): the four
     // keys of a bucket (64 bytes) are loaded together, so most updates take
-    // one round trip even at high load.  Partition capacities are powers of
-    // two >= 64.
+    // one round trip even at high load.
     unsigned long long h = slot_mix(key) & mask & ~3ull;
     for (unsigned long long probe = 0; probe <= mask; probe += 4) {
         Slot *s = tv.slots + off + h;
         unsigned long long k4[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) k4[q] = s[q].key;
+        load_bucket_keys(s, k4);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             unsigned long long k = k4[q];
