@@ -371,6 +371,9 @@ extern "C" crp_status crp_reset(crp_plan *pl) {
                                            pl->n_res, pl->stream));
             pl->launches += 1;
         }
+        if (pl->hot_R)
+            CRP_CUDA(launch_reserve_cells(pl->d_res_keys, (int32_t)pl->n_res, pl->d_rank_a,
+                                          pl->d_rank_b, pl->hot_R, pl->d_hot, pl->stream));
     }
     return CRP_OK;
 }
@@ -622,9 +625,25 @@ static crp_status summary_accumulate(crp_plan *pl, const crp_sparse *A, const cr
         AccumulateArgs a = make_args(pl, &As, &Bs, B->idx, B->val, 1);
         a.direct = 1;
         a.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
+        if (pl->hot_R) {
+            // the reserved pairs all fall in the dense block: no reserved-key
+            // test on the way to the summaries
+            a.hot_rank_a = pl->d_rank_a;
+            a.hot_rank_b = pl->d_rank_b;
+            a.hot_block = pl->d_hot;
+            a.hot_R = pl->hot_R;
+            a.hot_masked = 1;
+            a.tv.has_reserved = 0;
+        }
         CRP_CUDA(cudaMemsetAsync(&pl->dc->work_next, 0, sizeof(unsigned int), pl->stream));
         CRP_CUDA(cudaEventRecord(pl->ev0, pl->stream));
         CRP_CUDA(launch_accumulate(a, nullptr, pl->grid_direct, pl->stream));
+        if (pl->hot_R && k1 == K) {
+            CRP_CUDA(launch_hot_flush(pl->d_hot, pl->hot_R, pl->d_items_a, pl->d_items_b, pl->hp,
+                                      table_view(pl, pl->slots, pl->d_off, pl->d_mask),
+                                      &pl->dc->flushed, pl->stream, 1));
+            pl->launches += 1;
+        }
         CRP_CUDA(cudaEventRecord(pl->ev1, pl->stream));
         pl->launches += 1;
         crp_status st = summary_settle(pl, k1 == K);
@@ -1259,6 +1278,59 @@ extern "C" crp_status crp_timing(crp_plan *pl, double *accumulate_ms, uint64_t *
     return CRP_OK;
 }
 
+// The rows and columns that occur in reserved keys, when there are at most
+// 4096 of each, index a dense block (in L2) whose cells of reserved pairs
+// count those pairs during accumulation (the other cells are off: those
+// pairs take the summary path as before); the block is added into the
+// reserved counters at the end of each call.  A reserved pair then costs a
+// dense atomic instead of a hash probe, and the rest of the stream skips the
+// reserved-key test.
+static crp_status reserve_dense_block(crp_plan *pl) {
+    std::vector<unsigned long long> keys(pl->n_res);
+    CRP_CUDA(cudaMemcpyAsync(keys.data(), pl->d_res_keys, pl->n_res * 8, cudaMemcpyDeviceToHost,
+                             pl->stream));
+    CRP_CUDA(cudaStreamSynchronize(pl->stream));
+    std::vector<int64_t> ia, ib;
+    for (auto k : keys) {
+        ia.push_back((int64_t)(k >> 32));
+        ib.push_back((int64_t)(uint32_t)k);
+    }
+    for (auto *v : {&ia, &ib}) {
+        std::sort(v->begin(), v->end());
+        v->erase(std::unique(v->begin(), v->end()), v->end());
+    }
+    pl->hot_R = 0;
+    if (ia.empty() || ia.size() > 4096 || ib.size() > 4096) return CRP_OK;
+    const uint32_t na = (uint32_t)ia.size(), nb = (uint32_t)ib.size();
+    const uint32_t R = std::max(na, nb);
+    cudaFree(pl->d_hot);
+    cudaFree(pl->d_items_a);
+    cudaFree(pl->d_items_b);
+    pl->d_hot = nullptr;
+    pl->d_items_a = pl->d_items_b = nullptr;
+    CRP_CUDA(cudaMalloc(&pl->d_hot, (size_t)R * R * 4));
+    CRP_CUDA(cudaMalloc(&pl->d_items_a, (size_t)R * 8));
+    CRP_CUDA(cudaMalloc(&pl->d_items_b, (size_t)R * 8));
+    ia.resize(R, 0);   // ranks past a side's item count are never assigned, never counted
+    ib.resize(R, 0);
+    CRP_CUDA(cudaMemcpyAsync(pl->d_items_a, ia.data(), (size_t)R * 8, cudaMemcpyHostToDevice,
+                             pl->stream));
+    CRP_CUDA(cudaMemcpyAsync(pl->d_items_b, ib.data(), (size_t)R * 8, cudaMemcpyHostToDevice,
+                             pl->stream));
+    if (!pl->d_rank_a) {
+        CRP_CUDA(cudaMalloc(&pl->d_rank_a, (size_t)pl->d.n_rows * 2));
+        CRP_CUDA(cudaMalloc(&pl->d_rank_b, (size_t)pl->d.n_cols * 2));
+    }
+    CRP_CUDA(launch_hot_ranks(pl->d_rank_a, pl->d.n_rows, pl->d_items_a, na, pl->stream));
+    CRP_CUDA(launch_hot_ranks(pl->d_rank_b, pl->d.n_cols, pl->d_items_b, nb, pl->stream));
+    CRP_CUDA(launch_reserve_cells(pl->d_res_keys, (int32_t)pl->n_res, pl->d_rank_a, pl->d_rank_b, R,
+                                  pl->d_hot, pl->stream));
+    pl->launches += 5;
+    CRP_CUDA(cudaStreamSynchronize(pl->stream));
+    pl->hot_R = R;
+    return CRP_OK;
+}
+
 extern "C" crp_status crp_reserve(crp_plan *pl, const uint64_t *keys, int32_t n) {
     if (!pl || (n > 0 && !keys) || n < 0) return fail(CRP_EINVAL, "bad argument");
     if (!pl->summary || !pl->d.reserved_counters)
@@ -1276,5 +1348,5 @@ extern "C" crp_status crp_reserve(crp_plan *pl, const uint64_t *keys, int32_t n)
     pl->launches += 2;
     pl->n_res += n;
     CRP_CUDA(cudaStreamSynchronize(pl->stream));
-    return CRP_OK;
+    return reserve_dense_block(pl);
 }

@@ -354,8 +354,12 @@ __device__ __forceinline__ bool dense_tiers(const AccumulateArgs &A, uint32_t or
     if (orank < A.hot_R) {
         const uint32_t rb = __ldg(A.hot_rank_b + j);
         if (rb < A.hot_R) {
-            atomicAdd(&A.hot_block[orank * A.hot_R + rb], cnt);
-            return true;
+            unsigned int *c = &A.hot_block[orank * A.hot_R + rb];
+            // a masked block's cells that are off never change: a cached read is exact
+            if (!A.hot_masked || *c != kCellOff) {
+                atomicAdd(c, cnt);
+                return true;
+            }
         }
     }
     if (A.warm_W) {

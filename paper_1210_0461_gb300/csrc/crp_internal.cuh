@@ -16,6 +16,7 @@
 namespace crp {
 
 constexpr uint64_t kEmptyKey = ~0ull;   // i, j < 2^31 so no real key is all ones
+constexpr unsigned int kCellOff = 0xFFFFFFFFu;   // a dense-block cell that is not counted
 constexpr uint32_t kStatusTableFull = 1u;
 constexpr uint32_t kStatusSpillFull = 2u;
 constexpr uint32_t kStatusBadIndex = 4u;
@@ -138,6 +139,9 @@ struct AccumulateArgs {
     const uint16_t *hot_rank_b = nullptr;
     unsigned int *hot_block = nullptr;
     uint32_t hot_R = 0;
+    // 1: a cell holding kCellOff is not counted in the block (its pair takes
+    // the ordinary path); used for reserved pairs in summary mode
+    int hot_masked = 0;
     // warm stripes: dense counters for the pairs (warm row, any column) and
     // (any row, warm column) outside the hot block
     const uint16_t *warm_rank_a = nullptr;
@@ -186,7 +190,11 @@ cudaError_t launch_reserve_insert(Slot *slots, unsigned long long res_off,
 // Hot block (crp_accumulate.cu)
 cudaError_t launch_hot_flush(unsigned int *hot, uint32_t R, const int64_t *items_a,
                              const int64_t *items_b, HashPair hp, TableView tv,
-                             unsigned long long *flushed, cudaStream_t s);
+                             unsigned long long *flushed, cudaStream_t s, int masked = 0);
+// Dense-block cells of reserved pairs set to 0 (the rest stay kCellOff).
+cudaError_t launch_reserve_cells(const unsigned long long *keys, int32_t n, const uint16_t *rank_a,
+                                 const uint16_t *rank_b, uint32_t R, unsigned int *block,
+                                 cudaStream_t s);
 cudaError_t launch_hot_ranks(uint16_t *rank, int32_t n, const int64_t *items, uint32_t R,
                              cudaStream_t s);
 cudaError_t launch_warm_flush(unsigned int *stripe, uint32_t W, int32_t n_other,

@@ -132,6 +132,41 @@ def test_reserved_keys_are_counted_exactly(crp):
     plan.close()
 
 
+def test_reserved_dense_block_keeps_guarantees(crp):
+    # the rows and columns of the reserved keys index a dense block whose
+    # reserved cells count those pairs during the call (the other pairs of the
+    # block take the summary path) and go to the exact counters at its end:
+    # the reserved counts are exact and every summary entry keeps the
+    # Space-Saving bounds, over two streaming calls
+    T = ci.C1.scaled(m=12000).generate()
+    P, ell = 8, 128
+    ref, true, W = _truth(T, P)
+    ri, rj, rw = O.topk(ref.i, ref.j, ref.w, 200, upper_only=False)
+    keys = (ri.astype(np.uint64) << np.uint64(32)) | rj.astype(np.uint64)
+    plan = crp.Plan(1000, 1000, P, ci.SEED_A, ci.SEED_B, summary_counters=ell,
+                    reserved_counters=256)
+    plan.reserve(keys)
+    for lo, hi in ((0, 5000), (5000, 12000)):
+        part = ci.Sparse(T.ptr[lo:hi + 1] - T.ptr[lo], T.idx[T.ptr[lo]:T.ptr[hi]], None, 1000)
+        dd = crp.to_device(part)
+        plan.accumulate(dd, dd)
+    plan.sync()
+    reserved = set((int(a) * 1000 + int(b)) for a, b in zip(ri, rj))
+    i, j, up, lo_ = plan.export()   # the summaries (reserved counters are not in them)
+    kk = (i.astype(np.int64) * 1000 + j)
+    assert not any(int(k) in reserved for k in kk)
+    tv = np.array([true[int(k)] for k in kk])
+    assert (lo_ <= tv).all() and (tv <= up).all()
+    p = O.partition_of(i, j, P, ci.SEED_A, ci.SEED_B)
+    assert ((up - lo_) <= W[p] / ell + 1e-9).all()
+    # P * ell summary keys + 200 reserved keys < 8192: top-k returns all
+    ti, tj, tw, tl = plan.topk(8192)
+    got = {(int(a), int(b)): (u, l) for a, b, u, l in zip(ti, tj, tw, tl)}
+    for a, b, w in zip(ri, rj, rw):
+        assert got[(int(a), int(b))] == (w, w)
+    plan.close()
+
+
 def test_summary_streaming_chunks_keep_guarantees(crp):
     T = ci.C1.scaled(m=12000).generate()
     P, ell = 8, 256
