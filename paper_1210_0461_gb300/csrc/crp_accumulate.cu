@@ -399,18 +399,24 @@ cudaError_t launch_count_terms(const int64_t *a_ptr, const int64_t *b_ptr, int64
     return cudaGetLastError();
 }
 
+// Empty slots, two per 32-byte store (tables start 256-byte aligned).
 __global__ void k_fill_empty(Slot *slots, uint64_t n) {
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+    const uint64_t pairs = n >> 1;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < pairs;
          x += (uint64_t)gridDim.x * blockDim.x) {
-        slots[x].key = kEmptyKey;
-        slots[x].val = 0ull;
+        asm volatile("st.global.v4.u64 [%0], {%1, %2, %1, %2};"
+                     :: "l"(slots + 2 * x), "l"(kEmptyKey), "l"(0ull) : "memory");
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        slots[n - 1].key = kEmptyKey;
+        slots[n - 1].val = 0ull;
     }
 }
 
 cudaError_t launch_fill_empty(Slot *slots, uint64_t n, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    uint64_t blocks = (n + 255) / 256;
-    int grid = (int)(blocks < 65536 ? blocks : 65536);
+    uint64_t blocks = (n / 2 + 255) / 256;
+    int grid = (int)(blocks < 65536 ? (blocks > 0 ? blocks : 1) : 65536);
     k_fill_empty<<<grid, 256, 0, s>>>(slots, n);
     return cudaGetLastError();
 }

@@ -128,7 +128,9 @@ struct crp_plan {
     uint64_t pool_bytes = 0;
     uint32_t pool_chunks = 0, B = 0;
     unsigned int *d_chunk_bin = nullptr, *d_order = nullptr;
-    unsigned int *d_route_ctl = nullptr;   // chunk counter, count[B], fill[B], start[B + 1]
+    // chunk counter, count[B], fill[B], start[B + 1], overflow counter
+    unsigned int *d_route_ctl = nullptr;
+    uint32_t ov_chunks = 0;             // overflow chunks at the start of the pool
     // timing of the enumeration kernel and a count of our launches
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;
     bool timed = false, timed_mid = false;
@@ -680,13 +682,18 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
     const uint64_t rec = pl->d.value_type == CRP_I32 ? 8 : 16;
     // every term may become a record; each CTA also holds a partly filled
     // chunk and a spare per bin
-    const uint64_t chunks_needed = (terms + kChunkRecs - 1) / kChunkRecs + 2ull * Bn * grid + 1;
+    // overflow chunks for appends that find no chunk slot: 1/256 of the
+    // chunks, at least 256
+    const uint32_t ovc = (uint32_t)std::min<uint64_t>(
+        std::max<uint64_t>(terms / kChunkRecs / 256, 256), 1u << 20);
+    const uint64_t chunks_needed =
+        (terms + kChunkRecs - 1) / kChunkRecs + 2ull * Bn * grid + ovc + 1;
     const uint32_t chunks = (uint32_t)std::min<uint64_t>(chunks_needed, 0xFFFFFFF0ull);
     if (Bn != pl->B) {
         cudaFree(pl->d_route_ctl);
         pl->d_route_ctl = nullptr;
         pl->B = 0;
-        CRP_CUDA(cudaMalloc(&pl->d_route_ctl, (3 * (size_t)Bn + 2) * 4));
+        CRP_CUDA(cudaMalloc(&pl->d_route_ctl, (3 * (size_t)Bn + 3) * 4));
         pl->B = Bn;
     }
     if (chunks > pl->pool_chunks) {
@@ -703,7 +710,8 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
             if (cudaMalloc(&pl->pool, (size_t)c * kChunkRecs * rec) == cudaSuccess) break;
             cudaGetLastError();
             pl->pool = nullptr;
-            if (c <= chunks / 16 || c <= 2u * Bn * grid + 1) return fail(CRP_ENOMEM, "routed pool");
+            if (c <= chunks / 16 || c <= 2u * Bn * grid + ovc + 1)
+                return fail(CRP_ENOMEM, "routed pool");
             c /= 2;
         }
         CRP_CUDA(cudaMalloc(&pl->d_chunk_bin, (size_t)c * 4));
@@ -711,8 +719,15 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
         pl->pool_chunks = c;
         pl->pool_bytes = (uint64_t)c * kChunkRecs * rec;
     }
+    // chunks [0, ovc): overflow, bin 0, empty; the pool hands out chunks from ovc
+    pl->ov_chunks = ovc;
     CRP_CUDA(cudaMemsetAsync(pl->d_chunk_bin, 0xFF, (size_t)pl->pool_chunks * 4, pl->stream));
+    CRP_CUDA(cudaMemsetAsync(pl->d_chunk_bin, 0, (size_t)ovc * 4, pl->stream));
+    CRP_CUDA(cudaMemsetAsync(pl->pool, 0xFF, (size_t)ovc * kChunkRecs * rec, pl->stream));
     CRP_CUDA(cudaMemsetAsync(pl->d_route_ctl, 0, (2 * (size_t)Bn + 1) * 4, pl->stream));
+    CRP_CUDA(cudaMemsetAsync(pl->d_route_ctl + 3 * (size_t)Bn + 2, 0, 4, pl->stream));
+    CRP_CUDA(cudaMemcpyAsync(pl->d_route_ctl, &pl->ov_chunks, 4, cudaMemcpyHostToDevice,
+                             pl->stream));
     RouteArgs RA;
     RA.acc = make_args(pl, A, B, B->idx, B->val, 1);
     RA.acc.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
@@ -733,6 +748,8 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
     while ((1u << lgB) < Bn) ++lgB;
     RA.B_shift = pl->logP - lgB;
     RA.core_H = std::min<uint32_t>(RA.acc.hot_R, 128);
+    RA.ov_next = ctl + 3 * Bn + 2;
+    RA.ov_cap = ovc * kChunkRecs;
     CRP_CUDA(cudaMemsetAsync(&pl->dc->work_next, 0, sizeof(unsigned int), pl->stream));
     CRP_CUDA(cudaEventRecord(pl->ev0, pl->stream));
     CRP_CUDA(launch_route(RA, pl->sm_count, pl->stream));

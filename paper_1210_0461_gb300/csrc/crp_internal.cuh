@@ -169,6 +169,8 @@ struct RouteArgs {
     uint32_t n_chunks;
     uint32_t B, B_shift;
     uint32_t core_H;           // ranks < core_H of the hot block count in shared memory first
+    unsigned int *ov_next;     // records in the overflow chunks (chunks [0, ov_cap / kChunkRecs))
+    uint32_t ov_cap;
 };
 cudaError_t launch_route(const RouteArgs &RA, int grid, cudaStream_t s);
 cudaError_t launch_apply(const RouteArgs &RA, unsigned int *count, unsigned int *fill, int grid,

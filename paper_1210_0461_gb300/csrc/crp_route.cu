@@ -21,8 +21,10 @@
 //     time, adding each record into its partition table; a group's table
 //     region stays in L2 while it is updated.
 //
-// Appends that arrive while a chunk is being replaced, or when the pool is
-// exhausted, go straight to the tables (correct, only slower).
+// An append that arrives while its chunk is being replaced backs off and
+// retries; one that still finds no slot, or finds the pool exhausted, goes to
+// overflow chunks that the apply phase reads like the others: the routing
+// phase never touches the tables.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -94,34 +96,53 @@ __device__ __forceinline__ uint32_t reserve_chunk(const RouteArgs &RA) {
     return n < RA.n_chunks ? n : kNoChunk;
 }
 
+// A record that found no chunk slot (it arrived while its chunk was being
+// replaced, or the pool is exhausted) goes to the overflow chunks at the
+// start of the pool, which the apply phase reads like any other chunk; the
+// routing phase never touches the tables.  A full overflow region is
+// reported as lost counts (CRP_ETABLE_FULL).
+template <typename R>
+__device__ __forceinline__ void overflow_append(const RouteArgs &RA, const R &r) {
+    const unsigned int pos = atomicAdd(RA.ov_next, 1u);
+    if (pos < RA.ov_cap) store_rec((R *)RA.pool + pos, r);
+    else atomicOr(&RA.acc.tv.dc->status, kStatusSpillFull);
+}
+
 // Append record r to bin b through this CTA's current chunk of the bin.
 // cur[b] = (chunk << 32) | next position; nxt[b] = a chunk reserved ahead.
 template <typename R>
 __device__ __forceinline__ void bin_append(const RouteArgs &RA, unsigned long long *cur,
                                            unsigned int *nxt, uint32_t b, const R &r) {
     R *pool = (R *)RA.pool;
-    const unsigned long long old = atomicAdd(&cur[b], 1ull);
-    const uint32_t c = (uint32_t)(old >> 32), pos = (uint32_t)old;
-    if (pos < kChunkRecs) {
-        store_rec(pool + (size_t)c * kChunkRecs + pos, r);
-        if (pos == kChunkRecs / 2) {            // reserve the successor ahead of need
-            const uint32_t n = reserve_chunk(RA);
-            if (n != kNoChunk) atomicCAS(&nxt[b], kNoChunk, n);   // a spare stays unused
-        }
-        return;
-    }
-    if (pos == kChunkRecs) {                    // this lane installs the next chunk
-        uint32_t n = atomicExch(&nxt[b], kNoChunk);
-        if (n == kNoChunk) n = reserve_chunk(RA);
-        if (n != kNoChunk) {
-            RA.chunk_bin[n] = b;
-            store_rec(pool + (size_t)n * kChunkRecs, r);
-            atomicExch(&cur[b], ((unsigned long long)n << 32) | 1ull);
+    // an append that lands past the end while another lane installs the next
+    // chunk backs off and tries again (a bounded number of times: with few
+    // bins many lanes can queue behind one installation)
+    for (int attempt = 0; attempt < 4096; ++attempt) {
+        const unsigned long long old = atomicAdd(&cur[b], 1ull);
+        const uint32_t c = (uint32_t)(old >> 32), pos = (uint32_t)old;
+        if (pos < kChunkRecs) {
+            store_rec(pool + (size_t)c * kChunkRecs + pos, r);
+            if (pos == kChunkRecs / 2) {            // reserve the successor ahead of need
+                const uint32_t n = reserve_chunk(RA);
+                if (n != kNoChunk) atomicCAS(&nxt[b], kNoChunk, n);   // a spare stays unused
+            }
             return;
         }
-        atomicExch(&cur[b], ((unsigned long long)kNoChunk << 32) | kChunkRecs);
+        if (pos == kChunkRecs) {                    // this lane installs the next chunk
+            uint32_t n = atomicExch(&nxt[b], kNoChunk);
+            if (n == kNoChunk) n = reserve_chunk(RA);
+            if (n != kNoChunk) {
+                RA.chunk_bin[n] = b;
+                store_rec(pool + (size_t)n * kChunkRecs, r);
+                atomicExch(&cur[b], ((unsigned long long)n << 32) | 1ull);
+                return;
+            }
+            atomicExch(&cur[b], ((unsigned long long)kNoChunk << 32) | kChunkRecs);
+            break;                                  // the pool is exhausted
+        }
+        __nanosleep(32u << (attempt < 3 ? attempt : 3));
     }
-    apply_record(RA, r);
+    overflow_append(RA, r);
 }
 
 // Row-per-lane enumeration of the terms of a_k b_k.  A warp holds a batch of

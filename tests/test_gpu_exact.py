@@ -293,6 +293,42 @@ def test_partition_of_matches_oracle(crp):
     plan.close()
 
 
+@pytest.mark.parametrize("cfg", [dict(groups=16, flags=8 | 2, hot_items=64, warm_items=16),
+                                 dict(flags=4 | 2), dict(groups=4, flags=2)],
+                         ids=["routed", "direct", "smem"])
+def test_reset_between_calls(crp, cfg):
+    # a reset empties the tables before anything reads them again (the routed
+    # path runs it beside its routing kernel): reset -> empty top-k and
+    # stats; reset -> accumulate -> the product; two calls -> twice it
+    T = ci.C1.generate()
+    Tc = O.Compressed.of(T)
+    ref = O.exact_product(Tc, Tc, O.FULL)
+    d = crp.to_device(T)
+    plan = crp.Plan(1000, 1000, 64, ci.SEED_A, ci.SEED_B, **cfg)
+    plan.accumulate(d, d)
+    plan.sync()
+    _check_exact(crp, plan, ref, 64)
+    plan.reset()
+    assert len(plan.topk(10)[0]) == 0
+    assert plan.stats()["entries"] == 0
+    plan.accumulate(d, d)
+    plan.sync()
+    _check_exact(crp, plan, ref, 64)
+    plan.reset()
+    plan.accumulate(d, d)
+    plan.accumulate(d, d)
+    plan.sync()
+    i, j, w, _ = plan.export()
+    gi, gj, gw = _sorted(i, j, w)
+    assert np.array_equal(gi, ref.i) and np.array_equal(gj, ref.j)
+    assert np.array_equal(gw, 2 * ref.w)
+    plan.reset()
+    plan.accumulate(d, d)
+    plan.sync()
+    _check_exact(crp, plan, ref, 64)
+    plan.close()
+
+
 def test_repeat_runs_bit_identical(crp):
     T = ci.C1.scaled(m=8000).generate()
     d = crp.to_device(T)
