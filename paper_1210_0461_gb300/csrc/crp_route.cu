@@ -23,8 +23,8 @@
 //
 // An append that arrives while its chunk is being replaced backs off and
 // retries; one that still finds no slot, or finds the pool exhausted, goes to
-// overflow chunks that the apply phase reads like the others: the routing
-// phase never touches the tables.
+// overflow chunks that the apply phase reads like the others, and only when
+// those are full straight to the tables.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -96,16 +96,15 @@ __device__ __forceinline__ uint32_t reserve_chunk(const RouteArgs &RA) {
     return n < RA.n_chunks ? n : kNoChunk;
 }
 
-// A record that found no chunk slot (it arrived while its chunk was being
-// replaced, or the pool is exhausted) goes to the overflow chunks at the
-// start of the pool, which the apply phase reads like any other chunk; the
-// routing phase never touches the tables.  A full overflow region is
-// reported as lost counts (CRP_ETABLE_FULL).
+// A record that found no chunk slot (it kept arriving while its chunk was
+// being replaced, or the pool is exhausted) goes to the overflow chunks at
+// the start of the pool, which the apply phase reads like any other chunk;
+// once those are full, straight to its table (correct, only slower).
 template <typename R>
 __device__ __forceinline__ void overflow_append(const RouteArgs &RA, const R &r) {
     const unsigned int pos = atomicAdd(RA.ov_next, 1u);
     if (pos < RA.ov_cap) store_rec((R *)RA.pool + pos, r);
-    else atomicOr(&RA.acc.tv.dc->status, kStatusSpillFull);
+    else apply_record(RA, r);
 }
 
 // Append record r to bin b through this CTA's current chunk of the bin.
@@ -166,7 +165,7 @@ struct RowLane {
     int32_t sub, rpos;            // column offset within a step; row position in a_k
     bool va;
     // this lane's entry of the column batch (j = ~0u: none)
-    uint32_t jl, hbl, rbl, wbl;
+    uint32_t jl, hbl, rwl;        // rwl: hot rank | warm rank << 16 (0xFFFF: none)
     float bl;
 };
 
@@ -201,7 +200,7 @@ __device__ __forceinline__ void rl_load_cols(RowLane &st, const AccumulateArgs &
     st.m = 0;
     st.jl = ~0u;
     st.hbl = 0;
-    st.rbl = st.wbl = 0xFFFFu;
+    st.rwl = 0xFFFFFFFFu;
     st.bl = 1.0f;
     if (lane < st.mcount) {
         const int64_t y = st.b0 + st.bbase + lane;
@@ -209,8 +208,9 @@ __device__ __forceinline__ void rl_load_cols(RowLane &st, const AccumulateArgs &
         if (j < (uint32_t)A.n_cols) {
             st.jl = j;
             st.hbl = side_hash(A.hp.hb, j);
-            if (A.hot_rank_b) st.rbl = __ldg(A.hot_rank_b + j);
-            if (A.warm_rank_b) st.wbl = __ldg(A.warm_rank_b + j);
+            const uint32_t rb = A.hot_rank_b ? __ldg(A.hot_rank_b + j) : 0xFFFFu;
+            const uint32_t wb = A.warm_rank_b ? __ldg(A.warm_rank_b + j) : 0xFFFFu;
+            st.rwl = rb | (wb << 16);
             if (A.b_val) st.bl = __ldg(A.b_val + y);
         } else if (A.debug_checks) {
             atomicOr(&A.tv.dc->status, kStatusBadIndex);
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kRouteThreads, 1) k_route(RouteArgs RA) {
     __syncthreads();
     const uint32_t pmask = A.hp.ha.mask;
     const bool filter = A.part_lo != 0u || A.part_hi != 0xFFFFFFFFu;
-    unsigned long long my_terms = 0;
+    uint32_t my_terms = 0;   // terms of this lane (fewer than 2^32 per thread)
     RowLane st;
     st.k = st.a0 = st.b0 = 0;
     st.left = st.na = st.nb = st.abase = st.bbase = 0;
@@ -297,9 +297,10 @@ __global__ void __launch_bounds__(kRouteThreads, 1) k_route(RouteArgs RA) {
         const int src = c & 31;
         const uint32_t j = __shfl_sync(kFull, st.jl, src);
         const uint32_t hb = __shfl_sync(kFull, st.hbl, src);
-        const uint32_t rb = __shfl_sync(kFull, st.rbl, src);
-        const uint32_t wbk = __shfl_sync(kFull, st.wbl, src);
-        const float bv = __shfl_sync(kFull, st.bl, src);
+        const uint32_t rw = __shfl_sync(kFull, st.rwl, src);
+        const uint32_t rb = rw & 0xFFFFu, wbk = rw >> 16;
+        float bv = 1.0f;
+        if constexpr (VT != CRP_I32) bv = __shfl_sync(kFull, st.bl, src);
         const int32_t cpos = st.bbase + c;
         st.m += st.G;
         bool valid = st.va && c < st.mcount && j != ~0u;
@@ -349,9 +350,10 @@ __global__ void __launch_bounds__(kRouteThreads, 1) k_route(RouteArgs RA) {
         for (uint32_t x = pos + lane; x < kChunkRecs; x += 32)
             set_empty(pool + (size_t)c * kChunkRecs + x);
     }
+    unsigned long long warp_terms = my_terms;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) my_terms += __shfl_down_sync(kFull, my_terms, d);
-    if (lane == 0 && my_terms) atomicAdd(&A.tv.dc->terms, my_terms);
+    for (int d = 16; d > 0; d >>= 1) warp_terms += __shfl_down_sync(kFull, warp_terms, d);
+    if (lane == 0 && warp_terms) atomicAdd(&A.tv.dc->terms, warp_terms);
 }
 
 // Chunks per bin: count[b] over the installed chunks (chunk_bin != ~0u).
