@@ -291,7 +291,7 @@ def run_c4(args, np, torch, crp, ci, stream):
     by the product of marginals or by the trained network.  Top-1000 weight
     error against the GPU exact product (pinned bit-exact to the oracle by the
     tests)."""
-    w4 = ci.C4
+    w4 = ci.C4 if args.m is None else ci.C4.scaled(m=args.m)
     T = w4.generate()
     n = T.n_minor
     d = crp.to_device(T)
@@ -301,7 +301,7 @@ def run_c4(args, np, torch, crp, ci, stream):
     terms = int((L * (L - 1) // 2).sum())
     ex = crp.Plan(n, n, 1024, ci.SEED_A, ci.SEED_B, mode=crp.CRP_UPPER,
                   flags=crp.CRP_PLAN_ROUTED | crp.CRP_PLAN_SORTED_ROWS,
-                  groups=128, hot_items=4096, auto_grow=True, stream=stream)
+                  hot_items=2048, warm_items=32, auto_grow=True, stream=stream)
     ex.accumulate(d, d)
     ex.sync()
     exact_ms = ex.timing()[0]
@@ -375,8 +375,9 @@ def run_c4(args, np, torch, crp, ci, stream):
         plan.close()
     best = results["predictor"]
     _line(best["terms_per_s"], best["seconds"] * 1e3, args, "u32 counters",
-          {"workload": "c4: 50M transactions x 1M items, Poisson(15), Zipf(1.2); pairs i < j; "
-                       "2^20 counters per partition, P = 256, 2^16 reserved counters",
+          {"workload": f"c4: {w4.m} transactions x {w4.n} items, Poisson(15), Zipf(1.2); "
+                       "pairs i < j; 2^20 counters per partition, P = 256, 2^16 reserved "
+                       "counters",
            "terms_per_step": terms, "exact_reference_ms": exact_ms,
            "training": {"samples": int(len(y)), "steps": 300, "first_loss": losses[0],
                         "last_loss": losses[-1], "seconds": train_s},

@@ -58,14 +58,10 @@ __device__ __forceinline__ unsigned long long rec_val(const Rec16 &r) {
     return (unsigned long long)__double_as_longlong((double)r.p + (double)r.e);
 }
 
-// Records are written once and read once: evict-first hints keep them from
-// displacing the table region that the apply phase wants in L2.
-__device__ __forceinline__ void store_stream(unsigned long long *p, unsigned long long v) {
-    __stcs(p, v);
-}
-__device__ __forceinline__ void store_stream(Rec16 *p, const Rec16 &v) {
-    __stcs((ulonglong2 *)p, *(const ulonglong2 *)&v);
-}
+// Records are read once by the apply phase: an evict-first hint keeps them
+// from displacing the table region it wants in L2.  (They are written with
+// plain stores: a chunk fills over time, and its lines should stay in L2
+// until they are whole.)
 __device__ __forceinline__ unsigned long long load_stream(const unsigned long long *p) {
     return __ldcs(p);
 }
