@@ -7,8 +7,9 @@
 // tcgen05.mma kind::f16 with bf16 operands staged in shared memory and fp32
 // accumulators in TMEM (M = 128 rows per tile, N = 64); the output layer
 // (64 -> 1) is a dot product on the CUDA cores.  The backward pass uses three
-// more tensor-core products per tile (dH1 = dZ2 W2, dW2 = dZ2^T H1,
-// dW1 = dZ1^T X; the latter two with the batch as the reduction dimension).
+// more tensor-core products per tile (dH1 = dZ2 W2, [dW2 | gb2] = dZ2^T [H1 | 1],
+// [dW1 | gb1] = dZ1^T [X | 1]; the latter two with the batch as the reduction
+// dimension, accumulated in TMEM over all tiles of a CTA).
 //
 // Shared-memory operands use the canonical K-major layout without swizzle:
 // core matrices of 8 rows x 16 bytes (8 bf16); core (r/8, k/8) sits at
@@ -67,12 +68,14 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uin
 }
 
 // D[tmem_col..] (+)= A (M=128 x K) * B (N x K)^T, K = 16 * nk; one thread.
+// acc = 0 overwrites D, acc = 1 adds to it.
 __device__ __forceinline__ void gemm(uint32_t d_tmem, uint32_t a_saddr, uint32_t a_sbo,
-                                     uint32_t b_saddr, uint32_t b_sbo, int N, int nk) {
+                                     uint32_t b_saddr, uint32_t b_sbo, int N, int nk,
+                                     uint32_t acc = 0u) {
     const uint32_t id = idesc_bf16_f32(128, N);
     for (int kk = 0; kk < nk; ++kk)
         mma(d_tmem, sdesc(a_saddr + kk * 2 * kLBO, kLBO, a_sbo),
-            sdesc(b_saddr + kk * 2 * kLBO, kLBO, b_sbo), id, kk > 0 ? 1u : 0u);
+            sdesc(b_saddr + kk * 2 * kLBO, kLBO, b_sbo), id, (kk > 0 || acc) ? 1u : 0u);
 }
 
 __device__ __forceinline__ void commit(uint32_t mbar) {
@@ -139,10 +142,10 @@ struct Smem {
     alignas(1024) unsigned char A2[128 * 64 * 2];      // H1 tile     128 x 64
     alignas(1024) unsigned char AdH[128 * 64 * 2];     // dZ2 tile    128 x 64
     alignas(1024) unsigned char AdW2[128 * 128 * 2];   // dZ2^T       64(+64 zero) x 128
-    alignas(1024) unsigned char BdW2[64 * 128 * 2];    // H1^T        64 x 128
+    alignas(1024) unsigned char BdW2[80 * 128 * 2];    // [H1 | 1]^T  80 x 128 (row 64: ones)
     alignas(1024) unsigned char BdH[64 * 64 * 2];      // W2^T        64 x 64
     alignas(1024) unsigned char AdW1[128 * 128 * 2];   // dZ1^T       64(+64 zero) x 128
-    alignas(1024) unsigned char BdW1[16 * 128 * 2];    // X^T         16 x 128
+    alignas(1024) unsigned char BdW1[16 * 128 * 2];    // [X | 1]^T   16 x 128 (row 2: ones)
     float b1[64], b2[64], w3[64], b3;
     float gb1[64], gb2[64], gw3[64], gb3, loss;
     alignas(8) unsigned long long mbar;
@@ -181,6 +184,13 @@ __device__ void stage_weights(Smem &s, const float *prm, bool backward) {
             ((uint32_t *)s.AdW1)[x] = 0u;
         }
         for (int x = tid; x < (int)sizeof(s.BdW1) / 4; x += kThreads) ((uint32_t *)s.BdW1)[x] = 0u;
+        for (int x = tid; x < (int)sizeof(s.BdW2) / 4; x += kThreads) ((uint32_t *)s.BdW2)[x] = 0u;
+        __syncthreads();
+        // ones rows: the bias gradients come out of the weight-gradient products
+        for (int m = tid; m < kTM; m += kThreads) {
+            st_bf16(s.BdW2, kmaj_off(64, m, 2048), 1.0f);
+            st_bf16(s.BdW1, kmaj_off(2, m, 2048), 1.0f);
+        }
     }
 }
 
@@ -280,18 +290,51 @@ k_mlp_forward(const float *__restrict__ prm, const float *__restrict__ X, float 
 // Loss and gradient: grad += d/dtheta sum_m (y_m - t_m)^2 / n_total
 // ---------------------------------------------------------------------------
 
+// Sum over the warp of v[jl], where jl = bit1 + 2 bit2 + 4 bit3 + 8 bit4 of
+// the lane (a butterfly reduce-scatter of 16 values: 16 shuffles per lane;
+// lanes 2i and 2i + 1 end with the same slot).  v is overwritten.
+__device__ __forceinline__ float warp_reduce_scatter16(float *v, int lane) {
+#pragma unroll
+    for (int w = 8, bit = 16; w >= 1; w >>= 1, bit >>= 1) {
+        const bool upper = (lane & bit) != 0;
+#pragma unroll
+        for (int q = 0; q < w; ++q) {
+            const float send = upper ? v[q] : v[q + w];
+            const float keep = upper ? v[q + w] : v[q];
+            v[q] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+    return x;
+}
+
+// TMEM columns: Z1 0..63, Z2 64..127, dH1 128..191 (per tile); the weight
+// gradients accumulate over all tiles of the CTA: [dW2 | gb2] 256..335 and
+// [dW1 | gb1] 384..399 (the ones rows of [H1 | 1]^T and [X | 1]^T give the
+// bias gradients).  gw3 and gb3 are reduced across each warp with shuffles and
+// held in registers; one atomic per parameter per CTA at the end.
+constexpr uint32_t kColZ1 = 0, kColZ2 = 64, kColDH1 = 128, kColDW2 = 256, kColDW1 = 384;
+
 __global__ void __launch_bounds__(kThreads, 1)
 k_mlp_grad(const float *__restrict__ prm, const float *__restrict__ X,
            const float *__restrict__ Tg, int64_t n, float inv_total, float *grad, float *loss,
            unsigned int *err_out) {
     extern __shared__ __align__(1024) unsigned char raw[];
     Smem &s = *(Smem *)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     stage_weights(s, prm, true);
     setup_tmem_and_barrier(s, 512);
     const uint32_t tm = s.tmem;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
     uint32_t phase = 0;
+    float acc_w3[4] = {0.f, 0.f, 0.f, 0.f};   // gw3[c * 16 + slot(lane)] of this warp
+    float acc_b3 = 0.f, acc_loss = 0.f;        // lane 0 of each warp
+    bool first = true, ok = true;
     const int64_t tiles = (n + kTM - 1) / kTM;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         const int64_t m = t * kTM + tid;
@@ -299,18 +342,18 @@ k_mlp_grad(const float *__restrict__ prm, const float *__restrict__ X,
         const float x0 = valid ? X[2 * m] : 0.f, x1 = valid ? X[2 * m + 1] : 0.f;
 #pragma unroll
         for (int k = 0; k < 16; ++k) st_bf16(s.A1, kmaj_off(tid, k, 256), k == 0 ? x0 : (k == 1 ? x1 : 0.f));
-        st_bf16(s.BdW1, kmaj_off(0, tid, 2048), x0);   // X^T (rows 2..15 stay zero)
+        st_bf16(s.BdW1, kmaj_off(0, tid, 2048), x0);   // [X | 1]^T rows 0, 1
         st_bf16(s.BdW1, kmaj_off(1, tid, 2048), x1);
         cta_sync_tc();
         if (tid == 0) {
-            gemm(tm, smem_u32(s.A1), 256, smem_u32(s.B1), 256, 64, 1);
+            gemm(tm + kColZ1, smem_u32(s.A1), 256, smem_u32(s.B1), 256, 64, 1);
             commit(smem_u32(&s.mbar));
         }
-        if (__syncthreads_or(!wait_mma(s, phase))) break;
+        if (__syncthreads_or(!wait_mma(s, phase))) { ok = false; break; }
         uint64_t mask1 = 0;
         for (int c = 0; c < 4; ++c) {
             float v[16];
-            tmem_ld16(tm + lane_base + c * 16, v);
+            tmem_ld16(tm + lane_base + kColZ1 + c * 16, v);
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int j = c * 16 + q;
@@ -318,20 +361,20 @@ k_mlp_grad(const float *__restrict__ prm, const float *__restrict__ X,
                 const float h = valid ? fmaxf(z, 0.f) : 0.f;
                 if (z > 0.f) mask1 |= 1ull << j;
                 st_bf16(s.A2, kmaj_off(tid, j, 1024), h);
-                st_bf16(s.BdW2, kmaj_off(j, tid, 2048), h);   // H1^T
+                st_bf16(s.BdW2, kmaj_off(j, tid, 2048), h);   // [H1 | 1]^T rows 0..63
             }
         }
         cta_sync_tc();
         if (tid == 0) {
-            gemm(tm + 64, smem_u32(s.A2), 1024, smem_u32(s.B2), 1024, 64, 4);
+            gemm(tm + kColZ2, smem_u32(s.A2), 1024, smem_u32(s.B2), 1024, 64, 4);
             commit(smem_u32(&s.mbar));
         }
-        if (__syncthreads_or(!wait_mma(s, phase))) break;
+        if (__syncthreads_or(!wait_mma(s, phase))) { ok = false; break; }
         float y = s.b3;
         uint64_t mask2 = 0;
         for (int c = 0; c < 4; ++c) {
             float v[16];
-            tmem_ld16(tm + lane_base + 64 + c * 16, v);
+            tmem_ld16(tm + lane_base + kColZ2 + c * 16, v);
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int j = c * 16 + q;
@@ -342,81 +385,86 @@ k_mlp_grad(const float *__restrict__ prm, const float *__restrict__ X,
         }
         const float r = valid ? y - Tg[m] : 0.f;
         const float dy = 2.f * r * inv_total;
-        if (valid) {
-            atomicAdd(&s.loss, r * r * inv_total);
-            atomicAdd(&s.gb3, dy);
+        {
+            const float l = warp_sum(r * r * inv_total), g = warp_sum(dy);
+            if (lane == 0) { acc_loss += l; acc_b3 += g; }
         }
         for (int c = 0; c < 4; ++c) {
-            float v[16];
-            tmem_ld16(tm + lane_base + 64 + c * 16, v);
+            float v[16], gw[16];
+            tmem_ld16(tm + lane_base + kColZ2 + c * 16, v);
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int j = c * 16 + q;
-                const float h2 = fmaxf(v[q] + s.b2[j], 0.f);
+                gw[q] = fmaxf(v[q] + s.b2[j], 0.f) * dy;
                 const float dz = ((mask2 >> j) & 1ull) ? dy * s.w3[j] : 0.f;
-                if (dy != 0.f) {
-                    atomicAdd(&s.gw3[j], h2 * dy);
-                    atomicAdd(&s.gb2[j], dz);
-                }
                 st_bf16(s.AdH, kmaj_off(tid, j, 1024), dz);
                 st_bf16(s.AdW2, kmaj_off(j, tid, 2048), dz);   // dZ2^T
             }
+            acc_w3[c] += warp_reduce_scatter16(gw, lane);
         }
         cta_sync_tc();
         if (tid == 0) {
-            gemm(tm + 128, smem_u32(s.AdH), 1024, smem_u32(s.BdH), 1024, 64, 4);     // dH1
-            gemm(tm + 192, smem_u32(s.AdW2), 2048, smem_u32(s.BdW2), 2048, 64, 8);   // dW2
+            gemm(tm + kColDH1, smem_u32(s.AdH), 1024, smem_u32(s.BdH), 1024, 64, 4);     // dH1
+            gemm(tm + kColDW2, smem_u32(s.AdW2), 2048, smem_u32(s.BdW2), 2048, 80, 8,
+                 first ? 0u : 1u);                                                       // [dW2|gb2]
             commit(smem_u32(&s.mbar));
         }
-        if (__syncthreads_or(!wait_mma(s, phase))) break;
+        if (__syncthreads_or(!wait_mma(s, phase))) { ok = false; break; }
         for (int c = 0; c < 4; ++c) {
             float v[16];
-            tmem_ld16(tm + lane_base + 128 + c * 16, v);
+            tmem_ld16(tm + lane_base + kColDH1 + c * 16, v);
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int j = c * 16 + q;
                 const float dz1 = ((mask1 >> j) & 1ull) ? v[q] : 0.f;
-                if (dz1 != 0.f) atomicAdd(&s.gb1[j], dz1);
                 st_bf16(s.AdW1, kmaj_off(j, tid, 2048), dz1);   // dZ1^T
-            }
-        }
-        for (int c = 0; c < 4; ++c) {   // every warp must issue tcgen05.ld (.sync.aligned)
-            float v[16];
-            tmem_ld16(tm + lane_base + 192 + c * 16, v);
-            if (tid < 64) {
-#pragma unroll
-                for (int q = 0; q < 16; ++q) atomicAdd(&grad[kOffW2 + tid * 64 + c * 16 + q], v[q]);
             }
         }
         cta_sync_tc();
         if (tid == 0) {
-            gemm(tm + 256, smem_u32(s.AdW1), 2048, smem_u32(s.BdW1), 2048, 16, 8);   // dW1
+            gemm(tm + kColDW1, smem_u32(s.AdW1), 2048, smem_u32(s.BdW1), 2048, 16, 8,
+                 first ? 0u : 1u);                                                       // [dW1|gb1]
             commit(smem_u32(&s.mbar));
         }
-        if (__syncthreads_or(!wait_mma(s, phase))) break;
-        {
+        // the next tile's first writes (A1, BdW1, A2, BdW2, AdW1) must wait for
+        // this product: every tile ends with a completed MMA
+        if (__syncthreads_or(!wait_mma(s, phase))) { ok = false; break; }
+        first = false;
+    }
+    // read the accumulated weight gradients (every warp issues the loads)
+    if (ok && !first) {
+        for (int c = 0; c < 5; ++c) {
             float v[16];
-            tmem_ld16(tm + lane_base + 256, v);
+            tmem_ld16(tm + lane_base + kColDW2 + c * 16, v);
             if (tid < 64) {
-                atomicAdd(&grad[kOffW1 + tid * 2 + 0], v[0]);
-                atomicAdd(&grad[kOffW1 + tid * 2 + 1], v[1]);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int col = c * 16 + q;
+                    if (col < 64) atomicAdd(&grad[kOffW2 + tid * 64 + col], v[q]);
+                    else if (col == 64) atomicAdd(&grad[kOffB2 + tid], v[q]);
+                }
             }
         }
-        fence_before();
-        __syncthreads();
+        float v[16];
+        tmem_ld16(tm + lane_base + kColDW1, v);
+        if (tid < 64) {
+            atomicAdd(&grad[kOffW1 + tid * 2 + 0], v[0]);
+            atomicAdd(&grad[kOffW1 + tid * 2 + 1], v[1]);
+            atomicAdd(&grad[kOffB1 + tid], v[2]);
+        }
+        if ((lane & 1) == 0) {
+            const int slot = ((lane >> 1) & 1) + 2 * ((lane >> 2) & 1) + 4 * ((lane >> 3) & 1) +
+                             8 * ((lane >> 4) & 1);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) atomicAdd(&grad[kOffW3 + c * 16 + slot], acc_w3[c]);
+        }
+        if (lane == 0) {
+            atomicAdd(&grad[kOffB3], acc_b3);
+            atomicAdd(loss, acc_loss);
+        }
     }
     teardown_tmem(s, 512);
-    __syncthreads();
-    if (tid < 64) {
-        atomicAdd(&grad[kOffB1 + tid], s.gb1[tid]);
-        atomicAdd(&grad[kOffB2 + tid], s.gb2[tid]);
-        atomicAdd(&grad[kOffW3 + tid], s.gw3[tid]);
-    }
-    if (tid == 0) {
-        atomicAdd(&grad[kOffB3], s.gb3);
-        atomicAdd(loss, s.loss);
-        if (s.err) atomicOr(err_out, (unsigned)s.err);
-    }
+    if (tid == 0 && s.err) atomicOr(err_out, (unsigned)s.err);
 }
 
 // Adam (Kingma & Ba 2015) on the fp32 master parameters.
