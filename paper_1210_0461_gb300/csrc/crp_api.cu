@@ -660,13 +660,10 @@ static crp_status summary_accumulate(crp_plan *pl, const crp_sparse *A, const cr
 
 // Routed mode: enumerate every term once into per-group bins, then apply the
 // bins group by group so each group's table region stays in L2.
-static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp_sparse *B) {
+// Size the record pool and bins of the routed path for up to `terms`
+// records and fill RA's routing fields (RA.acc is the caller's).
+static crp_status routed_prepare(crp_plan *pl, uint64_t terms, RouteArgs &RA) {
     const uint32_t P = pl->d.P;
-    CRP_CUDA(launch_count_terms(A->ptr, B->ptr, A->n_major, pl->d_scratch64, pl->stream));
-    unsigned long long terms = 0;
-    CRP_CUDA(cudaMemcpyAsync(&terms, pl->d_scratch64, 8, cudaMemcpyDeviceToHost, pl->stream));
-    CRP_CUDA(cudaStreamSynchronize(pl->stream));
-    pl->launches += 1;
     // groups of partitions whose table region is about 96 MB or more (the
     // record chunks of every CTA stay open in L2 for each group, so more
     // groups cost the enumeration more than they save the apply phase), but
@@ -681,9 +678,8 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
     const int grid = 2 * pl->sm_count;
     const uint64_t rec = pl->d.value_type == CRP_I32 ? 8 : 16;
     // every term may become a record; each CTA also holds a partly filled
-    // chunk and a spare per bin
-    // overflow chunks for appends that find no chunk slot: 1/256 of the
-    // chunks, at least 256
+    // chunk and a spare per bin; overflow chunks for appends that find no
+    // chunk slot: 1/256 of the chunks, at least 256
     const uint32_t ovc = (uint32_t)std::min<uint64_t>(
         std::max<uint64_t>(terms / kChunkRecs / 256, 256), 1u << 20);
     const uint64_t chunks_needed =
@@ -728,14 +724,6 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
     CRP_CUDA(cudaMemsetAsync(pl->d_route_ctl + 3 * (size_t)Bn + 2, 0, 4, pl->stream));
     CRP_CUDA(cudaMemcpyAsync(pl->d_route_ctl, &pl->ov_chunks, 4, cudaMemcpyHostToDevice,
                              pl->stream));
-    RouteArgs RA;
-    RA.acc = make_args(pl, A, B, B->idx, B->val, 1);
-    RA.acc.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
-    if (pl->d.hot_items || pl->d.warm_items) {
-        crp_status hs = select_hot_items(pl, A, B);
-        if (hs != CRP_OK) return hs;
-        set_dense_args(pl, RA.acc);
-    }
     unsigned int *ctl = pl->d_route_ctl;
     RA.pool = pl->pool;
     RA.chunk_bin = pl->d_chunk_bin;
@@ -750,19 +738,57 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
     RA.core_H = std::min<uint32_t>(RA.acc.hot_R, 128);
     RA.ov_next = ctl + 3 * Bn + 2;
     RA.ov_cap = ovc * kChunkRecs;
+    return CRP_OK;
+}
+
+// The two routed phases on the plan's stream (evm between them).
+static crp_status routed_run(crp_plan *pl, const RouteArgs &RA) {
     CRP_CUDA(cudaMemsetAsync(&pl->dc->work_next, 0, sizeof(unsigned int), pl->stream));
-    CRP_CUDA(cudaEventRecord(pl->ev0, pl->stream));
     CRP_CUDA(launch_route(RA, pl->sm_count, pl->stream));
     CRP_CUDA(cudaEventRecord(pl->evm, pl->stream));
-    CRP_CUDA(launch_apply(RA, ctl + 1, ctl + 1 + Bn, grid, pl->stream));
-    {
-        crp_status fs = flush_dense(pl, RA.acc.tv);
-        if (fs != CRP_OK) return fs;
+    CRP_CUDA(launch_apply(RA, pl->d_route_ctl + 1, pl->d_route_ctl + 1 + RA.B,
+                          2 * pl->sm_count, pl->stream));
+    pl->launches += 5;
+    return CRP_OK;
+}
+
+static unsigned long long count_terms(crp_plan *pl, const crp_sparse *A, const crp_sparse *B,
+                                      crp_status &st) {
+    unsigned long long terms = 0;
+    st = CRP_OK;
+    if (launch_count_terms(A->ptr, B->ptr, A->n_major, pl->d_scratch64, pl->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&terms, pl->d_scratch64, 8, cudaMemcpyDeviceToHost, pl->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(pl->stream) != cudaSuccess)
+        st = fail(CRP_ECUDA, "counting terms failed");
+    pl->launches += 1;
+    return terms;
+}
+
+// Routed mode: enumerate every term once into per-group bins, then apply the
+// bins group by group so each group's table region stays in L2.
+static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp_sparse *B) {
+    crp_status st;
+    const unsigned long long terms = count_terms(pl, A, B, st);
+    if (st != CRP_OK) return st;
+    RouteArgs RA;
+    RA.acc = make_args(pl, A, B, B->idx, B->val, 1);
+    RA.acc.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
+    if (pl->d.hot_items || pl->d.warm_items) {
+        st = select_hot_items(pl, A, B);
+        if (st != CRP_OK) return st;
+        set_dense_args(pl, RA.acc);
     }
+    st = routed_prepare(pl, terms, RA);
+    if (st != CRP_OK) return st;
+    CRP_CUDA(cudaEventRecord(pl->ev0, pl->stream));
+    st = routed_run(pl, RA);
+    if (st != CRP_OK) return st;
+    st = flush_dense(pl, RA.acc.tv);
+    if (st != CRP_OK) return st;
     CRP_CUDA(cudaEventRecord(pl->ev1, pl->stream));
     pl->timed = true;
     pl->timed_mid = true;
-    pl->launches += 5;
     return CRP_OK;
 }
 
