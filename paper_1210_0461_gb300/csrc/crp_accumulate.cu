@@ -574,16 +574,15 @@ cudaError_t launch_warm_flush(unsigned int *stripe, uint32_t W, int32_t n_other,
     return cudaGetLastError();
 }
 
-// Add the hot block's counts to the partition tables and clear them (cells
-// that are off, in a masked block, are left as they are).
+// Add the hot block's counts to the partition tables and clear it.
 __global__ void k_hot_flush(unsigned int *hot, uint32_t R, const int64_t *items_a,
                             const int64_t *items_b, HashPair hp, TableView tv,
-                            unsigned long long *flushed, int masked) {
+                            unsigned long long *flushed) {
     unsigned long long n = 0;
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < (uint64_t)R * R;
          x += (uint64_t)gridDim.x * blockDim.x) {
         const unsigned int c = hot[x];
-        if (!c || (masked && c == kCellOff)) continue;
+        if (!c) continue;
         hot[x] = 0u;
         const uint32_t i = (uint32_t)items_a[x / R], j = (uint32_t)items_b[x % R];
         table_update(tv, partition_hash(hp, i, j), make_key(i, j), c);
@@ -595,20 +594,52 @@ __global__ void k_hot_flush(unsigned int *hot, uint32_t R, const int64_t *items_
     if ((threadIdx.x & 31) == 0 && n) atomicAdd(flushed, n);
 }
 
-__global__ void k_reserve_cells(const unsigned long long *keys, int32_t n, const uint16_t *rank_a,
-                                const uint16_t *rank_b, uint32_t R, unsigned int *block) {
-    for (int32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
-        const uint32_t ra = rank_a[(uint32_t)(keys[x] >> 32)], rb = rank_b[(uint32_t)keys[x]];
-        if (ra < R && rb < R) block[ra * R + rb] = 0u;
-    }
+__global__ void k_reserve_cells(const unsigned int *cells, int32_t n, unsigned int *block) {
+    for (int32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x)
+        block[cells[x]] = 0u;
 }
 
-cudaError_t launch_reserve_cells(const unsigned long long *keys, int32_t n, const uint16_t *rank_a,
-                                 const uint16_t *rank_b, uint32_t R, unsigned int *block,
-                                 cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(block, 0xFF, (size_t)R * R * sizeof(unsigned int), s);
+cudaError_t launch_reserve_cells(const unsigned int *cells, int32_t n, unsigned int *block,
+                                 uint64_t n_cells, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(block, 0xFF, n_cells * sizeof(unsigned int), s);
     if (e != cudaSuccess || n <= 0) return e;
-    k_reserve_cells<<<(n + 255) / 256, 256, 0, s>>>(keys, n, rank_a, rank_b, R, block);
+    k_reserve_cells<<<(n + 255) / 256, 256, 0, s>>>(cells, n, block);
+    return cudaGetLastError();
+}
+
+// Add the ragged reserved block's counts to the tables (the reserved
+// counters) and clear them; the row of cell x is found by binary search.
+__global__ void k_reserve_flush(unsigned int *block, uint64_t n_cells, const unsigned int *res_off,
+                                uint32_t rows, const int64_t *items_a, const int64_t *items_b,
+                                HashPair hp, TableView tv, unsigned long long *flushed) {
+    unsigned long long n = 0;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_cells;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned int c = block[x];
+        if (!c || c == kCellOff) continue;
+        block[x] = 0u;
+        uint32_t lo = 0, hi = rows;   // last row with res_off[row] <= x
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (res_off[mid] <= x) lo = mid; else hi = mid;
+        }
+        const uint32_t i = (uint32_t)items_a[lo], j = (uint32_t)items_b[x - res_off[lo]];
+        table_update(tv, partition_hash(hp, i, j), make_key(i, j), c);
+        ++n;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) n += __shfl_down_sync(0xffffffffu, n, d);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(flushed, n);
+}
+
+cudaError_t launch_reserve_flush(unsigned int *block, uint64_t n_cells, const unsigned int *res_off,
+                                 uint32_t rows, const int64_t *items_a, const int64_t *items_b,
+                                 HashPair hp, TableView tv, unsigned long long *flushed,
+                                 cudaStream_t s) {
+    if (n_cells == 0 || rows == 0) return cudaSuccess;
+    const uint64_t blocks = (n_cells + 255) / 256;
+    k_reserve_flush<<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(
+        block, n_cells, res_off, rows, items_a, items_b, hp, tv, flushed);
     return cudaGetLastError();
 }
 
@@ -626,11 +657,11 @@ __global__ void k_hot_scatter(uint16_t *rank, const int64_t *items, uint32_t R) 
 
 cudaError_t launch_hot_flush(unsigned int *hot, uint32_t R, const int64_t *items_a,
                              const int64_t *items_b, HashPair hp, TableView tv,
-                             unsigned long long *flushed, cudaStream_t s, int masked) {
+                             unsigned long long *flushed, cudaStream_t s) {
     const uint64_t n = (uint64_t)R * R;
     if (n == 0) return cudaSuccess;
     k_hot_flush<<<(int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192), 256, 0, s>>>(
-        hot, R, items_a, items_b, hp, tv, flushed, masked);
+        hot, R, items_a, items_b, hp, tv, flushed);
     return cudaGetLastError();
 }
 

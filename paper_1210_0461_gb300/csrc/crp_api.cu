@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "crp_internal.cuh"
@@ -120,6 +121,11 @@ struct crp_plan {
     uint16_t *d_rank_a = nullptr, *d_rank_b = nullptr;
     int64_t *d_items_a = nullptr, *d_items_b = nullptr;
     uint32_t warm_W = 0;
+    // summary mode: the ragged block of reserved pairs (rows, cells per row,
+    // first cell of each row, the reserved cells' indices)
+    uint32_t resv_rows = 0;
+    uint64_t resv_cells = 0;
+    unsigned int *d_resv_len = nullptr, *d_resv_off = nullptr, *d_resv_idx = nullptr;
     unsigned int *d_warm_a = nullptr, *d_warm_b = nullptr;
     uint16_t *d_wrank_a = nullptr, *d_wrank_b = nullptr;
     int64_t *d_witems_a = nullptr, *d_witems_b = nullptr;
@@ -335,6 +341,9 @@ extern "C" void crp_plan_destroy(crp_plan *pl) {
     cudaFree(pl->d_rank_b);
     cudaFree(pl->d_items_a);
     cudaFree(pl->d_items_b);
+    cudaFree(pl->d_resv_len);
+    cudaFree(pl->d_resv_off);
+    cudaFree(pl->d_resv_idx);
     cudaFree(pl->d_warm_a);
     cudaFree(pl->d_warm_b);
     cudaFree(pl->d_wrank_a);
@@ -373,9 +382,9 @@ extern "C" crp_status crp_reset(crp_plan *pl) {
                                            pl->n_res, pl->stream));
             pl->launches += 1;
         }
-        if (pl->hot_R)
-            CRP_CUDA(launch_reserve_cells(pl->d_res_keys, (int32_t)pl->n_res, pl->d_rank_a,
-                                          pl->d_rank_b, pl->hot_R, pl->d_hot, pl->stream));
+        if (pl->resv_rows)
+            CRP_CUDA(launch_reserve_cells(pl->d_resv_idx, (int32_t)pl->n_res, pl->d_hot,
+                                          pl->resv_cells, pl->stream));
     }
     return CRP_OK;
 }
@@ -627,23 +636,25 @@ static crp_status summary_accumulate(crp_plan *pl, const crp_sparse *A, const cr
         AccumulateArgs a = make_args(pl, &As, &Bs, B->idx, B->val, 1);
         a.direct = 1;
         a.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
-        if (pl->hot_R) {
-            // the reserved pairs all fall in the dense block: no reserved-key
+        if (pl->resv_rows) {
+            // the reserved pairs all fall in the ragged block: no reserved-key
             // test on the way to the summaries
             a.hot_rank_a = pl->d_rank_a;
             a.hot_rank_b = pl->d_rank_b;
             a.hot_block = pl->d_hot;
-            a.hot_R = pl->hot_R;
-            a.hot_masked = 1;
+            a.hot_R = pl->resv_rows;
+            a.resv_len = pl->d_resv_len;
+            a.resv_off = pl->d_resv_off;
             a.tv.has_reserved = 0;
         }
         CRP_CUDA(cudaMemsetAsync(&pl->dc->work_next, 0, sizeof(unsigned int), pl->stream));
         CRP_CUDA(cudaEventRecord(pl->ev0, pl->stream));
         CRP_CUDA(launch_accumulate(a, nullptr, pl->grid_direct, pl->stream));
-        if (pl->hot_R && k1 == K) {
-            CRP_CUDA(launch_hot_flush(pl->d_hot, pl->hot_R, pl->d_items_a, pl->d_items_b, pl->hp,
-                                      table_view(pl, pl->slots, pl->d_off, pl->d_mask),
-                                      &pl->dc->flushed, pl->stream, 1));
+        if (pl->resv_rows && k1 == K) {
+            CRP_CUDA(launch_reserve_flush(pl->d_hot, pl->resv_cells, pl->d_resv_off,
+                                          pl->resv_rows, pl->d_items_a, pl->d_items_b, pl->hp,
+                                          table_view(pl, pl->slots, pl->d_off, pl->d_mask),
+                                          &pl->dc->flushed, pl->stream));
             pl->launches += 1;
         }
         CRP_CUDA(cudaEventRecord(pl->ev1, pl->stream));
@@ -1321,56 +1332,94 @@ extern "C" crp_status crp_timing(crp_plan *pl, double *accumulate_ms, uint64_t *
     return CRP_OK;
 }
 
-// The rows and columns that occur in reserved keys, when there are at most
-// 4096 of each, index a dense block (in L2) whose cells of reserved pairs
-// count those pairs during accumulation (the other cells are off: those
-// pairs take the summary path as before); the block is added into the
-// reserved counters at the end of each call.  A reserved pair then costs a
-// dense atomic instead of a hash probe, and the rest of the stream skips the
-// reserved-key test.
+// A ragged block over the reserved pairs: rows are the items i of reserved
+// keys and columns the items j, each side ranked by how many reserved keys
+// hold it; row r spans the columns up to its last reserved one, so a pair
+// of a reserved row lies in the block when its column's rank is below the
+// row's length (one comparison per term).  Cells of reserved pairs count
+// them during accumulation; the other cells are off, and their pairs take
+// the summary path as before.  The block is added into the reserved counters
+// at the end of each call.  A reserved pair then costs a dense atomic instead
+// of a hash probe, and the rest of the stream skips the reserved-key test.
 static crp_status reserve_dense_block(crp_plan *pl) {
     std::vector<unsigned long long> keys(pl->n_res);
     CRP_CUDA(cudaMemcpyAsync(keys.data(), pl->d_res_keys, pl->n_res * 8, cudaMemcpyDeviceToHost,
                              pl->stream));
     CRP_CUDA(cudaStreamSynchronize(pl->stream));
-    std::vector<int64_t> ia, ib;
+    pl->resv_rows = 0;
+    pl->resv_cells = 0;
+    std::unordered_map<uint32_t, uint32_t> deg_a, deg_b;
     for (auto k : keys) {
-        ia.push_back((int64_t)(k >> 32));
-        ib.push_back((int64_t)(uint32_t)k);
+        ++deg_a[(uint32_t)(k >> 32)];
+        ++deg_b[(uint32_t)k];
     }
-    for (auto *v : {&ia, &ib}) {
-        std::sort(v->begin(), v->end());
-        v->erase(std::unique(v->begin(), v->end()), v->end());
+    if (deg_a.empty() || deg_a.size() >= 0xFFFF || deg_b.size() >= 0xFFFF) return CRP_OK;
+    auto ranked = [](const std::unordered_map<uint32_t, uint32_t> &deg) {
+        std::vector<std::pair<uint32_t, uint32_t>> v(deg.begin(), deg.end());
+        std::sort(v.begin(), v.end(), [](const auto &x, const auto &y) {
+            return x.second != y.second ? x.second > y.second : x.first < y.first;
+        });
+        return v;
+    };
+    const auto rows = ranked(deg_a), cols = ranked(deg_b);
+    std::unordered_map<uint32_t, uint32_t> ra, rb;
+    for (uint32_t r = 0; r < rows.size(); ++r) ra[rows[r].first] = r;
+    for (uint32_t c = 0; c < cols.size(); ++c) rb[cols[c].first] = c;
+    std::vector<unsigned int> len(rows.size(), 0), off(rows.size(), 0), idx(keys.size());
+    for (auto k : keys) {
+        unsigned int &l = len[ra[(uint32_t)(k >> 32)]];
+        l = std::max<unsigned int>(l, rb[(uint32_t)k] + 1);
     }
-    pl->hot_R = 0;
-    if (ia.empty() || ia.size() > 4096 || ib.size() > 4096) return CRP_OK;
-    const uint32_t na = (uint32_t)ia.size(), nb = (uint32_t)ib.size();
-    const uint32_t R = std::max(na, nb);
+    uint64_t total = 0;
+    for (size_t r = 0; r < rows.size(); ++r) {
+        off[r] = (unsigned int)total;
+        total += len[r];
+    }
+    if (total > (64ull << 20)) return CRP_OK;   // too sparse a block: keep the hash probe
+    for (size_t x = 0; x < keys.size(); ++x)
+        idx[x] = off[ra[(uint32_t)(keys[x] >> 32)]] + rb[(uint32_t)keys[x]];
+    std::vector<int64_t> ia(rows.size()), ib(cols.size());
+    for (size_t r = 0; r < rows.size(); ++r) ia[r] = rows[r].first;
+    for (size_t c = 0; c < cols.size(); ++c) ib[c] = cols[c].first;
     cudaFree(pl->d_hot);
     cudaFree(pl->d_items_a);
     cudaFree(pl->d_items_b);
+    cudaFree(pl->d_resv_len);
+    cudaFree(pl->d_resv_off);
+    cudaFree(pl->d_resv_idx);
     pl->d_hot = nullptr;
     pl->d_items_a = pl->d_items_b = nullptr;
-    CRP_CUDA(cudaMalloc(&pl->d_hot, (size_t)R * R * 4));
-    CRP_CUDA(cudaMalloc(&pl->d_items_a, (size_t)R * 8));
-    CRP_CUDA(cudaMalloc(&pl->d_items_b, (size_t)R * 8));
-    ia.resize(R, 0);   // ranks past a side's item count are never assigned, never counted
-    ib.resize(R, 0);
-    CRP_CUDA(cudaMemcpyAsync(pl->d_items_a, ia.data(), (size_t)R * 8, cudaMemcpyHostToDevice,
+    pl->d_resv_len = pl->d_resv_off = pl->d_resv_idx = nullptr;
+    CRP_CUDA(cudaMalloc(&pl->d_hot, std::max<uint64_t>(total, 1) * 4));
+    CRP_CUDA(cudaMalloc(&pl->d_items_a, ia.size() * 8));
+    CRP_CUDA(cudaMalloc(&pl->d_items_b, ib.size() * 8));
+    CRP_CUDA(cudaMalloc(&pl->d_resv_len, len.size() * 4));
+    CRP_CUDA(cudaMalloc(&pl->d_resv_off, off.size() * 4));
+    CRP_CUDA(cudaMalloc(&pl->d_resv_idx, idx.size() * 4));
+    CRP_CUDA(cudaMemcpyAsync(pl->d_items_a, ia.data(), ia.size() * 8, cudaMemcpyHostToDevice,
                              pl->stream));
-    CRP_CUDA(cudaMemcpyAsync(pl->d_items_b, ib.data(), (size_t)R * 8, cudaMemcpyHostToDevice,
+    CRP_CUDA(cudaMemcpyAsync(pl->d_items_b, ib.data(), ib.size() * 8, cudaMemcpyHostToDevice,
+                             pl->stream));
+    CRP_CUDA(cudaMemcpyAsync(pl->d_resv_len, len.data(), len.size() * 4, cudaMemcpyHostToDevice,
+                             pl->stream));
+    CRP_CUDA(cudaMemcpyAsync(pl->d_resv_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice,
+                             pl->stream));
+    CRP_CUDA(cudaMemcpyAsync(pl->d_resv_idx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice,
                              pl->stream));
     if (!pl->d_rank_a) {
         CRP_CUDA(cudaMalloc(&pl->d_rank_a, (size_t)pl->d.n_rows * 2));
         CRP_CUDA(cudaMalloc(&pl->d_rank_b, (size_t)pl->d.n_cols * 2));
     }
-    CRP_CUDA(launch_hot_ranks(pl->d_rank_a, pl->d.n_rows, pl->d_items_a, na, pl->stream));
-    CRP_CUDA(launch_hot_ranks(pl->d_rank_b, pl->d.n_cols, pl->d_items_b, nb, pl->stream));
-    CRP_CUDA(launch_reserve_cells(pl->d_res_keys, (int32_t)pl->n_res, pl->d_rank_a, pl->d_rank_b, R,
-                                  pl->d_hot, pl->stream));
+    CRP_CUDA(launch_hot_ranks(pl->d_rank_a, pl->d.n_rows, pl->d_items_a, (uint32_t)ia.size(),
+                              pl->stream));
+    CRP_CUDA(launch_hot_ranks(pl->d_rank_b, pl->d.n_cols, pl->d_items_b, (uint32_t)ib.size(),
+                              pl->stream));
+    CRP_CUDA(launch_reserve_cells(pl->d_resv_idx, (int32_t)idx.size(), pl->d_hot, total,
+                                  pl->stream));
     pl->launches += 5;
     CRP_CUDA(cudaStreamSynchronize(pl->stream));
-    pl->hot_R = R;
+    pl->resv_rows = (uint32_t)rows.size();
+    pl->resv_cells = total;
     return CRP_OK;
 }
 

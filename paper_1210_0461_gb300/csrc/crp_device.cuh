@@ -353,13 +353,19 @@ __device__ __forceinline__ bool dense_tiers(const AccumulateArgs &A, uint32_t or
                                             unsigned cnt) {
     if (orank < A.hot_R) {
         const uint32_t rb = __ldg(A.hot_rank_b + j);
-        if (rb < A.hot_R) {
-            unsigned int *c = &A.hot_block[orank * A.hot_R + rb];
-            // a masked block's cells that are off never change: a cached read is exact
-            if (!A.hot_masked || *c != kCellOff) {
-                atomicAdd(c, cnt);
-                return true;
+        if (A.resv_len) {
+            // ragged reserved block: cells that are off never change, so a
+            // cached read is exact
+            if (rb < __ldg(A.resv_len + orank)) {
+                unsigned int *c = &A.hot_block[__ldg(A.resv_off + orank) + rb];
+                if (*c != kCellOff) {
+                    atomicAdd(c, cnt);
+                    return true;
+                }
             }
+        } else if (rb < A.hot_R) {
+            atomicAdd(&A.hot_block[orank * A.hot_R + rb], cnt);
+            return true;
         }
     }
     if (A.warm_W) {

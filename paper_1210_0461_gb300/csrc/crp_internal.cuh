@@ -139,9 +139,11 @@ struct AccumulateArgs {
     const uint16_t *hot_rank_b = nullptr;
     unsigned int *hot_block = nullptr;
     uint32_t hot_R = 0;
-    // 1: a cell holding kCellOff is not counted in the block (its pair takes
-    // the ordinary path); used for reserved pairs in summary mode
-    int hot_masked = 0;
+    // ragged block of reserved pairs (summary mode; hot_block then holds its
+    // cells): row r = hot_rank_a has resv_len[r] cells from resv_off[r],
+    // indexed by hot_rank_b; a cell holding kCellOff is not reserved (its
+    // pair takes the summary path)
+    const unsigned int *resv_len = nullptr, *resv_off = nullptr;
     // warm stripes: dense counters for the pairs (warm row, any column) and
     // (any row, warm column) outside the hot block
     const uint16_t *warm_rank_a = nullptr;
@@ -192,10 +194,14 @@ cudaError_t launch_reserve_insert(Slot *slots, unsigned long long res_off,
 // Hot block (crp_accumulate.cu)
 cudaError_t launch_hot_flush(unsigned int *hot, uint32_t R, const int64_t *items_a,
                              const int64_t *items_b, HashPair hp, TableView tv,
-                             unsigned long long *flushed, cudaStream_t s, int masked = 0);
-// Dense-block cells of reserved pairs set to 0 (the rest stay kCellOff).
-cudaError_t launch_reserve_cells(const unsigned long long *keys, int32_t n, const uint16_t *rank_a,
-                                 const uint16_t *rank_b, uint32_t R, unsigned int *block,
+                             unsigned long long *flushed, cudaStream_t s);
+// The ragged reserved block: every cell kCellOff, then the reserved cells
+// (indices cells[0, n)) 0; and its flush into the tables (clearing counts).
+cudaError_t launch_reserve_cells(const unsigned int *cells, int32_t n, unsigned int *block,
+                                 uint64_t n_cells, cudaStream_t s);
+cudaError_t launch_reserve_flush(unsigned int *block, uint64_t n_cells, const unsigned int *res_off,
+                                 uint32_t rows, const int64_t *items_a, const int64_t *items_b,
+                                 HashPair hp, TableView tv, unsigned long long *flushed,
                                  cudaStream_t s);
 cudaError_t launch_hot_ranks(uint16_t *rank, int32_t n, const int64_t *items, uint32_t R,
                              cudaStream_t s);
