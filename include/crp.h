@@ -216,11 +216,16 @@ crp_status crp_topk(crp_plan *plan, int32_t k, uint32_t flags, int32_t *i_out, i
  * and reports the lower bound in w_lower; crp_export_partitions gives both.
  *
  * crp_reserve registers keys ((uint64_t)i << 32 | j; host or device array
- * of n) whose updates go to exact counters probed before the summaries
- * (desc.reserved_counters bounds their number).  Reserve before the
- * accumulate calls whose terms should be counted exactly: weight added to a
- * key before it was reserved stays in its partition's summary.  crp_reset
- * keeps the reserved keys and zeroes their counts.  Synchronises. */
+ * of n) whose updates go to exact counters instead of the summaries
+ * (desc.reserved_counters bounds their number).  During accumulation they
+ * are counted in a ragged block over their rows and columns (device memory
+ * about the number of reserved keys when they cluster on few rows and
+ * columns; more than 64 Mi cells, or 65,535 distinct rows or columns, fall
+ * back to a hash probe of the exact counters) and added to the exact
+ * counters at the end of each call.  Reserve before the accumulate calls
+ * whose terms should be counted exactly: weight added to a key before it was
+ * reserved stays in its partition's summary.  crp_reset keeps the reserved
+ * keys and zeroes their counts.  Synchronises. */
 crp_status crp_reserve(crp_plan *plan, const uint64_t *keys, int32_t n);
 
 /* Partition of entry (i,j): (h_a(i) + h_b(j)) mod P, computed on the host. */
