@@ -84,25 +84,29 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
     const unsigned long long total_items = (unsigned long long)A.n_tiles * n_groups_here;
     unsigned long long my_terms = 0, flushed = 0;
 
-    while (true) {
-        if (threadIdx.x == 0) ctrl[1] = atomicAdd(&A.tv.dc->work_next, 1u);
-        __syncthreads();
-        const unsigned long long item = ctrl[1];
-        __syncthreads();
-        if (item >= total_items) break;
-        const uint32_t g = A.group_begin + (uint32_t)(item / A.n_tiles);
-        const uint64_t tile = item % A.n_tiles;
-        const uint32_t q = g * w;
-
-        WarpEnum st;
-        st.k = (int64_t)tile * A.tile + warp - kWarps;
-        st.k_hi = min((int64_t)A.K, (int64_t)(tile + 1) * A.tile);
-        st.has_batch = false;
-        st.done = false;
-        st.total = 0;
-        st.pos = 0;
-
-        if (DIRECT) {
+    if (DIRECT) {
+        // each warp takes its own work items (1/kWarps of a tile of outer
+        // products, of one partition group): no CTA-wide barrier, so no warp
+        // waits for another
+        const int64_t wt = A.tile >= (uint32_t)kWarps ? A.tile / kWarps : 1;
+        const unsigned long long wtiles = (unsigned long long)((A.K + wt - 1) / wt);
+        const unsigned long long warp_items = wtiles * n_groups_here;
+        while (true) {
+            unsigned long long item = 0;
+            if (lane == 0) item = atomicAdd(&A.tv.dc->work64, 1ull);
+            item = __shfl_sync(kFull, item, 0);
+            if (item >= warp_items) break;
+            const uint32_t g = A.group_begin + (uint32_t)(item / wtiles);
+            const int64_t wtile = (int64_t)(item % wtiles);
+            const uint32_t q = g * w;
+            WarpEnum st;
+            st.k = wtile * wt - 1;
+            st.k_hi = min((int64_t)A.K, (wtile + 1) * wt);
+            st.kstride = 1;
+            st.has_batch = false;
+            st.done = false;
+            st.total = 0;
+            st.pos = 0;
             while (advance(st, A, b_hash, q, w, lane)) {
                 uint32_t oi, j;
                 float owa, wb;
@@ -136,8 +140,27 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
                     }
                 }
             }
-            continue;
         }
+    }
+
+    while (!DIRECT) {
+        if (threadIdx.x == 0) ctrl[1] = atomicAdd(&A.tv.dc->work_next, 1u);
+        __syncthreads();
+        const unsigned long long item = ctrl[1];
+        __syncthreads();
+        if (item >= total_items) break;
+        const uint32_t g = A.group_begin + (uint32_t)(item / A.n_tiles);
+        const uint64_t tile = item % A.n_tiles;
+        const uint32_t q = g * w;
+
+        WarpEnum st;
+        st.k = (int64_t)tile * A.tile + warp - kWarps;
+        st.k_hi = min((int64_t)A.K, (int64_t)(tile + 1) * A.tile);
+        st.kstride = kWarps;
+        st.has_batch = false;
+        st.done = false;
+        st.total = 0;
+        st.pos = 0;
 
         while (true) {
             for (int r = 0; r < kRoundChunks; ++r) {
@@ -219,6 +242,10 @@ static cudaError_t launch_one(const AccumulateArgs &args, const uint32_t *b_hash
 cudaError_t launch_accumulate(const AccumulateArgs &args, const uint32_t *b_hash, int grid,
                               cudaStream_t s) {
     const bool direct = args.direct != 0;
+    if (direct) {   // the direct kernel's warps take items from the 64-bit counter
+        cudaError_t e = cudaMemsetAsync(&args.tv.dc->work64, 0, sizeof(unsigned long long), s);
+        if (e != cudaSuccess) return e;
+    }
     if (args.tv.value_type == CRP_I32)
         return direct ? launch_one<CRP_I32, true>(args, b_hash, grid, s)
                       : launch_one<CRP_I32, false>(args, b_hash, grid, s);

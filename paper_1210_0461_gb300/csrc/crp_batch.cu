@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchArgs B) {
         const uint64_t tile = item - B.tile_prefix[q];
         WarpEnum st;
         st.k = (int64_t)tile * B.tile + warp - kWarps;
+        st.kstride = kWarps;
         st.k_hi = min((int64_t)pr.K, (int64_t)(tile + 1) * B.tile);
         st.has_batch = false;
         st.done = false;

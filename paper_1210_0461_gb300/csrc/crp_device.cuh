@@ -211,6 +211,7 @@ struct WarpEnum {
     float my_wa;
     int32_t lo1, n1, lo2, excl;
     int32_t total, pos;
+    int32_t kstride;           // outer products between this warp's (kWarps, or 1)
     bool has_batch, done;
 };
 
@@ -290,7 +291,7 @@ __device__ __forceinline__ bool advance(WarpEnum &st, const AccumulateArgs &A,
                 continue;
             }
         }
-        st.k += kWarps;
+        st.k += st.kstride;
         if (st.k >= st.k_hi) { st.done = true; return false; }
         int64_t a0 = __ldg(A.a_ptr + st.k), a1 = __ldg(A.a_ptr + st.k + 1);
         int64_t b0 = __ldg(A.b_ptr + st.k), b1 = __ldg(A.b_ptr + st.k + 1);
