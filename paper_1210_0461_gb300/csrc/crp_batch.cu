@@ -50,17 +50,16 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// Each warp takes its own work items (one tile of one problem): no CTA-wide
+// barrier, so no warp waits for another.
 __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchArgs B) {
-    __shared__ unsigned long long item_s;
-    __shared__ int skip_s;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const unsigned long long total = B.tile_prefix[B.nprob];
     unsigned long long my_terms = 0, flushed = 0;
     while (true) {
-        if (threadIdx.x == 0) item_s = atomicAdd(&B.tv.dc->work64, 1ull);
-        __syncthreads();
-        const unsigned long long item = item_s;
-        __syncthreads();
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(&B.tv.dc->work64, 1ull);
+        item = __shfl_sync(kFull, item, 0);
         if (item >= total) break;
         int32_t lo = 0, hi = B.nprob;
         while (hi - lo > 1) {
@@ -69,25 +68,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchArgs B) {
         }
         const int32_t q = lo;
         if (B.ready) {
-            if (threadIdx.x == 0) {
-                int skip = 0;
-                if (!*(volatile const unsigned int *)&B.ready[q]) {
-                    const unsigned long long t0 = global_ns();
-                    while (!*(volatile const unsigned int *)&B.ready[q]) {
-                        if (global_ns() - t0 > B.wait_ns) {
-                            atomicOr(&B.tv.dc->status, kStatusTimeout);
-                            skip = 1;
-                            break;
-                        }
-                        __nanosleep(1000);
+            int skip = 0;
+            if (lane == 0 && !*(volatile const unsigned int *)&B.ready[q]) {
+                const unsigned long long t0 = global_ns();
+                while (!*(volatile const unsigned int *)&B.ready[q]) {
+                    if (global_ns() - t0 > B.wait_ns) {
+                        atomicOr(&B.tv.dc->status, kStatusTimeout);
+                        skip = 1;
+                        break;
                     }
+                    __nanosleep(1000);
                 }
-                skip_s = skip;
             }
-            __syncthreads();
-            const int skip = skip_s;
-            __syncthreads();
-            if (skip) continue;
+            if (__shfl_sync(kFull, skip, 0)) continue;
         }
         const BatchProb pr = B.probs[q];
         AccumulateArgs A;
@@ -117,8 +110,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchArgs B) {
         A.tv.part_full = B.tv.part_full + (size_t)q * B.P;
         const uint64_t tile = item - B.tile_prefix[q];
         WarpEnum st;
-        st.k = (int64_t)tile * B.tile + warp - kWarps;
-        st.kstride = kWarps;
+        st.k = (int64_t)tile * B.tile - 1;
+        st.kstride = 1;
         st.k_hi = min((int64_t)pr.K, (int64_t)(tile + 1) * B.tile);
         st.has_batch = false;
         st.done = false;
