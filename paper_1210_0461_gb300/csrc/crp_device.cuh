@@ -82,13 +82,14 @@ __device__ __forceinline__ void summary_update(const TableView &tv, uint32_t p,
 
 // The keys of the 4-slot bucket at s (64 bytes, 64-byte aligned: partition
 // capacities are powers of two >= 64 and tables start 256-byte aligned), in
-// two 32-byte loads.
+// two 32-byte loads that do not allocate in L1 (a bucket is rarely read
+// twice by one SM, and L1 keeps the partition offsets and masks instead).
 __device__ __forceinline__ void load_bucket_keys(const Slot *s, unsigned long long *k4) {
     unsigned long long v0, v1;
-    asm volatile("ld.global.v4.u64 {%0, %1, %2, %3}, [%4];"
+    asm volatile("ld.global.L1::no_allocate.v4.u64 {%0, %1, %2, %3}, [%4];"
                  : "=l"(k4[0]), "=l"(v0), "=l"(k4[1]), "=l"(v1)
                  : "l"(s));
-    asm volatile("ld.global.v4.u64 {%0, %1, %2, %3}, [%4];"
+    asm volatile("ld.global.L1::no_allocate.v4.u64 {%0, %1, %2, %3}, [%4];"
                  : "=l"(k4[2]), "=l"(v0), "=l"(k4[3]), "=l"(v1)
                  : "l"(s + 2));
 }
