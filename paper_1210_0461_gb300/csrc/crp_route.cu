@@ -165,6 +165,14 @@ struct RowLane {
     float bl;
 };
 
+// An input index read that does not allocate in L1 (L1 keeps the rank
+// arrays of the dense tiers; the index arrays stream through once).
+__device__ __forceinline__ uint32_t ld_idx(const int32_t *p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
 __device__ __forceinline__ void rl_load_rows(RowLane &st, const AccumulateArgs &A, int lane) {
     const int32_t L = min(32, st.na - st.abase);
     st.G = 32 / L;
@@ -177,7 +185,7 @@ __device__ __forceinline__ void rl_load_rows(RowLane &st, const AccumulateArgs &
     st.rank = st.wrank = 0xFFFFu;
     st.wa = 1.0f;
     if (st.sub < st.G) {
-        const uint32_t i = (uint32_t)__ldg(A.a_idx + x);
+        const uint32_t i = ld_idx(A.a_idx + x);
         if (i < (uint32_t)A.n_rows) {
             st.va = true;
             st.i = i;
@@ -200,7 +208,7 @@ __device__ __forceinline__ void rl_load_cols(RowLane &st, const AccumulateArgs &
     st.bl = 1.0f;
     if (lane < st.mcount) {
         const int64_t y = st.b0 + st.bbase + lane;
-        const uint32_t j = (uint32_t)__ldg(A.b_idx + y);
+        const uint32_t j = ld_idx(A.b_idx + y);
         if (j < (uint32_t)A.n_cols) {
             st.jl = j;
             st.hbl = side_hash(A.hp.hb, j);
