@@ -8,7 +8,7 @@ then the 1,000 heaviest pairs (i < j).
 
 One step = reset the partition tables, enumerate + combine + flush every
 outer-product term (crp_outer_accumulate), crp_sync, and crp_topk(1000).
-Prints one JSON line (see the design doc for every field).
+Prints one JSON line: the metric, the roofline of the dominant kernel, the oracle baseline, the end-to-end figure and the clocks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """

@@ -22,11 +22,15 @@ Sections of the paper each function follows:
   scan, so that scan is checked against the definition).
 * Preliminaries, Space-Saving, with weighted positive updates
   -> :func:`space_saving`.
+* Preliminaries, Count-Sketch, and Figure 1 (``CS[h(e)] += e s(e)``); the
+  median of t instances
+  -> :func:`side_sign`, :func:`sign_of`, :func:`count_sketch_terms`,
+  :func:`count_sketch`, :func:`sketch_estimate`, :func:`sketch_median`.
 * Section 6 (case study): support of a pair = number of transactions holding
   it, i.e. the entries above the diagonal of ``T^T T``; heaviest entries
   -> :func:`topk`.
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent:
 
 * Hash family: the paper requires pairwise independence only.  ``(a, b)`` are
   the first two SplitMix64 outputs (Steele, Lea, Flood 2014) from the seed, and
@@ -36,6 +40,10 @@ Readings where the paper is silent (each also listed in the design doc):
   by the smallest key (i, j); a weighted insert of weight w into a full summary
   takes ``(key, min + w, min)``.
 * Top-k order: weight descending, then i ascending, then j ascending.
+* Sign hash of an entry: ``s(i, j) = s_a(i) s_b(j)`` with ``s_x(v) = +1`` or
+  ``-1`` from the top bit of a multiply-add hash whose ``(c, d)`` are the third
+  and fourth SplitMix64 outputs of the side's seed (pairwise independent over
+  pairs when the side hashes are); one estimator per partition.
 """
 from __future__ import annotations
 
@@ -107,6 +115,66 @@ def partition_of(i, j, P: int, seed_a: int, seed_b: int) -> np.ndarray:
     """``h(i,j) = (h_a(i) + h_b(j)) mod P`` (Lemma 1 proof)."""
     lg = log2_exact(P)
     return (side_hash(i, seed_a, lg) + side_hash(j, seed_b, lg)) % P
+
+
+# ---------------------------------------------------------------------------
+# Count-Sketch (Preliminaries, "Frequent items mining algorithms"; Figure 1)
+# ---------------------------------------------------------------------------
+
+def sign_params(seed: int) -> tuple[int, int]:
+    """Multiplier and addend of one side's sign hash: the third and fourth
+    SplitMix64 outputs of the side's seed (the first two belong to its
+    partition hash)."""
+    out = splitmix64(seed, 4)
+    return out[2], out[3]
+
+
+def side_sign(x, seed: int) -> np.ndarray:
+    """``s(x)``: +1 when the top bit of ``(c x + d) mod 2^64`` is 0, else -1
+    (multiply-add-shift to one bit)."""
+    x = np.asarray(x, dtype=np.int64).astype(np.uint64)
+    c, d = sign_params(seed)
+    with np.errstate(over="ignore"):
+        v = x * np.uint64(c) + np.uint64(d)
+    return 1 - 2 * (v >> np.uint64(63)).astype(np.int64)
+
+
+def sign_of(i, j, seed_a: int, seed_b: int) -> np.ndarray:
+    """``s(i, j) = s_a(i) s_b(j)``."""
+    return side_sign(i, seed_a) * side_sign(j, seed_b)
+
+
+def count_sketch_terms(A: "Compressed", B: "Compressed", P: int, seed_a: int, seed_b: int,
+                       mode: int = FULL) -> np.ndarray:
+    """Figure 1 as written: for every outer product, every term e adds
+    ``e s(e)`` to ``CS[h(e)]``.  One estimator per partition; fp64 (integer
+    weights stay exact)."""
+    cs = np.zeros(P)
+    _, i, j, w = outer_product_terms(A, B, 0, A.n_major, mode)
+    for a, b, v in zip(i.tolist(), j.tolist(), w.tolist()):
+        p = int(partition_of(np.array([a]), np.array([b]), P, seed_a, seed_b)[0])
+        cs[p] += v * int(sign_of(np.array([a]), np.array([b]), seed_a, seed_b)[0])
+    return cs
+
+
+def count_sketch(prod: "Product", P: int, seed_a: int, seed_b: int) -> np.ndarray:
+    """The same from the entries: the terms of one entry add up to its weight,
+    so ``CS[p]`` is the sum of ``w_e s(e)`` over the entries e in partition p."""
+    p = partition_of(prod.i, prod.j, P, seed_a, seed_b)
+    s = sign_of(prod.i, prod.j, seed_a, seed_b)
+    cs = np.zeros(P)
+    np.add.at(cs, p, prod.w * s)
+    return cs
+
+
+def sketch_estimate(cs: np.ndarray, i, j, P: int, seed_a: int, seed_b: int) -> np.ndarray:
+    """The Count-Sketch estimate of entries (i, j): ``CS[h(e)] s(e)``."""
+    return cs[partition_of(i, j, P, seed_a, seed_b)] * sign_of(i, j, seed_a, seed_b)
+
+
+def sketch_median(estimates) -> np.ndarray:
+    """The median of t instances' estimates (rows: instances)."""
+    return np.median(np.asarray(estimates, dtype=np.float64), axis=0)
 
 
 # ---------------------------------------------------------------------------
