@@ -25,7 +25,8 @@ Sections of the paper each function follows:
 * Preliminaries, Count-Sketch, and Figure 1 (``CS[h(e)] += e s(e)``); the
   median of t instances
   -> :func:`side_sign`, :func:`sign_of`, :func:`count_sketch_terms`,
-  :func:`count_sketch`, :func:`sketch_estimate`, :func:`sketch_median`.
+  :func:`count_sketch`, :func:`count_sketch_spectrum`, :func:`sketch_estimate`,
+  :func:`sketch_median`.
 * Section 6 (case study): support of a pair = number of transactions holding
   it, i.e. the entries above the diagonal of ``T^T T``; heaviest entries
   -> :func:`topk`.
@@ -170,6 +171,45 @@ def count_sketch(prod: "Product", P: int, seed_a: int, seed_b: int) -> np.ndarra
 def sketch_estimate(cs: np.ndarray, i, j, P: int, seed_a: int, seed_b: int) -> np.ndarray:
     """The Count-Sketch estimate of entries (i, j): ``CS[h(e)] s(e)``."""
     return cs[partition_of(i, j, P, seed_a, seed_b)] * sign_of(i, j, seed_a, seed_b)
+
+
+def count_sketch_spectrum(A: "Compressed", B: "Compressed", P: int, seed_a: int, seed_b: int,
+                          freqs) -> np.ndarray:
+    """``sum_p CS[p] exp(2 pi i f p / P)`` for each f of ``freqs``, from the
+    inputs alone (FULL mode).  Because ``h(i,j) = (h_a(i) + h_b(j)) mod P``
+    and ``s(i,j) = s_a(i) s_b(j)``, the transform of the sketch factors per
+    outer product k: ``sum_k (sum_{i in a_k} a_k(i) s_a(i) w^{h_a(i)})
+    (sum_{j in b_k} b_k(j) s_b(j) w^{h_b(j)})`` with ``w = exp(2 pi i f /
+    P)``.  Linear in nnz per frequency, so it checks a sketch of any size."""
+    lg = log2_exact(P)
+    out = np.zeros(len(freqs), dtype=np.complex128)
+    K = A.n_major
+    step = 1 << 20
+    for k0 in range(0, K, step):
+        k1 = min(K, k0 + step)
+        sides = []
+        for X, seed in ((A, seed_a), (B, seed_b)):
+            lo, hi = int(X.ptr[k0]), int(X.ptr[k1])
+            idx = X.idx[lo:hi]
+            val = np.ones(hi - lo) if X.val is None else X.val[lo:hi].astype(np.float64)
+            v = val * side_sign(idx, seed)
+            hx = side_hash(idx, seed, lg)
+            seg = (X.ptr[k0:k1] - lo).astype(np.int64)
+            sides.append((v, hx, seg, hi - lo))
+        for n, f in enumerate(freqs):
+            per = []
+            for v, hx, seg, m in sides:
+                z = v * np.exp(2j * np.pi * ((f * hx) % P) / P)
+                s = np.zeros(len(seg), dtype=np.complex128)
+                nz = seg < m
+                if m:
+                    s[nz] = np.add.reduceat(z, seg[nz])
+                    # reduceat of an empty vector returns the next element: zero those
+                    empty = np.diff(np.append(seg, m)) == 0
+                    s[empty] = 0
+                per.append(s)
+            out[n] += np.sum(per[0] * per[1])
+    return out
 
 
 def sketch_median(estimates) -> np.ndarray:

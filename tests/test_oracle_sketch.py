@@ -181,3 +181,36 @@ def test_median_of_instances_beats_one_instance():
     assert np.array_equal(med, np.sort(ests, axis=0)[5])
     one = np.abs(ests - prod.w[top]).mean()
     assert np.abs(med - prod.w[top]).mean() < one
+
+
+@pytest.mark.parametrize("P", [1, 8, 64])
+@pytest.mark.parametrize("values", [False, True])
+def test_sketch_spectrum_is_the_fft_of_the_sketch(P, values):
+    # The closed form computed from the inputs alone equals the discrete
+    # Fourier transform (numpy FFT) of the sketch built from the entries;
+    # empty vectors at the start, middle and end take part.
+    rng = np.random.default_rng(60 + P + values)
+    A = _rand_sparse(rng, 45, 30, 0.2, integer=not values)
+    B = _rand_sparse(rng, 45, 25, 0.2, integer=not values)
+    A = _with_empty(A, (0, 10, 11, 44))   # empty vectors: first, a middle run, last
+    B = _with_empty(B, (0, 10, 11, 44))
+    cs = O.count_sketch(O.exact_product(A, B), P, 13, 17)
+    freqs = list(range(P))
+    got = O.count_sketch_spectrum(A, B, P, 13, 17, freqs)
+    want = np.conj(np.fft.fft(cs)) if P > 1 else np.array([cs.sum()], dtype=complex)
+    # sum_p CS[p] exp(+2 pi i f p / P) is the conjugate of numpy's forward FFT
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-9)
+
+
+def _with_empty(X, ks):
+    ptr, idx = [0], []
+    val = [] if X.val is not None else None
+    for k in range(X.n_major):
+        s, e = int(X.ptr[k]), int(X.ptr[k + 1])
+        if k not in ks:
+            idx.extend(X.idx[s:e].tolist())
+            if val is not None:
+                val.extend(X.val[s:e].tolist())
+        ptr.append(len(idx))
+    return O.Compressed(np.array(ptr, np.int64), np.array(idx, np.int32),
+                        None if val is None else np.array(val, np.float32), X.n_minor)
