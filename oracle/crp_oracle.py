@@ -184,29 +184,31 @@ def count_sketch_spectrum(A: "Compressed", B: "Compressed", P: int, seed_a: int,
     lg = log2_exact(P)
     out = np.zeros(len(freqs), dtype=np.complex128)
     K = A.n_major
+    # per index x of each side: s(x) and h(x)
+    tabs = []
+    for X, seed in ((A, seed_a), (B, seed_b)):
+        x = np.arange(X.n_minor, dtype=np.int64)
+        tabs.append((side_sign(x, seed).astype(np.float64), side_hash(x, seed, lg)))
     step = 1 << 20
-    for k0 in range(0, K, step):
-        k1 = min(K, k0 + step)
-        sides = []
-        for X, seed in ((A, seed_a), (B, seed_b)):
-            lo, hi = int(X.ptr[k0]), int(X.ptr[k1])
-            idx = X.idx[lo:hi]
-            val = np.ones(hi - lo) if X.val is None else X.val[lo:hi].astype(np.float64)
-            v = val * side_sign(idx, seed)
-            hx = side_hash(idx, seed, lg)
-            seg = (X.ptr[k0:k1] - lo).astype(np.int64)
-            sides.append((v, hx, seg, hi - lo))
-        for n, f in enumerate(freqs):
+    for n, f in enumerate(freqs):
+        # s(x) w^{h(x)} for every index of each side
+        g = [sg * np.exp(2j * np.pi * ((f * hx) % P) / P) for sg, hx in tabs]
+        for k0 in range(0, K, step):
+            k1 = min(K, k0 + step)
             per = []
-            for v, hx, seg, m in sides:
-                z = v * np.exp(2j * np.pi * ((f * hx) % P) / P)
+            for X, gx in ((A, g[0]), (B, g[1])):
+                lo, hi = int(X.ptr[k0]), int(X.ptr[k1])
+                z = gx[X.idx[lo:hi]]
+                if X.val is not None:
+                    z = z * X.val[lo:hi].astype(np.float64)
+                seg = (X.ptr[k0:k1] - lo).astype(np.int64)
+                m = hi - lo
                 s = np.zeros(len(seg), dtype=np.complex128)
                 nz = seg < m
                 if m:
                     s[nz] = np.add.reduceat(z, seg[nz])
                     # reduceat of an empty vector returns the next element: zero those
-                    empty = np.diff(np.append(seg, m)) == 0
-                    s[empty] = 0
+                    s[np.diff(np.append(seg, m)) == 0] = 0
                 per.append(s)
             out[n] += np.sum(per[0] * per[1])
     return out
