@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--load", type=int, default=0, help="target table load %% (0 = library default)")
     ap.add_argument("--topk", type=int, default=1000)
     ap.add_argument("--no-match", action="store_true")
+    ap.add_argument("--sketch", action="store_true",
+                    help="also keep the per-partition Count-Sketch (direct mode)")
     ap.add_argument("--mode", choices=["direct", "smem", "routed"], default="direct",
                     help="accumulation variant (CRP_PLAN_DIRECT / on-chip table / CRP_PLAN_ROUTED)")
     ap.add_argument("--autotune", type=int, default=2_500_000,
@@ -353,11 +355,16 @@ def run_c4(args, np, torch, crp, ci, stream):
     losses = [trainer.step(X, Y) for _ in range(300)]
     train_s = time.time() - t0
     results = {}
-    for name, prm, reserve in (("plain", None, False), ("product_of_marginals", None, True),
-                               ("predictor", params, True)):
+    qi = torch.from_numpy(ri.astype(np.int32)).cuda()
+    qj = torch.from_numpy(rj.astype(np.int32)).cuda()
+    for name, prm, reserve, sketch in (("plain", None, False, False),
+                                       ("plain+sketch", None, False, True),
+                                       ("product_of_marginals", None, True, False),
+                                       ("predictor", params, True, False)):
+        flags = crp.CRP_PLAN_SORTED_ROWS | (crp.CRP_PLAN_SKETCH if sketch else 0)
         plan = crp.Plan(n, n, 256, ci.SEED_A, ci.SEED_B, mode=crp.CRP_UPPER,
                         summary_counters=1 << 20, reserved_counters=(1 << 16) if reserve else 0,
-                        flags=crp.CRP_PLAN_SORTED_ROWS, stream=stream)
+                        flags=flags, stream=stream)
         t0 = time.time()
         if reserve:
             crp.predict_reserve(plan, pre, n, prm, R, 1 << 16)
@@ -381,7 +388,26 @@ def run_c4(args, np, torch, crp, ci, stream):
         results[name] = {"terms_per_s": terms / wall, "seconds": wall,
                          "accumulate_kernel_ms": sum(kms) / len(kms), "top1000_weight_err": err,
                          "predict_reserve_s": predict_s, "passes": len(walls)}
-        plan.close()
+        if sketch:
+            # Count-Sketch estimates of the exact top-1000 pairs: this
+            # instance, and the median over 5 instances with independent seeds
+            # (the other 4 run one at a time, untimed)
+            ests = [crp.sketch_estimate([plan], qi, qj).cpu().numpy()]
+            plan.close()
+            for r in range(1, 5):
+                extra = crp.Plan(n, n, 256, ci.SEED_A + 2 * r, ci.SEED_B + 2 * r + 1,
+                                 mode=crp.CRP_UPPER, summary_counters=1 << 20, flags=flags,
+                                 stream=stream)
+                extra.accumulate(d, d)
+                extra.sync()
+                ests.append(crp.sketch_estimate([extra], qi, qj).cpu().numpy())
+                extra.close()
+            rel = [float(np.abs(e - rw).sum() / top_sum) for e in ests]
+            med = np.median(np.array(ests), axis=0)
+            results[name]["sketch_top1000_rel_err_one"] = rel[0]
+            results[name]["sketch_top1000_rel_err_median5"] = float(np.abs(med - rw).sum() / top_sum)
+        else:
+            plan.close()
     best = results["predictor"]
     _line(best["terms_per_s"], best["seconds"] * 1e3, args, "u32 counters",
           {"workload": f"c4: {w4.m} transactions x {w4.n} items, Poisson(15), Zipf(1.2); "
@@ -502,6 +528,8 @@ def main():
     # With N ranks, rank r owns partitions [r P / N, (r + 1) P / N) and reads the
     # whole input (Section 4: K instances on disjoint intervals, no exchange while
     # accumulating); the per-rank top-k lists are gathered and merged at the end.
+    if args.sketch:
+        flags |= crp.CRP_PLAN_SKETCH
     q, r = (0, 0)
     if world > 1:
         from paper_1210_0461_gb300.sharding import gather_topk, partition_interval
@@ -561,7 +589,7 @@ def main():
     alg_bytes = (terms_step * BYTES_PER_TERM_UPDATE + dT.nbytes() + entries * SLOT_BYTES)
     achieved = alg_bytes / (acc / 1e3) / 1e9
     tr = profiled_traffic(f"c2:{args.mode}:P{args.P}:G{args.groups}:S{args.smem_slots}"
-                          f":H{args.hot}:W{args.warm}")
+                          f":H{args.hot}:W{args.warm}" + (":sketch" if args.sketch else ""))
     traffic = tr * terms_step if tr is not None else None
 
     # ---- end to end through the C ABI from pinned host buffers ----
@@ -614,7 +642,7 @@ def main():
                        "P": args.P, "groups": args.groups, "tile_vectors": args.tile,
                        "smem_slots": args.smem_slots, "warp_match": not args.no_match,
                        "mode": args.mode, "hot_items": args.hot, "warm_items": args.warm,
-                       "target_load_pct": args.load,
+                       "target_load_pct": args.load, "count_sketch": bool(args.sketch),
                        "autotune": tuned,
                        "terms_per_step": terms_step, "entries": entries,
                        "nnz": int(T.nnz), "l2": "inputs (0.8 GB) and tables "

@@ -72,6 +72,12 @@ enum { CRP_PLAN_NO_WARP_MATCH = 1,  /* skip __match_any_sync pre-combining */
                                        indices are distinct and ascending: with
                                        CRP_UPPER and A, B the same arrays (T^T T)
                                        only the pairs i < j are enumerated */
+       CRP_PLAN_SKETCH = 32,        /* also keep a Count-Sketch with one
+                                       estimator per partition (Preliminaries
+                                       and Figure 1: CS[h(e)] += e s(e) for
+                                       every term e), updated in the same pass
+                                       as the tables.  Needs CRP_PLAN_DIRECT or
+                                       a summary plan; see crp_sketch_read. */
        CRP_PLAN_ROUTED = 8 };       /* two phases: enumerate every term once
                                        into per-partition-group bins, then
                                        apply the bins group by group so each
@@ -250,6 +256,31 @@ crp_status crp_stats(crp_plan *plan, crp_stats_t *stats, uint64_t *terms_out);
  * kernels the plan has launched so far.  Either pointer may be NULL.  Cheap:
  * it does not scan the tables. */
 crp_status crp_timing(crp_plan *plan, double *accumulate_ms, uint64_t *launches);
+
+/* Count-Sketch of a plan created with CRP_PLAN_SKETCH (Preliminaries,
+ * "Count-Sketch"; Figure 1 updates CS[h(e)] by e s(e) for every term e of
+ * every outer product, h the plan's partition hash).  The sign of entry
+ * (i,j) is s(i,j) = s_a(i) s_b(j), s_x(v) = +1 or -1 from the top bit of
+ * (c v + d) mod 2^64 with (c, d) the third and fourth SplitMix64 outputs of
+ * that side's seed (the first two give h_x).  The sketch adds up over the
+ * plan's accumulate calls; crp_reset zeroes it.
+ *
+ * crp_sketch_read copies the P estimators to out (host or device): int64
+ * for CRP_I32 plans (exact), double for CRP_F32_COMP plans (each term the
+ * exact fp32 product, summed in fp64 in no fixed order).  Synchronises.
+ * CRP_EINVAL when the plan keeps no sketch. */
+crp_status crp_sketch_read(crp_plan *plan, void *out);
+
+/* Estimates of entries (i[q], j[q]), q < n, from t plans (1 <= t <= 32) with
+ * sketches, the same P, n_rows, n_cols and value type and independent seeds:
+ * plan r's estimate is s_r(i,j) CS_r[h_r(i,j)], and out[q] is the median of
+ * the t estimates (the mean of the two middle ones when t is even), the
+ * paper's median over independent runs.  i, j (int32) and out (double, n
+ * entries) are device arrays; indices must lie in [0, n_rows) and [0, n_cols)
+ * (CRP_EINVAL otherwise; the check costs one small readback).  Runs on
+ * plans[0]'s stream after every plan's pending work; synchronises. */
+crp_status crp_sketch_estimate(crp_plan *const *plans, int32_t t, const int32_t *i,
+                               const int32_t *j, int64_t n, double *out);
 
 /* Measurement helper, not on the product path: device time (*ms_out) of
  * n_updates random updates into a freshly allocated region of region_bytes

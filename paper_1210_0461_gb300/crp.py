@@ -25,6 +25,7 @@ CRP_FULL, CRP_UPPER = 0, 1
 CRP_TOPK_UPPER = 1
 CRP_PLAN_NO_WARP_MATCH, CRP_PLAN_DEBUG_CHECKS, CRP_PLAN_DIRECT, CRP_PLAN_ROUTED = 1, 2, 4, 8
 CRP_PLAN_SORTED_ROWS = 16
+CRP_PLAN_SKETCH = 32
 
 
 class CrpError(RuntimeError):
@@ -114,6 +115,8 @@ _SIGS = {
                                     ctypes.POINTER(crp_sparse), ctypes.c_int64, ctypes.c_char_p,
                                     ctypes.POINTER(crp_plan_desc),
                                     ctypes.POINTER(ctypes.c_double), _P]),
+    "crp_sketch_read": (ctypes.c_int, [_P, _P]),
+    "crp_sketch_estimate": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int64, _P]),
     "crp_version": (ctypes.c_char_p, []),
     "crp_last_error": (ctypes.c_char_p, []),
 }
@@ -325,6 +328,13 @@ class Plan:
         _check(self._lib.crp_timing(self._h, ctypes.byref(ms), ctypes.byref(n)), "crp_timing")
         return ms.value, n.value
 
+    def sketch(self) -> np.ndarray:
+        """The Count-Sketch's P estimators (CRP_PLAN_SKETCH): int64 for
+        CRP_I32 plans, float64 for CRP_F32_COMP plans."""
+        out = np.zeros(self.P, np.int64 if self.value_type == CRP_I32 else np.float64)
+        _check(self._lib.crp_sketch_read(self._h, out.ctypes.data), "crp_sketch_read")
+        return out
+
     def stats(self, per_partition: bool = False):
         s = crp_stats_t()
         terms = np.zeros(self.P, np.uint64) if per_partition else None
@@ -334,6 +344,19 @@ class Plan:
         if per_partition:
             d["partition_terms"] = terms
         return d
+
+
+def sketch_estimate(plans, i, j):
+    """Median over the plans' Count-Sketches of the estimates of entries
+    (i[q], j[q]); i, j: int32 CUDA tensors.  Returns a float64 CUDA tensor."""
+    import torch
+    i = i.to(torch.int32).contiguous()
+    j = j.to(torch.int32).contiguous()
+    out = torch.empty(i.numel(), dtype=torch.float64, device=i.device)
+    arr = (_P * len(plans))(*[p._h for p in plans])
+    _check(lib().crp_sketch_estimate(arr, len(plans), i.data_ptr(), j.data_ptr(), i.numel(),
+                                     out.data_ptr()), "crp_sketch_estimate")
+    return out
 
 
 def probe_update_rate(region_bytes: int, n_updates: int, mode: int) -> float:

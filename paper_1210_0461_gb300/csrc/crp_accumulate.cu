@@ -84,6 +84,17 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
     const unsigned long long total_items = (unsigned long long)A.n_tiles * n_groups_here;
     unsigned long long my_terms = 0, flushed = 0;
 
+    // Count-Sketch (direct kernel only): this CTA's estimators in shared
+    // memory after the 64-byte control block, or the plan's in HBM
+    const bool sketch = DIRECT && A.sketch != nullptr;
+    void *cs = A.sketch;
+    if (sketch && A.sketch_smem) {
+        cs = (void *)(smem_raw + 64);
+        for (uint32_t p = threadIdx.x; p <= A.hp.ha.mask; p += kThreads)
+            ((unsigned long long *)cs)[p] = 0ull;
+        __syncthreads();
+    }
+
     if (DIRECT) {
         // each warp takes its own work items (1/kWarps of a tile of outer
         // products, of one partition group): no CTA-wide barrier, so no warp
@@ -126,6 +137,12 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
                             lead = lane == __ffs(peers) - 1;
                             cnt = __popc(peers);
                         }
+                        if (lead && sketch) {   // CS[h(e)] += cnt s(e)
+                            const long long c = sign_negative(A.sg, oi, j) ? -(long long)cnt
+                                                                            : (long long)cnt;
+                            atomicAdd((unsigned long long *)cs + partition_hash(A.hp, oi, j),
+                                      (unsigned long long)c);
+                        }
                         if (lead && !dense_tiers(A, orank, owrank, oi, j, cnt)) {
                             table_update(A.tv, partition_hash(A.hp, oi, j), key, cnt);
                             ++flushed;
@@ -134,7 +151,10 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
                         const float p = __fmul_rn(owa, wb);
                         const float e = __fmaf_rn(owa, wb, -p);
                         const double d = (double)p + (double)e;
-                        table_update(A.tv, partition_hash(A.hp, oi, j), key,
+                        const uint32_t part = partition_hash(A.hp, oi, j);
+                        if (sketch)
+                            atomicAdd((double *)cs + part, sign_negative(A.sg, oi, j) ? -d : d);
+                        table_update(A.tv, part, key,
                                      (unsigned long long)__double_as_longlong(d));
                         ++flushed;
                     }
@@ -215,6 +235,15 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
         __syncthreads();
         flush_table<VT>(keys, vals, S, A, flushed);
     }
+    if (sketch && A.sketch_smem) {   // add this CTA's estimators to the plan's
+        __syncthreads();
+        for (uint32_t p = threadIdx.x; p <= A.hp.ha.mask; p += kThreads) {
+            const unsigned long long v = ((unsigned long long *)cs)[p];
+            if (v == 0ull) continue;
+            if (VT == CRP_I32) atomicAdd((unsigned long long *)A.sketch + p, v);
+            else atomicAdd((double *)A.sketch + p, __longlong_as_double((long long)v));
+        }
+    }
 
     // aggregate counters: warp reduce then one atomic per warp
 #pragma unroll
@@ -231,7 +260,9 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
 template <int VT, bool DIRECT>
 static cudaError_t launch_one(const AccumulateArgs &args, const uint32_t *b_hash, int grid,
                               cudaStream_t s) {
-    const size_t smem = DIRECT ? 64 : accumulate_smem_bytes(VT, args.smem_slots);
+    const size_t smem =
+        DIRECT ? 64 + (args.sketch_smem ? 8 * ((size_t)args.hp.ha.mask + 1) : 0)
+               : accumulate_smem_bytes(VT, args.smem_slots);
     cudaError_t e = cudaFuncSetAttribute(k_accumulate<VT, DIRECT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -70,6 +70,22 @@ static SideHash make_side_hash(uint64_t seed, uint32_t logP) {
     return h;
 }
 
+// Count-Sketch signs: the third and fourth SplitMix64 outputs of each seed
+static SignPair make_sign_pair(uint64_t seed_a, uint64_t seed_b) {
+    SignPair s;
+    uint64_t st = seed_a;
+    splitmix64_next(st);
+    splitmix64_next(st);
+    s.ca = splitmix64_next(st);
+    s.da = splitmix64_next(st);
+    st = seed_b;
+    splitmix64_next(st);
+    splitmix64_next(st);
+    s.cb = splitmix64_next(st);
+    s.db = splitmix64_next(st);
+    return s;
+}
+
 // ---------------------------------------------------------------------------
 // Plan
 // ---------------------------------------------------------------------------
@@ -137,6 +153,9 @@ struct crp_plan {
     // chunk counter, count[B], fill[B], start[B + 1], overflow counter
     unsigned int *d_route_ctl = nullptr;
     uint32_t ov_chunks = 0;             // overflow chunks at the start of the pool
+    // Count-Sketch: P estimators (int64 or fp64) and the sign hash
+    void *d_sketch = nullptr;
+    SignPair sg = {0, 0, 0, 0};
     // timing of the enumeration kernel and a count of our launches
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;
     bool timed = false, timed_mid = false;
@@ -257,6 +276,10 @@ extern "C" crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc,
                                 "CRP_I32, exact mode, <= 4096");
     if (d.summary_counters && d.value_type != CRP_I32)
         return fail(CRP_EUNSUPPORTED, "summaries count {0,1} inputs (CRP_I32) only");
+    if ((d.flags & CRP_PLAN_SKETCH) &&
+        (d.flags & CRP_PLAN_ROUTED || !(d.flags & CRP_PLAN_DIRECT || d.summary_counters)))
+        return fail(CRP_EINVAL, "CRP_PLAN_SKETCH needs CRP_PLAN_DIRECT or a summary plan "
+                                "(not CRP_PLAN_ROUTED)");
     if (d.summary_counters > (1u << 24))
         return fail(CRP_EINVAL, "summary_counters must be <= 2^24 per partition");
     if (d.reserved_counters > (1u << 24))
@@ -290,6 +313,13 @@ extern "C" crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc,
     ALLOC(pl->dc, sizeof(DevCounters));
     ALLOC(pl->d_scratch64, (2ull * d.P + 16) * sizeof(unsigned long long));
     ALLOC(pl->d_topk_hist, (kTopkBuckets + 512) * sizeof(unsigned int));
+    if (d.flags & CRP_PLAN_SKETCH) {
+        ALLOC(pl->d_sketch, (size_t)d.P * 8);
+        if (st == CRP_OK && cudaMemsetAsync(pl->d_sketch, 0, (size_t)d.P * 8, pl->stream) !=
+                                cudaSuccess)
+            st = fail(CRP_ECUDA, "memset failed");
+        pl->sg = make_sign_pair(d.seed_a, d.seed_b);
+    }
 #undef ALLOC
     if (st == CRP_OK && cudaMemsetAsync(pl->dc, 0, sizeof(DevCounters), pl->stream) != cudaSuccess)
         st = fail(CRP_ECUDA, "memset failed");
@@ -360,6 +390,7 @@ extern "C" void crp_plan_destroy(crp_plan *pl) {
     cudaFree(pl->d_chunk_bin);
     cudaFree(pl->d_order);
     cudaFree(pl->d_route_ctl);
+    cudaFree(pl->d_sketch);
     if (pl->ev0) cudaEventDestroy(pl->ev0);
     if (pl->ev1) cudaEventDestroy(pl->ev1);
     if (pl->evm) cudaEventDestroy(pl->evm);
@@ -369,6 +400,7 @@ extern "C" void crp_plan_destroy(crp_plan *pl) {
 extern "C" crp_status crp_reset(crp_plan *pl) {
     if (!pl) return fail(CRP_EINVAL, "null plan");
     CRP_CUDA(cudaMemsetAsync(pl->dc, 0, sizeof(DevCounters), pl->stream));
+    if (pl->d_sketch) CRP_CUDA(cudaMemsetAsync(pl->d_sketch, 0, (size_t)pl->d.P * 8, pl->stream));
     if (pl->tables_ready) {
         CRP_CUDA(launch_fill_empty(pl->slots, pl->n_slots, pl->stream));
         pl->launches += 1;
@@ -493,6 +525,11 @@ static AccumulateArgs make_args(crp_plan *pl, const crp_sparse *A, const crp_spa
     }
     a.smem_slots = pl->S;
     a.hp = pl->hp;
+    if (pl->d_sketch) {
+        a.sketch = pl->d_sketch;
+        a.sg = pl->sg;
+        a.sketch_smem = pl->d.P <= kSketchSmemMaxP ? 1 : 0;
+    }
     return a;
 }
 
@@ -542,6 +579,8 @@ static crp_status estimate_and_allocate(crp_plan *pl, const crp_sparse *A, const
             sb_val = B->val ? pl->s_val : nullptr;
         }
         AccumulateArgs a = make_args(pl, A, B, sb_idx, sb_val, Gs);
+        a.sketch = nullptr;   // a sizing pass: the sketch counts the real pass only
+        a.sketch_smem = 0;
         a.group_begin = 0;   // the sample is group 0 of the whole hash space,
         a.group_end = 1;     // whatever interval the plan owns
         a.part_lo = 0;
@@ -1441,4 +1480,55 @@ extern "C" crp_status crp_reserve(crp_plan *pl, const uint64_t *keys, int32_t n)
     pl->n_res += n;
     CRP_CUDA(cudaStreamSynchronize(pl->stream));
     return reserve_dense_block(pl);
+}
+
+// ---------------------------------------------------------------------------
+// Count-Sketch (Preliminaries; Figure 1)
+// ---------------------------------------------------------------------------
+
+extern "C" crp_status crp_sketch_read(crp_plan *pl, void *out) {
+    if (!pl || !out) return fail(CRP_EINVAL, "null argument");
+    if (!pl->d_sketch) return fail(CRP_EINVAL, "the plan keeps no sketch (CRP_PLAN_SKETCH)");
+    CRP_CUDA(cudaSetDevice(pl->device));
+    CRP_CUDA(cudaMemcpyAsync(out, pl->d_sketch, (size_t)pl->d.P * 8, cudaMemcpyDefault,
+                             pl->stream));
+    CRP_CUDA(cudaStreamSynchronize(pl->stream));
+    return CRP_OK;
+}
+
+extern "C" crp_status crp_sketch_estimate(crp_plan *const *plans, int32_t t, const int32_t *i,
+                                          const int32_t *j, int64_t n, double *out) {
+    if (!plans || t < 1 || t > kSketchMaxT || n < 0 || (n > 0 && (!i || !j || !out)))
+        return fail(CRP_EINVAL, "bad argument (1 <= t <= 32, n >= 0, device arrays)");
+    SketchSet S;
+    memset(&S, 0, sizeof(S));
+    S.t = t;
+    const crp_plan *p0 = plans[0];
+    if (!p0) return fail(CRP_EINVAL, "null plan");
+    S.value_type = p0->d.value_type;
+    for (int32_t r = 0; r < t; ++r) {
+        const crp_plan *pl = plans[r];
+        if (!pl || !pl->d_sketch)
+            return fail(CRP_EINVAL, "every plan must keep a sketch (CRP_PLAN_SKETCH)");
+        if (pl->d.P != p0->d.P || pl->d.n_rows != p0->d.n_rows || pl->d.n_cols != p0->d.n_cols ||
+            pl->d.value_type != p0->d.value_type || pl->device != p0->device)
+            return fail(CRP_EINVAL, "the plans differ in P, shape, value type or device");
+        S.hp[r] = pl->hp;
+        S.sg[r] = pl->sg;
+        S.cs[r] = pl->d_sketch;
+    }
+    if (n == 0) return CRP_OK;
+    CRP_CUDA(cudaSetDevice(p0->device));
+    for (int32_t r = 1; r < t; ++r)
+        if (plans[r]->stream != p0->stream) CRP_CUDA(cudaStreamSynchronize(plans[r]->stream));
+    unsigned int *bad = (unsigned int *)(p0->d_scratch64 + 2 * p0->d.P + 8);
+    CRP_CUDA(cudaMemsetAsync(bad, 0, 4, p0->stream));
+    CRP_CUDA(launch_sketch_estimate(S, i, j, n, p0->d.n_rows, p0->d.n_cols, out, bad,
+                                    p0->stream));
+    plans[0]->launches += 1;
+    unsigned int h_bad = 0;
+    CRP_CUDA(cudaMemcpyAsync(&h_bad, bad, 4, cudaMemcpyDeviceToHost, p0->stream));
+    CRP_CUDA(cudaStreamSynchronize(p0->stream));
+    if (h_bad) return fail(CRP_EINVAL, "an index lies outside [0, n_rows) x [0, n_cols)");
+    return CRP_OK;
 }

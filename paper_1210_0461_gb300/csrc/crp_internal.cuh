@@ -46,6 +46,20 @@ __host__ __device__ __forceinline__ uint32_t partition_hash(const HashPair &hp, 
     return (side_hash(hp.ha, i) + side_hash(hp.hb, j)) & hp.ha.mask;
 }
 
+// Count-Sketch sign of entry (i,j) (Preliminaries, "Count-Sketch"):
+// s(i,j) = s_a(i) s_b(j), each side's sign taken from the top bit of a
+// multiply-add hash ((c x + d) mod 2^64) whose (c, d) are the third and
+// fourth SplitMix64 outputs of that side's seed.  The product of the two
+// signs is negative exactly when the two top bits differ.
+struct SignPair {
+    uint64_t ca, da, cb, db;
+};
+
+__host__ __device__ __forceinline__ bool sign_negative(const SignPair &s, uint32_t i,
+                                                       uint32_t j) {
+    return ((s.ca * (uint64_t)i + s.da) ^ (s.cb * (uint64_t)j + s.db)) >> 63;
+}
+
 // Slot position hash inside one partition table (independent of the
 // partition hash): the 64-bit finaliser of MurmurHash3 (Appleby).
 __host__ __device__ __forceinline__ uint64_t slot_mix(uint64_t k) {
@@ -156,7 +170,28 @@ struct AccumulateArgs {
     // pairs i < j of T^T T with a_k == b_k (same sorted list): the window of
     // the a entry at position x starts at position x + 1 of b_k
     int sym_upper = 0;
+    // Count-Sketch (direct kernel): P estimators, int64 (int mode) or fp64
+    // (real mode); sketch_smem: each CTA sums into shared memory first and
+    // adds its P estimators at the end
+    void *sketch = nullptr;
+    SignPair sg = {0, 0, 0, 0};
+    int sketch_smem = 0;
 };
+
+// Count-Sketch estimates from t <= kSketchMaxT plans (crp_sketch.cu)
+constexpr int kSketchMaxT = 32;
+struct SketchSet {
+    HashPair hp[kSketchMaxT];
+    SignPair sg[kSketchMaxT];
+    const void *cs[kSketchMaxT];
+    int32_t t;
+    int32_t value_type;
+};
+cudaError_t launch_sketch_estimate(const SketchSet &S, const int32_t *i, const int32_t *j,
+                                   int64_t n, int32_t n_rows, int32_t n_cols, double *out,
+                                   unsigned int *bad, cudaStream_t s);
+// largest P whose per-CTA sketch the direct kernel keeps in shared memory
+constexpr uint32_t kSketchSmemMaxP = 4096;
 
 // Two-phase (routed) accumulation: bins of records per partition group.
 constexpr uint32_t kChunkRecs = 256;   // records per chunk of the routed pool
