@@ -76,8 +76,34 @@ enum { CRP_PLAN_NO_WARP_MATCH = 1,  /* skip __match_any_sync pre-combining */
                                        estimator per partition (Preliminaries
                                        and Figure 1: CS[h(e)] += e s(e) for
                                        every term e), updated in the same pass
-                                       as the tables.  Needs CRP_PLAN_DIRECT or
-                                       a summary plan; see crp_sketch_read. */
+                                       as the tables (per term in direct
+                                       plans, per combined entry when the
+                                       on-chip table flushes; the sketch is
+                                       linear, so both give the same sums).
+                                       Not with CRP_PLAN_ROUTED; see
+                                       crp_sketch_read. */
+       CRP_PLAN_LOCKED_SUMMARY = 64,/* summary plans: each partition is ONE
+                                       Space-Saving summary of exactly
+                                       summary_counters (<= 64) counters, a
+                                       bucket updated under its own lock in
+                                       the order updates arrive -- the
+                                       sequential algorithm of the
+                                       Preliminaries on one arrival order of
+                                       the partition's terms; one enumeration
+                                       launch per call, no compaction.  The
+                                       paper's regime of many small buckets
+                                       (Section 6: 10^6 buckets, 2 counters).
+                                       By default each CTA first combines
+                                       equal keys in its on-chip table and
+                                       flushes weighted updates (heavy pairs
+                                       then take few locks); with
+                                       CRP_PLAN_DIRECT every warp-combined
+                                       term takes its bucket's lock, and
+                                       hot_items / warm_items may be set (the
+                                       dense tiers count pairs of frequent
+                                       items exactly and add them as weighted
+                                       updates at the end of the call).
+                                       reserved_counters may not be set. */
        CRP_PLAN_ROUTED = 8 };       /* two phases: enumerate every term once
                                        into per-partition-group bins, then
                                        apply the bins group by group so each

@@ -26,6 +26,7 @@ CRP_TOPK_UPPER = 1
 CRP_PLAN_NO_WARP_MATCH, CRP_PLAN_DEBUG_CHECKS, CRP_PLAN_DIRECT, CRP_PLAN_ROUTED = 1, 2, 4, 8
 CRP_PLAN_SORTED_ROWS = 16
 CRP_PLAN_SKETCH = 32
+CRP_PLAN_LOCKED_SUMMARY = 64
 
 
 class CrpError(RuntimeError):

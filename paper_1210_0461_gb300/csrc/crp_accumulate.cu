@@ -30,33 +30,51 @@ size_t accumulate_smem_bytes(int value_type, uint32_t S) {
 // The accumulation kernel
 // ---------------------------------------------------------------------------
 
-template <int VT>
+// S is a multiple of kThreads, so every lane runs the same number of
+// iterations and the warp's updates go out together.
+template <int VT, bool LOCKED>
 __device__ void flush_table(unsigned long long *keys, void *vals, uint32_t S,
                             const AccumulateArgs &A, unsigned long long &flushed) {
     for (uint32_t s = threadIdx.x; s < S; s += kThreads) {
-        unsigned long long key = keys[s];
-        if (key == kEmptyKey) continue;
-        unsigned long long v;
-        if (VT == CRP_I32) {
-            v = ((unsigned int *)vals)[s];
-            ((unsigned int *)vals)[s] = 0u;
-        } else {
-            unsigned long long pk = ((unsigned long long *)vals)[s];
-            double d = (double)__uint_as_float((unsigned int)(pk >> 32)) +
-                       (double)__uint_as_float((unsigned int)pk);
-            v = (unsigned long long)__double_as_longlong(d);
-            ((unsigned long long *)vals)[s] = 0ull;
+        const unsigned long long key = keys[s];
+        const bool has = key != kEmptyKey;
+        unsigned long long v = 0;
+        uint32_t p = 0;
+        if (has) {
+            if (VT == CRP_I32) {
+                v = ((unsigned int *)vals)[s];
+                ((unsigned int *)vals)[s] = 0u;
+            } else {
+                unsigned long long pk = ((unsigned long long *)vals)[s];
+                double d = (double)__uint_as_float((unsigned int)(pk >> 32)) +
+                           (double)__uint_as_float((unsigned int)pk);
+                v = (unsigned long long)__double_as_longlong(d);
+                ((unsigned long long *)vals)[s] = 0ull;
+            }
+            keys[s] = kEmptyKey;
+            const uint32_t i = (uint32_t)(key >> 32), j = (uint32_t)key;
+            p = partition_hash(A.hp, i, j);
+            if (A.sketch) {   // Count-Sketch of the combined entry: CS[h(e)] += v s(e)
+                const bool neg = sign_negative(A.sg, i, j);
+                if (VT == CRP_I32)
+                    atomicAdd((unsigned long long *)A.sketch + p,
+                              (unsigned long long)(neg ? -(long long)v : (long long)v));
+                else {
+                    const double d = __longlong_as_double((long long)v);
+                    atomicAdd((double *)A.sketch + p, neg ? -d : d);
+                }
+            }
+            ++flushed;
         }
-        keys[s] = kEmptyKey;
-        uint32_t i = (uint32_t)(key >> 32), j = (uint32_t)key;
-        table_update(A.tv, partition_hash(A.hp, i, j), key, v);
-        ++flushed;
+        if (LOCKED) locked_update_warp(A.tv, has, p, key, v);
+        else if (has) table_update(A.tv, p, key, v);
     }
 }
 
 // VT: value type.  DIRECT: no on-chip table; every (warp-combined) term goes
-// straight to its partition table in HBM.
-template <int VT, bool DIRECT>
+// straight to its partition table in HBM.  LOCKED: the tables are locked
+// Space-Saving buckets (int mode), updated by whole warps.
+template <int VT, bool DIRECT, bool LOCKED>
 __global__ void __launch_bounds__(kThreads, 2)
 k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -84,15 +102,17 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
     const unsigned long long total_items = (unsigned long long)A.n_tiles * n_groups_here;
     unsigned long long my_terms = 0, flushed = 0;
 
-    // Count-Sketch (direct kernel only): this CTA's estimators in shared
-    // memory after the 64-byte control block, or the plan's in HBM
+    // Count-Sketch, per term in the direct kernel: sketch_smem copies of the
+    // estimators in shared memory after the 64-byte control block (warp w
+    // adds into copy w mod sketch_smem, so few warps share an address), or
+    // the plan's in HBM (the on-chip-table kernel adds each combined entry
+    // at its flush)
     const bool sketch = DIRECT && A.sketch != nullptr;
-    void *cs = A.sketch;
+    unsigned long long *cs_s = (unsigned long long *)(smem_raw + 64);
     if (sketch && A.sketch_smem) {
-        cs = (void *)(smem_raw + 64);
-        for (uint32_t p = threadIdx.x; p <= A.hp.ha.mask; p += kThreads)
-            ((unsigned long long *)cs)[p] = 0ull;
+        for (uint32_t x = threadIdx.x; x < A.sketch_smem * P; x += kThreads) cs_s[x] = 0ull;
         __syncthreads();
+        cs_s += (size_t)(warp % A.sketch_smem) * P;
     }
 
     if (DIRECT) {
@@ -128,9 +148,10 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
                 const unsigned long long key = make_key(oi, j);
                 const unsigned act = __ballot_sync(kFull, valid);
                 my_terms += valid ? 1 : 0;
+                unsigned cnt = 1;
+                bool bucket = false;   // a locked-bucket update, made by the whole warp below
                 if (valid) {
                     if (VT == CRP_I32) {
-                        unsigned cnt = 1;
                         bool lead = true;
                         if (A.use_match) {
                             unsigned peers = __match_any_sync(act, key);
@@ -140,11 +161,14 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
                         if (lead && sketch) {   // CS[h(e)] += cnt s(e)
                             const long long c = sign_negative(A.sg, oi, j) ? -(long long)cnt
                                                                             : (long long)cnt;
-                            atomicAdd((unsigned long long *)cs + partition_hash(A.hp, oi, j),
-                                      (unsigned long long)c);
+                            const uint32_t pp = partition_hash(A.hp, oi, j);
+                            if (A.sketch_smem) atomicAdd(cs_s + pp, (unsigned long long)c);
+                            else atomicAdd((unsigned long long *)A.sketch + pp,
+                                           (unsigned long long)c);
                         }
                         if (lead && !dense_tiers(A, orank, owrank, oi, j, cnt)) {
-                            table_update(A.tv, partition_hash(A.hp, oi, j), key, cnt);
+                            if (LOCKED) bucket = true;
+                            else table_update(A.tv, partition_hash(A.hp, oi, j), key, cnt);
                             ++flushed;
                         }
                     } else {
@@ -152,13 +176,18 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
                         const float e = __fmaf_rn(owa, wb, -p);
                         const double d = (double)p + (double)e;
                         const uint32_t part = partition_hash(A.hp, oi, j);
-                        if (sketch)
-                            atomicAdd((double *)cs + part, sign_negative(A.sg, oi, j) ? -d : d);
+                        if (sketch) {
+                            const double sd = sign_negative(A.sg, oi, j) ? -d : d;
+                            if (A.sketch_smem) atomicAdd((double *)cs_s + part, sd);
+                            else atomicAdd((double *)A.sketch + part, sd);
+                        }
                         table_update(A.tv, part, key,
                                      (unsigned long long)__double_as_longlong(d));
                         ++flushed;
                     }
                 }
+                if (LOCKED)   // the warp is converged here
+                    locked_update_warp(A.tv, bucket, partition_hash(A.hp, oi, j), key, cnt);
             }
         }
     }
@@ -223,7 +252,7 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
             const int more = __syncthreads_or(st.done ? 0 : 1);
             if (ctrl[0] >= threshold) {
                 __syncthreads();
-                flush_table<VT>(keys, vals, S, A, flushed);
+                flush_table<VT, LOCKED>(keys, vals, S, A, flushed);
                 __syncthreads();
                 if (threadIdx.x == 0) ctrl[0] = 0u;
                 __syncthreads();
@@ -233,15 +262,22 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
     }
     if (!DIRECT) {
         __syncthreads();
-        flush_table<VT>(keys, vals, S, A, flushed);
+        flush_table<VT, LOCKED>(keys, vals, S, A, flushed);
     }
     if (sketch && A.sketch_smem) {   // add this CTA's estimators to the plan's
         __syncthreads();
-        for (uint32_t p = threadIdx.x; p <= A.hp.ha.mask; p += kThreads) {
-            const unsigned long long v = ((unsigned long long *)cs)[p];
-            if (v == 0ull) continue;
-            if (VT == CRP_I32) atomicAdd((unsigned long long *)A.sketch + p, v);
-            else atomicAdd((double *)A.sketch + p, __longlong_as_double((long long)v));
+        const unsigned long long *all = (const unsigned long long *)(smem_raw + 64);
+        for (uint32_t p = threadIdx.x; p < P; p += kThreads) {
+            if (VT == CRP_I32) {
+                unsigned long long v = 0;
+                for (uint32_t c = 0; c < A.sketch_smem; ++c) v += all[(size_t)c * P + p];
+                if (v) atomicAdd((unsigned long long *)A.sketch + p, v);
+            } else {
+                double v = 0.0;
+                for (uint32_t c = 0; c < A.sketch_smem; ++c)
+                    v += __longlong_as_double((long long)all[(size_t)c * P + p]);
+                if (v != 0.0) atomicAdd((double *)A.sketch + p, v);
+            }
         }
     }
 
@@ -257,16 +293,16 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
     }
 }
 
-template <int VT, bool DIRECT>
+template <int VT, bool DIRECT, bool LOCKED>
 static cudaError_t launch_one(const AccumulateArgs &args, const uint32_t *b_hash, int grid,
                               cudaStream_t s) {
     const size_t smem =
-        DIRECT ? 64 + (args.sketch_smem ? 8 * ((size_t)args.hp.ha.mask + 1) : 0)
+        DIRECT ? 64 + 8 * (size_t)args.sketch_smem * ((size_t)args.hp.ha.mask + 1)
                : accumulate_smem_bytes(VT, args.smem_slots);
-    cudaError_t e = cudaFuncSetAttribute(k_accumulate<VT, DIRECT>,
+    cudaError_t e = cudaFuncSetAttribute(k_accumulate<VT, DIRECT, LOCKED>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_accumulate<VT, DIRECT><<<grid, kThreads, smem, s>>>(args, b_hash);
+    k_accumulate<VT, DIRECT, LOCKED><<<grid, kThreads, smem, s>>>(args, b_hash);
     return cudaGetLastError();
 }
 
@@ -277,22 +313,25 @@ cudaError_t launch_accumulate(const AccumulateArgs &args, const uint32_t *b_hash
         cudaError_t e = cudaMemsetAsync(&args.tv.dc->work64, 0, sizeof(unsigned long long), s);
         if (e != cudaSuccess) return e;
     }
+    if (args.tv.summary == 2)   // locked buckets: int mode only
+        return direct ? launch_one<CRP_I32, true, true>(args, b_hash, grid, s)
+                      : launch_one<CRP_I32, false, true>(args, b_hash, grid, s);
     if (args.tv.value_type == CRP_I32)
-        return direct ? launch_one<CRP_I32, true>(args, b_hash, grid, s)
-                      : launch_one<CRP_I32, false>(args, b_hash, grid, s);
-    return direct ? launch_one<CRP_F32_COMP, true>(args, b_hash, grid, s)
-                  : launch_one<CRP_F32_COMP, false>(args, b_hash, grid, s);
+        return direct ? launch_one<CRP_I32, true, false>(args, b_hash, grid, s)
+                      : launch_one<CRP_I32, false, false>(args, b_hash, grid, s);
+    return direct ? launch_one<CRP_F32_COMP, true, false>(args, b_hash, grid, s)
+                  : launch_one<CRP_F32_COMP, false, false>(args, b_hash, grid, s);
 }
 
 template <int VT, bool DIRECT>
 static int occupancy_one(uint32_t smem_slots) {
     const size_t smem = DIRECT ? 64 : accumulate_smem_bytes(VT, smem_slots);
     int n = 0;
-    if (cudaFuncSetAttribute(k_accumulate<VT, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_accumulate<VT, DIRECT, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_accumulate<VT, DIRECT>, kThreads, smem)
-        != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_accumulate<VT, DIRECT, false>, kThreads,
+                                                      smem) != cudaSuccess)
         return 0;
     return n;
 }
@@ -605,16 +644,22 @@ __global__ void k_warm_flush(unsigned int *stripe, uint32_t W, int32_t n_other,
                              unsigned long long *flushed) {
     unsigned long long n = 0;
     const uint64_t total = (uint64_t)W * (uint64_t)n_other;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
-         x += (uint64_t)gridDim.x * blockDim.x) {
-        const unsigned int c = stripe[x];
-        if (!c) continue;
-        stripe[x] = 0u;
-        const uint32_t w = (uint32_t)items[x / (uint64_t)n_other];
-        const uint32_t o = (uint32_t)(x % (uint64_t)n_other);
-        const uint32_t i = rows ? w : o, j = rows ? o : w;
-        table_update(tv, partition_hash(hp, i, j), make_key(i, j), c);
-        ++n;
+    // warp-uniform trip count (blockDim is a multiple of 32): the warp's
+    // updates go out together
+    const uint64_t first = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+    for (uint64_t base = first; base < total; base += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = base + (threadIdx.x & 31u);
+        const unsigned int c = x < total ? stripe[x] : 0u;
+        uint32_t i = 0, j = 0;
+        if (c) {
+            stripe[x] = 0u;
+            const uint32_t w = (uint32_t)items[x / (uint64_t)n_other];
+            const uint32_t o = (uint32_t)(x % (uint64_t)n_other);
+            i = rows ? w : o;
+            j = rows ? o : w;
+            ++n;
+        }
+        table_update_warp(tv, c != 0u, partition_hash(hp, i, j), make_key(i, j), c);
     }
     // one atomic per warp: a counter taken by every thread serialises on one address
 #pragma unroll
@@ -637,14 +682,20 @@ __global__ void k_hot_flush(unsigned int *hot, uint32_t R, const int64_t *items_
                             const int64_t *items_b, HashPair hp, TableView tv,
                             unsigned long long *flushed) {
     unsigned long long n = 0;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < (uint64_t)R * R;
-         x += (uint64_t)gridDim.x * blockDim.x) {
-        const unsigned int c = hot[x];
-        if (!c) continue;
-        hot[x] = 0u;
-        const uint32_t i = (uint32_t)items_a[x / R], j = (uint32_t)items_b[x % R];
-        table_update(tv, partition_hash(hp, i, j), make_key(i, j), c);
-        ++n;
+    const uint64_t total = (uint64_t)R * R;
+    // warp-uniform trip count (blockDim is a multiple of 32)
+    const uint64_t first = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
+    for (uint64_t base = first; base < total; base += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = base + (threadIdx.x & 31u);
+        const unsigned int c = x < total ? hot[x] : 0u;
+        uint32_t i = 0, j = 0;
+        if (c) {
+            hot[x] = 0u;
+            i = (uint32_t)items_a[x / R];
+            j = (uint32_t)items_b[x % R];
+            ++n;
+        }
+        table_update_warp(tv, c != 0u, partition_hash(hp, i, j), make_key(i, j), c);
     }
     // one atomic per warp: a counter taken by every thread serialises on one address
 #pragma unroll

@@ -153,6 +153,9 @@ struct crp_plan {
     // chunk counter, count[B], fill[B], start[B + 1], overflow counter
     unsigned int *d_route_ctl = nullptr;
     uint32_t ov_chunks = 0;             // overflow chunks at the start of the pool
+    // locked-bucket summaries: a lock word per partition
+    bool locked = false;
+    unsigned int *d_locks = nullptr;
     // Count-Sketch: P estimators (int64 or fp64) and the sign hash
     void *d_sketch = nullptr;
     SignPair sg = {0, 0, 0, 0};
@@ -209,7 +212,10 @@ static crp_status alloc_summary(crp_plan *pl) {
     const uint32_t P = pl->d.P;
     pl->summary = true;
     pl->ell = pl->d.summary_counters;
-    const uint64_t cap = next_pow2(std::max<uint64_t>(4ull * pl->ell, 64));
+    pl->locked = (pl->d.flags & CRP_PLAN_LOCKED_SUMMARY) != 0;
+    // locked buckets: exactly ell counters used of next_pow2(ell) slots
+    const uint64_t cap = pl->locked ? next_pow2(pl->ell)
+                                    : next_pow2(std::max<uint64_t>(4ull * pl->ell, 64));
     const uint64_t rcap = pl->d.reserved_counters
                               ? next_pow2(std::max<uint64_t>(2ull * pl->d.reserved_counters, 64))
                               : 0;
@@ -240,6 +246,10 @@ static crp_status alloc_summary(crp_plan *pl) {
     CRP_CUDA(cudaMalloc(&pl->d_spill2, pl->spill_cap * sizeof(SpillRec)));
     pl->ctmp_grid = (int)std::min<uint32_t>(P, (uint32_t)pl->sm_count);
     CRP_CUDA(cudaMalloc(&pl->d_ctmp, (size_t)pl->ctmp_grid * pl->ell * sizeof(Slot)));
+    if (pl->locked) {
+        CRP_CUDA(cudaMalloc(&pl->d_locks, (size_t)P * 8));   // ticket, serving
+        CRP_CUDA(cudaMemsetAsync(pl->d_locks, 0, (size_t)P * 8, pl->stream));
+    }
     if (pl->d.reserved_counters) {
         CRP_CUDA(cudaMalloc(&pl->d_res_keys, (size_t)pl->d.reserved_counters * 8));
         const size_t words = (size_t)(pl->d.n_rows + 31) / 32 + (size_t)(pl->d.n_cols + 31) / 32;
@@ -269,17 +279,20 @@ extern "C" crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc,
         return fail(CRP_EINVAL, "smem_slots must be a power of two in [4096, 16384]");
     if (d.groups && (!is_pow2(d.groups) || d.groups > d.P))
         return fail(CRP_EINVAL, "groups must be a power of two <= P");
+    const bool locked = (d.flags & CRP_PLAN_LOCKED_SUMMARY) != 0;
+    if (locked && (d.summary_counters < 1 || d.summary_counters > 64 || d.reserved_counters ||
+                   (d.flags & CRP_PLAN_ROUTED)))
+        return fail(CRP_EINVAL, "CRP_PLAN_LOCKED_SUMMARY needs 1 <= summary_counters <= 64, no "
+                                "reserved_counters, not CRP_PLAN_ROUTED");
     if ((d.hot_items || d.warm_items) &&
         (d.hot_items > 4096 || d.warm_items > 4096 || d.value_type != CRP_I32 ||
-         !(d.flags & (CRP_PLAN_DIRECT | CRP_PLAN_ROUTED)) || d.summary_counters))
+         !(d.flags & (CRP_PLAN_DIRECT | CRP_PLAN_ROUTED)) || (d.summary_counters && !locked)))
         return fail(CRP_EINVAL, "hot_items / warm_items need CRP_PLAN_DIRECT or CRP_PLAN_ROUTED, "
-                                "CRP_I32, exact mode, <= 4096");
+                                "CRP_I32, <= 4096, and exact or locked-bucket tables");
     if (d.summary_counters && d.value_type != CRP_I32)
         return fail(CRP_EUNSUPPORTED, "summaries count {0,1} inputs (CRP_I32) only");
-    if ((d.flags & CRP_PLAN_SKETCH) &&
-        (d.flags & CRP_PLAN_ROUTED || !(d.flags & CRP_PLAN_DIRECT || d.summary_counters)))
-        return fail(CRP_EINVAL, "CRP_PLAN_SKETCH needs CRP_PLAN_DIRECT or a summary plan "
-                                "(not CRP_PLAN_ROUTED)");
+    if ((d.flags & CRP_PLAN_SKETCH) && (d.flags & CRP_PLAN_ROUTED))
+        return fail(CRP_EINVAL, "CRP_PLAN_SKETCH is not available with CRP_PLAN_ROUTED");
     if (d.summary_counters > (1u << 24))
         return fail(CRP_EINVAL, "summary_counters must be <= 2^24 per partition");
     if (d.reserved_counters > (1u << 24))
@@ -391,6 +404,7 @@ extern "C" void crp_plan_destroy(crp_plan *pl) {
     cudaFree(pl->d_order);
     cudaFree(pl->d_route_ctl);
     cudaFree(pl->d_sketch);
+    cudaFree(pl->d_locks);
     if (pl->ev0) cudaEventDestroy(pl->ev0);
     if (pl->ev1) cudaEventDestroy(pl->ev1);
     if (pl->evm) cudaEventDestroy(pl->evm);
@@ -406,6 +420,7 @@ extern "C" crp_status crp_reset(crp_plan *pl) {
         pl->launches += 1;
         CRP_CUDA(cudaMemsetAsync(pl->d_full, 0, pl->d.P * sizeof(unsigned int), pl->stream));
     }
+    if (pl->d_locks) CRP_CUDA(cudaMemsetAsync(pl->d_locks, 0, (size_t)pl->d.P * 8, pl->stream));
     if (pl->summary) {
         CRP_CUDA(cudaMemsetAsync(pl->d_live, 0, pl->d.P * 4, pl->stream));
         CRP_CUDA(cudaMemsetAsync(pl->d_floor, 0, pl->d.P * 4, pl->stream));
@@ -474,7 +489,9 @@ static TableView table_view(crp_plan *pl, Slot *slots, const unsigned long long 
     tv.spill_cap = pl->spill_cap;
     tv.dc = pl->dc;
     tv.value_type = pl->d.value_type;
-    tv.summary = pl->summary ? 1 : 0;
+    tv.summary = pl->summary ? (pl->locked ? 2 : 1) : 0;
+    tv.locks = pl->d_locks;
+    tv.bucket_ell = pl->ell;
     tv.live = pl->d_live;
     tv.floor = pl->d_floor;
     tv.hard_cap = 2u * pl->ell;
@@ -486,6 +503,14 @@ static TableView table_view(crp_plan *pl, Slot *slots, const unsigned long long 
         tv.res_bits_b = pl->d_res_bits + (pl->d.n_rows + 31) / 32;
     }
     return tv;
+}
+
+// Shared-memory copies of the sketch in the direct kernel (decided once
+// a.direct is final).
+static void set_sketch_copies(const crp_plan *pl, AccumulateArgs &a) {
+    a.sketch_smem = (a.sketch && a.direct && pl->d.P <= kSketchSmemMaxP)
+                        ? std::min<uint32_t>(kSketchSmemMaxP / pl->d.P, 16u)
+                        : 0u;
 }
 
 static AccumulateArgs make_args(crp_plan *pl, const crp_sparse *A, const crp_sparse *B,
@@ -528,8 +553,8 @@ static AccumulateArgs make_args(crp_plan *pl, const crp_sparse *A, const crp_spa
     if (pl->d_sketch) {
         a.sketch = pl->d_sketch;
         a.sg = pl->sg;
-        a.sketch_smem = pl->d.P <= kSketchSmemMaxP ? 1 : 0;
     }
+    set_sketch_copies(pl, a);
     return a;
 }
 
@@ -674,6 +699,7 @@ static crp_status summary_accumulate(crp_plan *pl, const crp_sparse *A, const cr
         Bs.n_major = k1 - k0;
         AccumulateArgs a = make_args(pl, &As, &Bs, B->idx, B->val, 1);
         a.direct = 1;
+        set_sketch_copies(pl, a);
         a.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
         if (pl->resv_rows) {
             // the reserved pairs all fall in the ragged block: no reserved-key
@@ -986,7 +1012,7 @@ extern "C" crp_status crp_outer_accumulate(crp_plan *pl, const crp_sparse *A, co
         st = estimate_and_allocate(pl, A, B, b_idx, b_val);
         if (st != CRP_OK) return st;
     }
-    if (pl->summary) return summary_accumulate(pl, A, B);
+    if (pl->summary && !pl->locked) return summary_accumulate(pl, A, B);
     if (pl->d.flags & CRP_PLAN_ROUTED) return routed_accumulate(pl, A, B);
     AccumulateArgs a = make_args(pl, A, B, b_idx, b_val, pl->G);
     a.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);

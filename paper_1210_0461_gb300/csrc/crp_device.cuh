@@ -80,6 +80,110 @@ __device__ __forceinline__ void summary_update(const TableView &tv, uint32_t p,
     spill_update(tv, key, v);
 }
 
+// Locked-bucket summary update of partition p: the partition is one
+// Space-Saving summary of bucket_ell counters (Preliminaries, weighted
+// updates), applied under the partition's lock in the order the updates
+// arrive -- the sequential algorithm on one arrival order of the
+// partition's stream.  A recorded key gains v; else the first empty counter
+// takes (key, v, 0); else the counter of least count (ties: smallest key)
+// becomes (key, min + v, min).  Counters hold the count in the low 32 bits
+// of val and the overestimation in the high 32 (the summary slot format).
+// The wait for the lock is bounded (about 4 s of SM clock); past it the
+// update is dropped and the status records a timeout.
+constexpr long long kLockWaitCycles = 8ll << 30;
+
+// The counters of the locked bucket at b after one weighted update (the
+// caller holds the bucket's lock).
+__device__ __forceinline__ void bucket_apply(Slot *b, uint32_t ell, unsigned long long key,
+                                             unsigned long long v) {
+    uint32_t at = ell, mn_at = 0;
+    unsigned long long mn_key = ~0ull;
+    unsigned int mn = 0xFFFFFFFFu;
+    bool empty = false;
+    for (uint32_t e = 0; e < ell; ++e) {
+        const unsigned long long k = __ldcg(&b[e].key);
+        if (k == key) {
+            at = e;
+            break;
+        }
+        if (k == kEmptyKey) {   // counters fill in order and are never emptied
+            at = e;
+            empty = true;
+            break;
+        }
+        const unsigned int c = (unsigned int)__ldcg(&b[e].val);
+        if (c < mn || (c == mn && k < mn_key)) {
+            mn = c;
+            mn_key = k;
+            mn_at = e;
+        }
+    }
+    if (at < ell && !empty) {
+        const unsigned long long val = __ldcg(&b[at].val);
+        __stcg(&b[at].val, (val & 0xFFFFFFFF00000000ull) | (unsigned int)((unsigned int)val + v));
+    } else if (empty) {
+        __stcg(&b[at].val, (unsigned long long)(unsigned int)v);
+        __stcg(&b[at].key, key);
+    } else {
+        __stcg(&b[mn_at].val, ((unsigned long long)mn << 32) | (unsigned int)(mn + v));
+        __stcg(&b[mn_at].key, key);
+    }
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *a) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int *a) {
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add_u32(unsigned int *a, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" : : "l"(a), "r"(v) : "memory");
+}
+
+// A ticket lock per partition (locks[2p] = next ticket, locks[2p + 1] = now
+// serving): waiters are served in the order they arrive, so none starves
+// however many wait for one bucket, and they poll with a plain load, sleeping
+// in proportion to their place in the queue.  A waiter gives up when the wait
+// passes the bound or when another waiter of the plan has already given up
+// (the plan then reports the timeout); returns whether the lock is held.
+__device__ __forceinline__ bool bucket_lock(const TableView &tv, uint32_t p) {
+    unsigned int *next = tv.locks + 2 * (size_t)p;
+    unsigned int *serving = next + 1;
+    const unsigned int ticket = atomicAdd(next, 1u);
+    const long long t0 = clock64();
+    while (true) {
+        const unsigned int now = ld_acquire_u32(serving);
+        if (now == ticket) return true;
+        if (ld_relaxed_u32(&tv.dc->status) & kStatusTimeout) return false;
+        if (clock64() - t0 > kLockWaitCycles) {
+            atomicOr(&tv.dc->status, kStatusTimeout);
+            return false;
+        }
+        const unsigned int ahead = ticket - now;
+        __nanosleep(ahead < 128u ? 64u * ahead : 8192u);
+    }
+}
+
+__device__ __forceinline__ void bucket_unlock(const TableView &tv, uint32_t p) {
+    red_release_add_u32(tv.locks + 2 * (size_t)p + 1, 1u);
+}
+
+// One thread's update of a locked bucket (a caller whose warp has no other
+// lane waiting for a lock).
+__device__ __forceinline__ void locked_summary_update(const TableView &tv, uint32_t p,
+                                                      unsigned long long key,
+                                                      unsigned long long v) {
+    if (!bucket_lock(tv, p)) return;
+    bucket_apply(tv.slots + tv.part_off[p], tv.bucket_ell, key, v);
+    bucket_unlock(tv, p);   // a release: the counters are written before the hand-on
+}
+
 // The keys of the 4-slot bucket at s (64 bytes, 64-byte aligned: partition
 // capacities are powers of two >= 64 and tables start 256-byte aligned), in
 // two 32-byte loads that do not allocate in L1 (a bucket is rarely read
@@ -92,13 +196,16 @@ __device__ __forceinline__ void load_bucket_keys(const Slot *s, unsigned long lo
     asm volatile("ld.global.L1::no_allocate.v4.u64 {%0, %1, %2, %3}, [%4];"
                  : "=l"(k4[2]), "=l"(v0), "=l"(k4[3]), "=l"(v1)
                  : "l"(s + 2));
+    (void)v0;
+    (void)v1;
 }
 
 // Add v (u32 count, or the bits of a double) to entry `key` of partition p.
 __device__ __forceinline__ void table_update(const TableView &tv, uint32_t p,
                                              unsigned long long key, unsigned long long v) {
     if (tv.summary) {
-        summary_update(tv, p, key, v);
+        if (tv.summary == 2) locked_summary_update(tv, p, key, v);
+        else summary_update(tv, p, key, v);
         return;
     }
     // Plain (cacheable) loads are enough here: a partition marked full stays
@@ -142,6 +249,76 @@ __device__ __forceinline__ void table_update(const TableView &tv, uint32_t p,
     atomicOr(&tv.part_full[p], 1u);
     atomicOr(&tv.dc->status, kStatusTableFull);
     spill_update(tv, key, v);
+}
+
+// The updates of a warp (lane with `has`) into its tables.  Every lane of
+// the warp must call it together.  For locked buckets the lanes that update
+// one partition form a group whose first lane takes one ticket of that
+// partition's lock.  Then, round after round, every group still waiting
+// checks whether its ticket is served; the groups served in a round apply
+// their members' updates (members of one group one after another, in lane
+// order; different groups side by side) and hand their locks on in the same
+// round.  No lane holds a lock from one round to the next, so lanes of one
+// warp never wait for each other, and the waits of the groups overlap.
+__device__ __forceinline__ void locked_update_warp(const TableView &tv, bool has, uint32_t p,
+                                                unsigned long long key, unsigned long long v) {
+    if (!__ballot_sync(0xffffffffu, has)) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(0xffffffffu, has ? p : 0xFFFFFFFFu);
+    const int first = __ffs(peers) - 1;
+    const bool leader = has && lane == first;
+    const unsigned rank = __popc(peers & ((1u << lane) - 1u));   // place in the group
+    const unsigned size = has ? __popc(peers) : 0u;
+    unsigned int *next = tv.locks + 2 * (size_t)(has ? p : 0u);
+    unsigned int *serving = next + 1;
+    unsigned int ticket = 0;
+    if (leader) ticket = atomicAdd(next, 1u);
+    unsigned pending = __ballot_sync(0xffffffffu, leader);   // groups, by first lane
+    const long long t0 = clock64();
+    while (pending) {
+        unsigned int ahead = 0xFFFFFFFFu;
+        bool served = false;
+        if (leader && ((pending >> lane) & 1u)) {
+            const unsigned int now = ld_acquire_u32(serving);
+            served = now == ticket;
+            ahead = ticket - now;
+        }
+        const unsigned srv = __ballot_sync(0xffffffffu, served);
+        if (srv) {
+            const bool mine = has && ((srv >> first) & 1u);   // my group is served
+            const unsigned rounds = __reduce_max_sync(0xffffffffu, mine ? size : 0u);
+            Slot *b = tv.slots + tv.part_off[has ? p : 0u];
+            for (unsigned r = 0; r < rounds; ++r) {
+                if (mine && rank == r) bucket_apply(b, tv.bucket_ell, key, v);
+                __syncwarp();   // each member sees the previous member's counters
+            }
+            if (served) {
+                __threadfence();   // every member's counters before the hand-on
+                red_release_add_u32(serving, 1u);
+            }
+            pending &= ~srv;
+            continue;
+        }
+        // nobody served this round: give up on the bound or when the plan has
+        // already failed, else sleep in proportion to the shortest queue
+        bool stop = false;
+        if (lane == 0)
+            stop = (ld_relaxed_u32(&tv.dc->status) & kStatusTimeout) ||
+                   clock64() - t0 > kLockWaitCycles;
+        if (__shfl_sync(0xffffffffu, stop, 0)) {
+            if (lane == 0) atomicOr(&tv.dc->status, kStatusTimeout);
+            return;
+        }
+        const unsigned int wait = __reduce_min_sync(0xffffffffu, ahead);
+        __nanosleep(wait < 128u ? 64u * wait : 8192u);
+    }
+}
+
+__device__ __forceinline__ void table_update_warp(const TableView &tv, bool has, uint32_t p,
+                                                  unsigned long long key,
+                                                  unsigned long long v) {
+    if (tv.summary == 2) locked_update_warp(tv, has, p, key, v);
+    else if (has) table_update(tv, p, key, v);
 }
 
 // ---------------------------------------------------------------------------

@@ -113,7 +113,12 @@ struct TableView {
     DevCounters *dc = nullptr;
     int value_type = 0;
     // summary mode (Space-Saving semantics per partition)
-    int summary = 0;                          // 1: tables are counter summaries
+    int summary = 0;                          // 1: tables are counter summaries;
+                                              // 2: one locked bucket of bucket_ell
+                                              //    counters per partition
+    unsigned int *locks = nullptr;            // summary 2: a ticket lock per partition
+                                              //    (next ticket, now serving)
+    uint32_t bucket_ell = 0;
     unsigned int *live = nullptr;             // occupied slots per partition
     const unsigned int *floor = nullptr;      // current floor (min count) per partition
     unsigned int hard_cap = 0;                // max live slots before new keys spill
@@ -170,12 +175,12 @@ struct AccumulateArgs {
     // pairs i < j of T^T T with a_k == b_k (same sorted list): the window of
     // the a entry at position x starts at position x + 1 of b_k
     int sym_upper = 0;
-    // Count-Sketch (direct kernel): P estimators, int64 (int mode) or fp64
-    // (real mode); sketch_smem: each CTA sums into shared memory first and
-    // adds its P estimators at the end
+    // Count-Sketch: P estimators, int64 (int mode) or fp64 (real mode);
+    // sketch_smem > 0 (direct kernel): each CTA sums into that many copies
+    // of the estimators in shared memory and adds them at the end
     void *sketch = nullptr;
     SignPair sg = {0, 0, 0, 0};
-    int sketch_smem = 0;
+    uint32_t sketch_smem = 0;
 };
 
 // Count-Sketch estimates from t <= kSketchMaxT plans (crp_sketch.cu)
@@ -190,7 +195,8 @@ struct SketchSet {
 cudaError_t launch_sketch_estimate(const SketchSet &S, const int32_t *i, const int32_t *j,
                                    int64_t n, int32_t n_rows, int32_t n_cols, double *out,
                                    unsigned int *bad, cudaStream_t s);
-// largest P whose per-CTA sketch the direct kernel keeps in shared memory
+// the direct kernel keeps its sketch in shared memory for P <= 4096, in
+// 4096 / P copies (at most one per warp): 32 KB per CTA
 constexpr uint32_t kSketchSmemMaxP = 4096;
 
 // Two-phase (routed) accumulation: bins of records per partition group.

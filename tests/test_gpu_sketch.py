@@ -1,6 +1,7 @@
 """GPU parity of the per-partition Count-Sketch (Preliminaries; Figure 1)
 against the oracle: integer sketches bit-exact (direct exact plans with every
-dense tier, UPPER, partition intervals, summary plans with reserved keys,
+dense tier, on-chip-table plans, UPPER, partition intervals, summary plans
+with reserved keys,
 streaming calls, reset), real sketches within the fp64 summation bound, the
 median estimate over t plans exactly, and the sketch of the full
 10,000,000-transaction co-occurrence workload through its Fourier transform
@@ -51,6 +52,7 @@ C1_CONFIGS = [
     dict(P=64, flags=4 | 1 | 2),                     # no warp match
     dict(P=64, hot_items=500), dict(P=256, hot_items=64, warm_items=16),
     dict(P=64, warm_items=100),
+    dict(P=64, flags=2), dict(P=8192, groups=4, flags=2),   # on-chip table: added at flush
 ]
 
 
@@ -121,13 +123,13 @@ def test_random_edge_cases_sketch(crp, seed, P, G):
     plan.close()
 
 
-@pytest.mark.parametrize("seed,P", [(10, 32), (11, 8192)])
-def test_real_sketch_within_summation_bound(crp, seed, P):
+@pytest.mark.parametrize("seed,P,fl", [(10, 32, None), (11, 8192, None), (12, 64, 2)])
+def test_real_sketch_within_summation_bound(crp, seed, P, fl):
     # every term is the exact fp32 product; the fp64 sums differ from the
     # oracle's only in order: |error| <= n eps sum |terms| per estimator
     A, B = _random_case(seed, 600, 80, 90, 0.15, True)
     ref = O.exact_product(A, B, O.FULL)
-    plan = _plan(crp, 80, 90, P, value_type=crp.CRP_F32_COMP)
+    plan = _plan(crp, 80, 90, P, value_type=crp.CRP_F32_COMP, flags=fl)
     plan.accumulate(crp.to_device(A), crp.to_device(B))
     plan.sync()
     got = plan.sketch()
@@ -210,8 +212,6 @@ def test_invalid_uses_are_rejected(crp):
     import torch
     with pytest.raises(crp.CrpError):
         crp.Plan(100, 100, 16, 1, 2, flags=crp.CRP_PLAN_SKETCH | crp.CRP_PLAN_ROUTED)
-    with pytest.raises(crp.CrpError):
-        crp.Plan(100, 100, 16, 1, 2, flags=crp.CRP_PLAN_SKETCH)     # on-chip tables
     plain = crp.Plan(100, 100, 16, 1, 2, flags=crp.CRP_PLAN_DIRECT)
     with pytest.raises(crp.CrpError):
         plain.sketch()
