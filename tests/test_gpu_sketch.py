@@ -141,6 +141,28 @@ def test_real_sketch_within_summation_bound(crp, seed, P, fl):
     plan.close()
 
 
+def test_signed_values_sketch(crp):
+    # Count-Sketch allows signed weights: inputs of both signs, so entries
+    # cancel; the bound uses the absolute terms (|a||b| summed per estimator)
+    A, B = _random_case(13, 600, 80, 90, 0.15, True)
+    rng = np.random.default_rng(99)
+    A.val[:] = A.val * np.where(rng.random(len(A.val)) < 0.5, -1, 1).astype(np.float32)
+    B.val[:] = B.val * np.where(rng.random(len(B.val)) < 0.5, -1, 1).astype(np.float32)
+    ref = O.exact_product(A, B, O.FULL)
+    assert (ref.w < 0).any() and (ref.w > 0).any()
+    absA = O.Compressed(A.ptr, A.idx, np.abs(A.val), A.n_minor)
+    absB = O.Compressed(B.ptr, B.idx, np.abs(B.val), B.n_minor)
+    mag = O.exact_product(absA, absB, O.FULL).w.sum()
+    for P, fl in ((64, None), (64, 2), (8192, None)):
+        plan = _plan(crp, 80, 90, P, value_type=crp.CRP_F32_COMP, flags=fl)
+        plan.accumulate(crp.to_device(A), crp.to_device(B))
+        plan.sync()
+        want = O.count_sketch(ref, P, ci.SEED_A, ci.SEED_B)
+        bound = O.total_terms(A, B) * 2.0 ** -52 * mag
+        np.testing.assert_allclose(plan.sketch(), want, rtol=0, atol=bound)
+        plan.close()
+
+
 def test_summary_plan_sketch_with_reserved_keys(crp):
     # the summaries drop weight, the sketch does not: in a summary plan with
     # reserved keys (dense block) the sketch is still exact, over two calls
