@@ -743,6 +743,7 @@ def main():
                        "smem_slots": args.smem_slots, "warp_match": not args.no_match,
                        "mode": args.mode, "hot_items": args.hot, "warm_items": args.warm,
                        "target_load_pct": args.load, "count_sketch": bool(args.sketch),
+                       "topk_from_hot_block": plan.topk_certified_calls(),
                        "autotune": tuned,
                        "terms_per_step": terms_step, "entries": entries,
                        "nnz": int(T.nnz), "l2": "inputs (0.8 GB) and tables "

@@ -239,6 +239,17 @@ crp_status crp_sync(crp_plan *plan);
 crp_status crp_topk(crp_plan *plan, int32_t k, uint32_t flags, int32_t *i_out, int32_t *j_out,
                     double *w_out, double *w_lower, int32_t *n_out);
 
+/* How many crp_topk calls of the plan were answered from the hot block alone.
+ * For CRP_I32 exact plans with hot_items > 0 the plan keeps the degree of
+ * every row and column over the calls since the last reset (deg(i) = number
+ * of outer products whose a_k holds i; deg(j) likewise in B).  An entry is at
+ * most min(deg(i), deg(j)), so when the k-th heaviest of the hot pairs
+ * (hot rows x hot columns of the last call) weighs more than every degree
+ * outside the hot set, no other entry can be in the top k and crp_topk
+ * answers from the hot pairs without scanning the tables; otherwise it scans
+ * them.  The result is the same either way. */
+uint64_t crp_topk_certified_calls(const crp_plan *plan);
+
 /* Summary mode (desc.summary_counters = ell > 0, CRP_I32 only): each
  * partition keeps a counter summary with the Space-Saving guarantees of the
  * paper's Preliminaries -- for every key of partition p with stream weight

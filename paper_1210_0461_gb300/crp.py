@@ -78,6 +78,7 @@ _SIGS = {
     "crp_topk": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32, _P, _P, _P, _P,
                                 ctypes.POINTER(ctypes.c_int32)]),
     "crp_partition_of": (ctypes.c_uint32, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "crp_topk_certified_calls": (ctypes.c_uint64, [_P]),
     "crp_reserve": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
     "crp_export_partitions": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint32, _P, _P, _P, _P,
                                              ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
@@ -301,6 +302,10 @@ class Plan:
         _check(self._lib.crp_topk(self._h, k, flags, *ptrs, ctypes.byref(n)), "crp_topk")
         m = n.value
         return i[:m], j[:m], w[:m], wl[:m]
+
+    def topk_certified_calls(self) -> int:
+        """crp_topk calls answered from the hot block alone (see include/crp.h)."""
+        return int(self._lib.crp_topk_certified_calls(self._h))
 
     def export(self, p_begin: int = 0, p_end: int | None = None):
         """All entries of partitions [p_begin, p_end): (i, j, w, w_lower, counts

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "crp_internal.cuh"
+#include "crp_topk.cuh"
 
 using namespace crp;
 
@@ -153,6 +154,11 @@ struct crp_plan {
     // chunk counter, count[B], fill[B], start[B + 1], overflow counter
     unsigned int *d_route_ctl = nullptr;
     uint32_t ov_chunks = 0;             // overflow chunks at the start of the pool
+    // certified top-k: cumulative degrees of rows and columns since the last
+    // reset, the hot pairs' candidate buffer, calls answered from it
+    unsigned long long *d_deg_a = nullptr, *d_deg_b = nullptr;
+    TopkCand *d_hot_cand = nullptr;
+    uint64_t topk_certified = 0;
     // locked-bucket summaries: a lock word per partition
     bool locked = false;
     unsigned int *d_locks = nullptr;
@@ -405,6 +411,9 @@ extern "C" void crp_plan_destroy(crp_plan *pl) {
     cudaFree(pl->d_route_ctl);
     cudaFree(pl->d_sketch);
     cudaFree(pl->d_locks);
+    cudaFree(pl->d_deg_a);
+    cudaFree(pl->d_deg_b);
+    cudaFree(pl->d_hot_cand);
     if (pl->ev0) cudaEventDestroy(pl->ev0);
     if (pl->ev1) cudaEventDestroy(pl->ev1);
     if (pl->evm) cudaEventDestroy(pl->evm);
@@ -421,6 +430,10 @@ extern "C" crp_status crp_reset(crp_plan *pl) {
         CRP_CUDA(cudaMemsetAsync(pl->d_full, 0, pl->d.P * sizeof(unsigned int), pl->stream));
     }
     if (pl->d_locks) CRP_CUDA(cudaMemsetAsync(pl->d_locks, 0, (size_t)pl->d.P * 8, pl->stream));
+    if (pl->d_deg_a) {
+        CRP_CUDA(cudaMemsetAsync(pl->d_deg_a, 0, (size_t)pl->d.n_rows * 8, pl->stream));
+        CRP_CUDA(cudaMemsetAsync(pl->d_deg_b, 0, (size_t)pl->d.n_cols * 8, pl->stream));
+    }
     if (pl->summary) {
         CRP_CUDA(cudaMemsetAsync(pl->d_live, 0, pl->d.P * 4, pl->stream));
         CRP_CUDA(cudaMemsetAsync(pl->d_floor, 0, pl->d.P * 4, pl->stream));
@@ -924,6 +937,21 @@ static crp_status select_hot_items(crp_plan *pl, const crp_sparse *A, const crp_
         CRP_CUDA(launch_hot_ranks(pl->d_rank_a, pl->d.n_rows, pl->d_items_a, pl->hot_R, s));
         CRP_CUDA(launch_hot_ranks(pl->d_rank_b, pl->d.n_cols, pl->d_items_b, pl->hot_R, s));
         pl->launches += 2 * 5 + 6;
+        if (!pl->summary && pl->d.value_type == CRP_I32) {
+            // degrees of every row and column over all calls since the reset:
+            // the bound that lets crp_topk answer from the hot pairs
+            if (!pl->d_deg_a) {
+                CRP_CUDA(cudaMalloc(&pl->d_deg_a, (size_t)pl->d.n_rows * 8));
+                CRP_CUDA(cudaMalloc(&pl->d_deg_b, (size_t)pl->d.n_cols * 8));
+                CRP_CUDA(cudaMemsetAsync(pl->d_deg_a, 0, (size_t)pl->d.n_rows * 8, s));
+                CRP_CUDA(cudaMemsetAsync(pl->d_deg_b, 0, (size_t)pl->d.n_cols * 8, s));
+            }
+            CRP_CUDA(launch_degrees(A->idx, A->nnz, pl->d.n_rows, pl->d_rank_a, pl->hot_R,
+                                    pl->d_items_a, pl->d_deg_a, pl->sm_count, s));
+            CRP_CUDA(launch_degrees(B->idx, B->nnz, pl->d.n_cols, pl->d_rank_b, pl->hot_R,
+                                    pl->d_items_b, pl->d_deg_b, pl->sm_count, s));
+            pl->launches += 2;
+        }
     }
     if (pl->warm_W) {
         CRP_CUDA(select_top(pl->d_cnt_a, pl->d.n_rows, pl->warm_W, pl->d_witems_a, pl->d_sel, s));
@@ -1145,15 +1173,13 @@ static bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-extern "C" crp_status crp_topk(crp_plan *pl, int32_t k, uint32_t flags, int32_t *i_out,
-                               int32_t *j_out, double *w_out, double *w_lower, int32_t *n_out) {
-    if (!pl || !i_out || !j_out || !w_out || !n_out) return fail(CRP_EINVAL, "null argument");
-    if (k < 1 || k > kTopkSortMax) return fail(CRP_EINVAL, "k must be in [1, 8192]");
-    *n_out = 0;
-    if (!pl->tables_ready) return CRP_OK;
-    const int upper = (flags & CRP_TOPK_UPPER) ? 1 : 0;
+// The k heaviest of n_c candidates (an MSD radix select first when more than
+// one CTA can sort), sorted and written out; *n_out = entries written and
+// *kth_w (nullable) = the weight of the last one.  cand stays the caller's.
+static crp_status topk_from_candidates(crp_plan *pl, const TopkCand *cand, uint64_t n_c, int32_t k,
+                                       int32_t *i_out, int32_t *j_out, double *w_out,
+                                       double *w_lower, int32_t *n_out, double *kth_w) {
     cudaStream_t s = pl->stream;
-    const int vt = pl->summary ? kVTSummary : pl->d.value_type;
     unsigned int *cnt = pl->d_topk_hist + kTopkBuckets;  // 3 counters + 256-bin hist after
     unsigned int *dhist = cnt + 4;
     crp_status st = CRP_OK;
@@ -1162,56 +1188,7 @@ extern "C" crp_status crp_topk(crp_plan *pl, int32_t k, uint32_t flags, int32_t 
             st = fail(CRP_ECUDA, std::string("topk: ") + cudaGetErrorString(e));
         return st == CRP_OK;
     };
-    // candidates: the slots at or above a histogram bucket.  A large table is
-    // first tried with a 1/32 sample histogram and a bucket expected to hold
-    // about 2k + 256 slots; k or more collected slots at or above a bucket
-    // contain the top k, otherwise the exact histogram decides.
-    const int shift = pl->n_slots >= (1ull << 26) ? 5 : 0;
-    TopkCand *cand = nullptr, *sel = nullptr, *keep = nullptr;
-    uint64_t n_c = 0;
-    std::vector<unsigned int> hist(kTopkBuckets);
-    for (int sh : {shift, 0}) {
-        CRP_CUDA(launch_topk_hist(pl->slots, pl->n_slots, vt, upper, sh, pl->d_topk_hist, s));
-        pl->launches += 1;
-        CRP_CUDA(cudaMemcpyAsync(hist.data(), pl->d_topk_hist, kTopkBuckets * 4,
-                                 cudaMemcpyDeviceToHost, s));
-        CRP_CUDA(cudaStreamSynchronize(s));
-        const uint64_t want = sh ? (((uint64_t)2 * k + 256) >> sh) + 1 : (uint64_t)k;
-        uint64_t cum = 0;
-        int b = kTopkBuckets - 1;
-        for (; b >= 0; --b) {
-            cum += hist[b];
-            if (cum >= want) break;
-        }
-        if (b < 0) {
-            if (sh) continue;   // the sample holds too few slots: take the exact histogram
-            b = 0;
-        }
-        if (cum == 0) break;
-        // capacity: the exact count, or twice the sampled estimate plus slack
-        const uint64_t cap = sh ? (cum << sh) * 2 + 4 * (uint64_t)k + 1024 : cum;
-        cudaFree(cand);
-        if (cap > 0xffffffffull) return fail(CRP_EUNSUPPORTED, "too many top-k candidates");
-        cand = nullptr;
-        CRP_CUDA(cudaMalloc(&cand, cap * sizeof(TopkCand)));
-        CRP_CUDA(launch_topk_collect(pl->slots, pl->n_slots, vt, upper, (unsigned)b, cand, cnt,
-                                     (unsigned)cap, s));
-        pl->launches += 1;
-        if (sh == 0) {   // the exact histogram already counted the candidates
-            n_c = cum;
-            break;
-        }
-        unsigned int got = 0;
-        CRP_CUDA(cudaMemcpyAsync(&got, cnt, 4, cudaMemcpyDeviceToHost, s));
-        CRP_CUDA(cudaStreamSynchronize(s));
-        n_c = got;
-        if (got >= (unsigned)k && got <= cap) break;
-        n_c = 0;
-    }
-    if (n_c == 0) {
-        cudaFree(cand);
-        return CRP_OK;
-    }
+    TopkCand *sel = nullptr, *keep = nullptr;
     const TopkCand *final_c = cand;
     unsigned int final_sort = (unsigned int)n_c;  // candidates to sort
     unsigned int final_n = (unsigned int)std::min<uint64_t>(n_c, (uint64_t)k);
@@ -1219,7 +1196,7 @@ extern "C" crp_status crp_topk(crp_plan *pl, int32_t k, uint32_t flags, int32_t 
         // MSD radix select on the candidates down to exactly k
         cuda_ok(cudaMalloc(&sel, (size_t)k * sizeof(TopkCand)));
         cuda_ok(cudaMalloc(&keep, n_c * sizeof(TopkCand)));
-        TopkCand *und = cand, *nxt = keep;
+        TopkCand *und = const_cast<TopkCand *>(cand), *nxt = keep;
         unsigned int n_und = (unsigned int)n_c, n_sel = 0, need = (unsigned int)k;
         cuda_ok(cudaMemsetAsync(cnt + 1, 0, 4, s));  // sel count
         for (int d = 0; d < 16 && st == CRP_OK && need > 0; ++d) {
@@ -1277,12 +1254,131 @@ extern "C" crp_status crp_topk(crp_plan *pl, int32_t k, uint32_t flags, int32_t 
         if (w_lower) cuda_ok(cudaMemcpyAsync(w_lower, dwl, final_n * 8, cudaMemcpyDeviceToHost, s));
     }
     cuda_ok(cudaStreamSynchronize(s));
+    if (st == CRP_OK && kth_w && final_n)
+        cuda_ok(cudaMemcpy(kth_w, dw + (final_n - 1), 8, cudaMemcpyDeviceToHost));
     cudaFree(stage);
-    cudaFree(cand);
     cudaFree(sel);
     cudaFree(keep);
     if (st == CRP_OK) *n_out = (int32_t)final_n;
     return st;
+}
+
+
+// Top k certified from the hot block ({0,1} inputs, exact tables, a hot set):
+// the hot pairs present in the tables are the candidates, and their top k is
+// the answer when its k-th weight is above every degree outside the hot set
+// (each entry is at most the smaller degree of its row and column, so no
+// entry outside the hot block can reach it).  *done = false when the bound
+// does not hold or there are fewer than k candidates: the caller then scans
+// the tables.
+static crp_status topk_certified(crp_plan *pl, int32_t k, int upper, int32_t *i_out,
+                                 int32_t *j_out, double *w_out, double *w_lower, int32_t *n_out,
+                                 bool *done) {
+    *done = false;
+    const uint32_t R = pl->hot_R;
+    cudaStream_t s = pl->stream;
+    if (!pl->d_hot_cand)
+        CRP_CUDA(cudaMalloc(&pl->d_hot_cand, (size_t)R * R * sizeof(TopkCand)));
+    unsigned int *count = pl->d_topk_hist + kTopkBuckets + 3;
+    unsigned long long *bound = pl->d_scratch64 + 2 * (size_t)pl->d.P + 10;
+    CRP_CUDA(cudaMemsetAsync(bound, 0, 8, s));
+    CRP_CUDA(launch_topk_hot_candidates(pl->slots, pl->d_off, pl->d_mask, pl->hp, pl->d_items_a,
+                                        pl->d_items_b, R, upper, pl->d_hot_cand, count, s));
+    CRP_CUDA(launch_max_outside(pl->d_deg_a, pl->d.n_rows, pl->d_rank_a, R, bound, s));
+    CRP_CUDA(launch_max_outside(pl->d_deg_b, pl->d.n_cols, pl->d_rank_b, R, bound, s));
+    pl->launches += 3;
+    unsigned int n_c = 0;
+    unsigned long long S = 0;
+    CRP_CUDA(cudaMemcpyAsync(&n_c, count, 4, cudaMemcpyDeviceToHost, s));
+    CRP_CUDA(cudaMemcpyAsync(&S, bound, 8, cudaMemcpyDeviceToHost, s));
+    CRP_CUDA(cudaStreamSynchronize(s));
+    if (n_c < (unsigned int)k) return CRP_OK;
+    double kth = 0.0;
+    int32_t n = 0;
+    crp_status st = topk_from_candidates(pl, pl->d_hot_cand, n_c, k, i_out, j_out, w_out, w_lower,
+                                         &n, &kth);
+    if (st != CRP_OK) return st;
+    if (n == k && kth > (double)S) {
+        *n_out = n;
+        *done = true;
+        pl->topk_certified += 1;
+    }
+    return CRP_OK;
+}
+
+extern "C" crp_status crp_topk(crp_plan *pl, int32_t k, uint32_t flags, int32_t *i_out,
+                               int32_t *j_out, double *w_out, double *w_lower, int32_t *n_out) {
+    if (!pl || !i_out || !j_out || !w_out || !n_out) return fail(CRP_EINVAL, "null argument");
+    if (k < 1 || k > kTopkSortMax) return fail(CRP_EINVAL, "k must be in [1, 8192]");
+    *n_out = 0;
+    if (!pl->tables_ready) return CRP_OK;
+    const int upper = (flags & CRP_TOPK_UPPER) ? 1 : 0;
+    if (!pl->summary && pl->d.value_type == CRP_I32 && pl->hot_R && pl->d_deg_a) {
+        bool done = false;
+        crp_status cs = topk_certified(pl, k, upper, i_out, j_out, w_out, w_lower, n_out, &done);
+        if (cs != CRP_OK || done) return cs;
+    }
+    cudaStream_t s = pl->stream;
+    const int vt = pl->summary ? kVTSummary : pl->d.value_type;
+    unsigned int *cnt = pl->d_topk_hist + kTopkBuckets;  // collected-candidate counter
+    // candidates: the slots at or above a histogram bucket.  A large table is
+    // first tried with a 1/32 sample histogram and a bucket expected to hold
+    // about 2k + 256 slots; k or more collected slots at or above a bucket
+    // contain the top k, otherwise the exact histogram decides.
+    const int shift = pl->n_slots >= (1ull << 26) ? 5 : 0;
+    TopkCand *cand = nullptr;
+    uint64_t n_c = 0;
+    std::vector<unsigned int> hist(kTopkBuckets);
+    for (int sh : {shift, 0}) {
+        CRP_CUDA(launch_topk_hist(pl->slots, pl->n_slots, vt, upper, sh, pl->d_topk_hist, s));
+        pl->launches += 1;
+        CRP_CUDA(cudaMemcpyAsync(hist.data(), pl->d_topk_hist, kTopkBuckets * 4,
+                                 cudaMemcpyDeviceToHost, s));
+        CRP_CUDA(cudaStreamSynchronize(s));
+        const uint64_t want = sh ? (((uint64_t)2 * k + 256) >> sh) + 1 : (uint64_t)k;
+        uint64_t cum = 0;
+        int b = kTopkBuckets - 1;
+        for (; b >= 0; --b) {
+            cum += hist[b];
+            if (cum >= want) break;
+        }
+        if (b < 0) {
+            if (sh) continue;   // the sample holds too few slots: take the exact histogram
+            b = 0;
+        }
+        if (cum == 0) break;
+        // capacity: the exact count, or twice the sampled estimate plus slack
+        const uint64_t cap = sh ? (cum << sh) * 2 + 4 * (uint64_t)k + 1024 : cum;
+        cudaFree(cand);
+        if (cap > 0xffffffffull) return fail(CRP_EUNSUPPORTED, "too many top-k candidates");
+        cand = nullptr;
+        CRP_CUDA(cudaMalloc(&cand, cap * sizeof(TopkCand)));
+        CRP_CUDA(launch_topk_collect(pl->slots, pl->n_slots, vt, upper, (unsigned)b, cand, cnt,
+                                     (unsigned)cap, s));
+        pl->launches += 1;
+        if (sh == 0) {   // the exact histogram already counted the candidates
+            n_c = cum;
+            break;
+        }
+        unsigned int got = 0;
+        CRP_CUDA(cudaMemcpyAsync(&got, cnt, 4, cudaMemcpyDeviceToHost, s));
+        CRP_CUDA(cudaStreamSynchronize(s));
+        n_c = got;
+        if (got >= (unsigned)k && got <= cap) break;
+        n_c = 0;
+    }
+    if (n_c == 0) {
+        cudaFree(cand);
+        return CRP_OK;
+    }
+    crp_status fs = topk_from_candidates(pl, cand, n_c, k, i_out, j_out, w_out, w_lower, n_out,
+                                         nullptr);
+    cudaFree(cand);
+    return fs;
+}
+
+extern "C" uint64_t crp_topk_certified_calls(const crp_plan *pl) {
+    return pl ? pl->topk_certified : 0;
 }
 
 extern "C" crp_status crp_export_partitions(crp_plan *pl, uint32_t p0, uint32_t p1, int32_t *i_out,

@@ -14,7 +14,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "crp_internal.cuh"
+#include "crp_topk.cuh"
 
 namespace crp {
 
@@ -270,6 +273,131 @@ cudaError_t launch_export_range(const Slot *slots, const unsigned long long *par
     uint32_t n = p1 - p0;
     k_export<<<n < 4096 ? n : 4096, 256, 0, s>>>(slots, part_off, part_mask, p0, p1, base,
                                                   value_type, i_out, j_out, w_out, wl_out);
+    return cudaGetLastError();
+}
+
+
+
+// ---------------------------------------------------------------------------
+// Top-k certified from the hot block
+// ---------------------------------------------------------------------------
+//
+// For {0,1} inputs an entry is bounded by the degrees of its row and column:
+// C(i,j) = sum_k a_k(i) b_k(j) <= min(deg_A(i), deg_B(j)).  So every entry
+// with its row outside the hot rows or its column outside the hot columns is
+// at most S = max(max deg_A outside the hot rows, max deg_B outside the hot
+// columns).  When the k-th heaviest entry among the hot pairs (hot row x hot
+// column) is above S, no other entry can enter the top k, and the top k of
+// the hot pairs is the exact answer: the full-table scan is skipped.
+
+namespace {
+constexpr int kDegreeSmem = 4096;   // hot ranks counted in shared memory first
+}
+
+// deg[v] += occurrences of v in idx[0, nnz); items of hot rank r < R count
+// in shared memory first (the Zipf head would serialise on a few addresses).
+__global__ void k_degrees(const int32_t *__restrict__ idx, int64_t nnz, int32_t n,
+                          const uint16_t *__restrict__ rank, uint32_t R,
+                          const int64_t *__restrict__ items, unsigned long long *deg) {
+    __shared__ unsigned int h[kDegreeSmem];
+    for (uint32_t r = threadIdx.x; r < R; r += blockDim.x) h[r] = 0u;
+    __syncthreads();
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nnz;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = idx[x];
+        if (v < 0 || v >= n) continue;
+        const uint32_t r = R ? rank[v] : 0xFFFFu;
+        if (r < R) atomicAdd(&h[r], 1u);
+        else atomicAdd(&deg[v], 1ull);
+    }
+    __syncthreads();
+    for (uint32_t r = threadIdx.x; r < R; r += blockDim.x)
+        if (h[r]) atomicAdd(&deg[items[r]], (unsigned long long)h[r]);
+}
+
+cudaError_t launch_degrees(const int32_t *idx, int64_t nnz, int32_t n, const uint16_t *rank,
+                           uint32_t R, const int64_t *items, unsigned long long *deg,
+                           int sm_count, cudaStream_t s) {
+    if (nnz <= 0) return cudaSuccess;
+    if (R > (uint32_t)kDegreeSmem) R = 0;   // (hot sets are at most 4096 items)
+    const int64_t want = (nnz + 1023) / 1024;
+    const int grid = (int)std::min<int64_t>(want, (int64_t)sm_count * 4);
+    k_degrees<<<grid > 0 ? grid : 1, 1024, 0, s>>>(idx, nnz, n, R ? rank : nullptr, R, items, deg);
+    return cudaGetLastError();
+}
+
+// out[0] = max deg[v] over the v whose hot rank is >= R (atomicMax).
+__global__ void k_max_outside(const unsigned long long *__restrict__ deg, int32_t n,
+                              const uint16_t *__restrict__ rank, uint32_t R,
+                              unsigned long long *out) {
+    unsigned long long m = 0;
+    for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        if (rank[v] >= R && deg[v] > m) m = deg[v];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long o = __shfl_down_sync(0xffffffffu, m, d);
+        m = o > m ? o : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+cudaError_t launch_max_outside(const unsigned long long *deg, int32_t n, const uint16_t *rank,
+                               uint32_t R, unsigned long long *out, cudaStream_t s) {
+    const int grid = (int)std::min<int64_t>(((int64_t)n + 255) / 256, 1024);
+    k_max_outside<<<grid > 0 ? grid : 1, 256, 0, s>>>(deg, n, rank, R, out);
+    return cudaGetLastError();
+}
+
+// Candidates: every hot pair (items_a[r], items_b[c]) present in the exact
+// tables (read-only probe from its bucket), with its count.
+__global__ void k_topk_hot_candidates(const Slot *__restrict__ slots,
+                                      const unsigned long long *__restrict__ part_off,
+                                      const unsigned long long *__restrict__ part_mask, HashPair hp,
+                                      const int64_t *__restrict__ items_a,
+                                      const int64_t *__restrict__ items_b, uint32_t R,
+                                      int upper_only, TopkCand *out, unsigned int *count) {
+    const uint64_t total = (uint64_t)R * R;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = (uint32_t)items_a[x / R], j = (uint32_t)items_b[x % R];
+        if (upper_only && !(i < j)) continue;
+        const uint32_t p = partition_hash(hp, i, j);
+        const unsigned long long mask = part_mask[p];
+        if (mask == ~0ull) continue;   // outside the plan's interval
+        const unsigned long long key = make_key(i, j);
+        const Slot *base = slots + part_off[p];
+        unsigned long long h = slot_mix(key) & mask & ~3ull;
+        unsigned int c = 0;
+        for (unsigned long long probe = 0; probe <= mask; ++probe) {
+            const Slot sl = base[h];
+            if (sl.key == key) {
+                c = (unsigned int)sl.val;
+                break;
+            }
+            if (sl.key == kEmptyKey) break;
+            h = (h + 1) & mask;
+        }
+        if (!c) continue;
+        TopkCand cand;
+        cand.wkey = c;
+        cand.ij = key;
+        cand.w = (double)c;
+        cand.wl = (double)c;
+        out[atomicAdd(count, 1u)] = cand;
+    }
+}
+
+cudaError_t launch_topk_hot_candidates(const Slot *slots, const unsigned long long *part_off,
+                                       const unsigned long long *part_mask, const HashPair &hp,
+                                       const int64_t *items_a, const int64_t *items_b, uint32_t R,
+                                       int upper_only, TopkCand *out, unsigned int *count,
+                                       cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess || R == 0) return e;
+    const uint64_t total = (uint64_t)R * R;
+    const int grid = (int)std::min<uint64_t>((total + 255) / 256, 8192);
+    k_topk_hot_candidates<<<grid, 256, 0, s>>>(slots, part_off, part_mask, hp, items_a, items_b, R,
+                                               upper_only, out, count);
     return cudaGetLastError();
 }
 
