@@ -131,7 +131,14 @@ typedef struct {
 
 typedef struct {
     int32_t n_rows, n_cols;       /* C is n_rows x n_cols */
-    uint32_t P;                   /* partitions (power of two, >= 1) */
+    uint32_t P;                   /* partitions (power of two, >= 1), or 0:
+                                     chosen, with groups, tile_vectors,
+                                     smem_slots, the variant flags and the
+                                     dense tiers, by crp_autotune on the first
+                                     min(K, 2^21) outer products of the first
+                                     crp_outer_accumulate (which then
+                                     synchronises); exact plans over all
+                                     partitions only */
     uint32_t _pad0;
     uint64_t seed_a, seed_b;      /* hash seeds of h_a and h_b */
     int32_t value_type;           /* CRP_I32 | CRP_F32_COMP */

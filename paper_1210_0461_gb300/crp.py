@@ -268,6 +268,10 @@ class Plan:
         a, b = A.c_struct(), B.c_struct()
         _check(self._lib.crp_outer_accumulate(self._h, ctypes.byref(a), ctypes.byref(b)),
                "crp_outer_accumulate")
+        if self.P == 0 and A.n_major > 0:   # tuned by the first call: learn its P
+            s = crp_stats_t()
+            _check(self._lib.crp_stats(self._h, ctypes.byref(s), None), "crp_stats")
+            self.P = int(s.P)
 
     def sync(self):
         _check(self._lib.crp_sync(self._h), "crp_sync")

@@ -154,6 +154,9 @@ struct crp_plan {
     // chunk counter, count[B], fill[B], start[B + 1], overflow counter
     unsigned int *d_route_ctl = nullptr;
     uint32_t ov_chunks = 0;             // overflow chunks at the start of the pool
+    // P = 0 in the descriptor: a placeholder until the first call tunes the plan
+    bool tune_first = false;
+    crp_plan_desc user_desc = {};
     // certified top-k: cumulative degrees of rows and columns since the last
     // reset, the hot pairs' candidate buffer, calls answered from it
     unsigned long long *d_deg_a = nullptr, *d_deg_b = nullptr;
@@ -271,6 +274,22 @@ extern "C" crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc,
     *out = nullptr;
     const crp_plan_desc &d = *desc;
     if (d.n_rows <= 0 || d.n_cols <= 0) return fail(CRP_EINVAL, "n_rows and n_cols must be > 0");
+    if (d.P == 0) {   // tuned at the first call: a valid single-partition placeholder until then
+        if (d.summary_counters || d.part_begin || d.part_end)
+            return fail(CRP_EINVAL, "P = 0 (tuned at the first call) is for exact plans over all "
+                                    "partitions");
+        crp_plan_desc ph = d;
+        ph.P = 1;
+        ph.groups = 0;
+        ph.hot_items = ph.warm_items = 0;
+        ph.table_capacity_hint = 0;
+        ph.flags &= ~(uint32_t)CRP_PLAN_ROUTED;
+        crp_status st = crp_plan_create(out, &ph, stream);
+        if (st != CRP_OK) return st;
+        (*out)->tune_first = true;
+        (*out)->user_desc = d;
+        return CRP_OK;
+    }
     if (!is_pow2(d.P) || d.P > (1u << 24))
         return fail(CRP_EINVAL, "P must be a power of two in [1, 2^24]");
     if (d.value_type != CRP_I32 && d.value_type != CRP_F32_COMP)
@@ -1009,6 +1028,19 @@ extern "C" crp_status crp_outer_accumulate(crp_plan *pl, const crp_sparse *A, co
         return fail(CRP_EINVAL, "CRP_I32 counts {0,1} inputs: val must be NULL");
     if (A->n_major == 0) return CRP_OK;
     CRP_CUDA(cudaSetDevice(pl->device));
+    if (pl->tune_first) {
+        // P = 0: tune on this call's first outer products, then become that plan
+        crp_plan_desc best;
+        const int64_t sample = std::min<int64_t>(A->n_major, (int64_t)1 << 21);
+        crp_status ts = crp_autotune(&pl->user_desc, A, B, sample, nullptr, &best, nullptr,
+                                     (void *)pl->stream);
+        if (ts != CRP_OK) return ts;
+        crp_plan *fresh = nullptr;
+        ts = crp_plan_create(&fresh, &best, (void *)pl->stream);
+        if (ts != CRP_OK) return ts;
+        std::swap(*pl, *fresh);
+        crp_plan_destroy(fresh);   // the placeholder's buffers
+    }
     if (pl->d.flags & CRP_PLAN_DEBUG_CHECKS) {
         unsigned int *bad = (unsigned int *)(pl->d_scratch64 + 2 * pl->d.P + 8);
         CRP_CUDA(cudaMemsetAsync(bad, 0, 4, pl->stream));
