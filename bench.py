@@ -159,7 +159,8 @@ def workload(args):
 
 def cpu_baseline(T, budget_s: float):
     """The oracle, as it stands, on a bounded prefix of the workload's
-    transactions (grown until it takes about ``budget_s`` seconds)."""
+    transactions (doubled until one pass takes at least 2/3 of ``budget_s``
+    seconds: 10-20 s of CPU work for the default budget)."""
     from oracle import crp_oracle as O
     import numpy as np
     m = 2000
@@ -168,7 +169,7 @@ def cpu_baseline(T, budget_s: float):
         t0 = time.perf_counter()
         prod = O.exact_product(sub, sub, O.FULL)
         dt = time.perf_counter() - t0
-        if dt >= budget_s / 4 or m * 2 > T.n_major:
+        if dt >= budget_s * 2 / 3 or m * 2 > T.n_major:
             break
         m *= 2
     return {"value": prod.terms / dt, "unit": "terms/s", "cores": 1, "kind": "oracle",
