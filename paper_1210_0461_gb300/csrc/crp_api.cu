@@ -160,6 +160,7 @@ struct crp_plan {
     // certified top-k: cumulative degrees of rows and columns since the last
     // reset, the hot pairs' candidate buffer, calls answered from it
     unsigned long long *d_deg_a = nullptr, *d_deg_b = nullptr;
+    bool deg_b_mirrors_a = true;   // every call since the reset had B == A: d_deg_b unused
     TopkCand *d_hot_cand = nullptr;
     uint64_t topk_certified = 0;
     // locked-bucket summaries: a lock word per partition
@@ -453,6 +454,7 @@ extern "C" crp_status crp_reset(crp_plan *pl) {
         CRP_CUDA(cudaMemsetAsync(pl->d_deg_a, 0, (size_t)pl->d.n_rows * 8, pl->stream));
         CRP_CUDA(cudaMemsetAsync(pl->d_deg_b, 0, (size_t)pl->d.n_cols * 8, pl->stream));
     }
+    pl->deg_b_mirrors_a = true;
     if (pl->summary) {
         CRP_CUDA(cudaMemsetAsync(pl->d_live, 0, pl->d.P * 4, pl->stream));
         CRP_CUDA(cudaMemsetAsync(pl->d_floor, 0, pl->d.P * 4, pl->stream));
@@ -965,11 +967,23 @@ static crp_status select_hot_items(crp_plan *pl, const crp_sparse *A, const crp_
                 CRP_CUDA(cudaMemsetAsync(pl->d_deg_a, 0, (size_t)pl->d.n_rows * 8, s));
                 CRP_CUDA(cudaMemsetAsync(pl->d_deg_b, 0, (size_t)pl->d.n_cols * 8, s));
             }
+            // (B the same arrays as A, as for T^T T: one count serves both sides
+            // for as long as every call since the reset is like that)
+            const bool same = A->idx == B->idx && A->nnz == B->nnz &&
+                              pl->d.n_rows == pl->d.n_cols;
+            if (!same && pl->deg_b_mirrors_a) {
+                CRP_CUDA(cudaMemcpyAsync(pl->d_deg_b, pl->d_deg_a, (size_t)pl->d.n_cols * 8,
+                                         cudaMemcpyDeviceToDevice, s));
+                pl->deg_b_mirrors_a = false;
+            }
             CRP_CUDA(launch_degrees(A->idx, A->nnz, pl->d.n_rows, pl->d_rank_a, pl->hot_R,
                                     pl->d_items_a, pl->d_deg_a, pl->sm_count, s));
-            CRP_CUDA(launch_degrees(B->idx, B->nnz, pl->d.n_cols, pl->d_rank_b, pl->hot_R,
-                                    pl->d_items_b, pl->d_deg_b, pl->sm_count, s));
-            pl->launches += 2;
+            pl->launches += 1;
+            if (!pl->deg_b_mirrors_a) {
+                CRP_CUDA(launch_degrees(B->idx, B->nnz, pl->d.n_cols, pl->d_rank_b, pl->hot_R,
+                                        pl->d_items_b, pl->d_deg_b, pl->sm_count, s));
+                pl->launches += 1;
+            }
         }
     }
     if (pl->warm_W) {
@@ -1317,7 +1331,8 @@ static crp_status topk_certified(crp_plan *pl, int32_t k, int upper, int32_t *i_
     CRP_CUDA(launch_topk_hot_candidates(pl->slots, pl->d_off, pl->d_mask, pl->hp, pl->d_items_a,
                                         pl->d_items_b, R, upper, pl->d_hot_cand, count, s));
     CRP_CUDA(launch_max_outside(pl->d_deg_a, pl->d.n_rows, pl->d_rank_a, R, bound, s));
-    CRP_CUDA(launch_max_outside(pl->d_deg_b, pl->d.n_cols, pl->d_rank_b, R, bound, s));
+    CRP_CUDA(launch_max_outside(pl->deg_b_mirrors_a ? pl->d_deg_a : pl->d_deg_b, pl->d.n_cols,
+                                pl->d_rank_b, R, bound, s));
     pl->launches += 3;
     unsigned int n_c = 0;
     unsigned long long S = 0;

@@ -133,3 +133,27 @@ def test_partition_interval_plan(crp):
     for k, up in ((1, True), (100, True), (1000, False)):
         _check(plan, sub, k, up)
     plan.close()
+
+
+def test_separate_a_and_b_arrays_and_a_mix_of_calls(crp):
+    # B given as other arrays than A (its degrees counted on their own), and
+    # a first call with B == A followed by one with separate arrays
+    T1 = ci.C1.scaled(m=9000).generate()
+    T2 = ci.transactions(ci.C1.seed + 5, 9000, 1000, 10.0, 2, 40, 1.1)
+    both = ci.Sparse(np.concatenate([T1.ptr, T2.ptr[1:] + T1.ptr[-1]]),
+                     np.concatenate([T1.idx, T2.idx]), None, 1000)
+    for calls in (((T2, False),), ((T1, True), (T2, False))):
+        plan = crp.Plan(1000, 1000, 64, ci.SEED_A, ci.SEED_B, flags=8 | 2, hot_items=100)
+        for T, same in calls:
+            a = crp.to_device(T)
+            b = a if same else crp.to_device(T)
+            plan.accumulate(a, b)
+        plan.sync()
+        src = T2 if len(calls) == 1 else both
+        Sc = O.Compressed.of(src)
+        ref = O.exact_product(Sc, Sc, O.FULL)
+        before = plan.topk_certified_calls()
+        for k, up in ((1, True), (10, True), (500, False)):
+            _check(plan, ref, k, up)
+        assert plan.topk_certified_calls() > before
+        plan.close()
