@@ -703,11 +703,18 @@ def main():
         dd = crp.DeviceSparse(dptr, didx, None, T.n_minor)
         ti = np.zeros(args.topk, np.int32)
 
+        copy_stream = torch.cuda.Stream(device=f"cuda:{local}")
+
         def e2e_step():
-            with torch.cuda.stream(stream):
+            # the host-to-device copy of the step's input runs on its own stream,
+            # beside the table reset; the accumulate waits for it
+            with torch.cuda.stream(copy_stream):
                 dptr.copy_(hp, non_blocking=True)
                 didx.copy_(hi, non_blocking=True)
+                copied = torch.cuda.Event()
+                copied.record(copy_stream)
             plan.reset()
+            stream.wait_event(copied)
             plan.accumulate(dd, dd)
             plan.sync()
             top = plan.topk(args.topk, upper=True)   # host outputs: D2H inside
