@@ -5,7 +5,9 @@ disjoint interval of the hash table and a full copy of the input, need no
 communication while they accumulate; every entry is produced by exactly one
 instance.  The heaviest entries of the whole product are then the heaviest of
 the union of every instance's own heaviest entries, which is the only exchange
-(a gather of k candidates per rank).
+(a gather of k candidates per rank).  The per-partition Count-Sketch of an
+interval plan holds estimators for its own partitions only (zero elsewhere),
+so the whole sketch is the sum of the ranks' sketches.
 """
 from __future__ import annotations
 
@@ -40,3 +42,14 @@ def gather_topk(local, k: int, group=None):
     if dist.get_rank(group) != 0:
         return None
     return merge_topk([tuple(np.asarray(x) for x in o) for o in out], k)
+
+
+def gather_sketch(local, group=None):
+    """All ranks pass the P estimators of their interval plan's Count-Sketch
+    (numpy int64 or float64, zero outside the interval); every rank gets the
+    sketch of the whole product, their sum.  Uses torch.distributed."""
+    import torch
+    import torch.distributed as dist
+    t = torch.from_numpy(np.ascontiguousarray(local)).clone()
+    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return t.numpy()

@@ -71,3 +71,41 @@ def test_merge_topk_ties_and_order():
     b = (np.array([0, 3]), np.array([1, 4]), np.array([7., 9.]))
     i, j, w = merge_topk([a, b], 3)
     assert list(zip(i, j, w)) == [(3, 4, 9.), (0, 1, 7.), (0, 5, 7.)]
+
+
+
+def _sketch_worker(rank, world, port, P, out):
+    import torch.distributed as dist
+    from paper_1210_0461_gb300.sharding import gather_sketch
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    T = O.Compressed.of(ci.C1.scaled(m=4000).generate())
+    full = O.exact_product(T, T, O.FULL)
+    q, r = partition_interval(rank, world, P)
+    local = O.count_sketch(full, P, ci.SEED_A, ci.SEED_B).astype(np.int64)
+    local[:q] = 0
+    local[r:] = 0                                   # this rank's interval plan
+    merged = gather_sketch(local)
+    out.put((rank, merged.tolist()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gathered_sketch_equals_the_whole_sketch_two_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    P, world = 64, 2
+    port = _free_port()
+    procs = [ctx.Process(target=_sketch_worker, args=(r, world, port, P, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    got = dict(q.get(timeout=120) for _ in range(world))
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    T = O.Compressed.of(ci.C1.scaled(m=4000).generate())
+    want = O.count_sketch(O.exact_product(T, T, O.FULL), P, ci.SEED_A, ci.SEED_B)
+    for r in range(world):
+        assert np.array_equal(np.array(got[r]), want)
