@@ -157,7 +157,7 @@ def workload(args):
     return w
 
 
-def cpu_baseline(T, budget_s: float):
+def cpu_baseline(T, budget_s: float, mode: int = 0):
     """The oracle, as it stands, on a bounded prefix of the workload's
     transactions (doubled until one pass takes at least 2/3 of ``budget_s``
     seconds: 10-20 s of CPU work for the default budget)."""
@@ -167,7 +167,7 @@ def cpu_baseline(T, budget_s: float):
     while True:
         sub = O.Compressed(T.ptr[:m + 1], T.idx[:T.ptr[m]], None, T.n_minor)
         t0 = time.perf_counter()
-        prod = O.exact_product(sub, sub, O.FULL)
+        prod = O.exact_product(sub, sub, mode)
         dt = time.perf_counter() - t0
         if dt >= budget_s * 2 / 3 or m * 2 > T.n_major:
             break
@@ -412,8 +412,9 @@ def run_c4(args, np, torch, crp, ci, stream):
         else:
             plan.close()
     regime = c4_paper_regime(args, np, torch, crp, ci, stream, d, n, terms, ri, rj, rw, top_sum,
-                             true_weight) if args.paper_regime else None
+                             true_weight, T) if args.paper_regime else None
     best = results["predictor"]
+    cpu = None if args.no_cpu else cpu_baseline(T, args.cpu_seconds, mode=1)
     _line(best["terms_per_s"], best["seconds"] * 1e3, args, "u32 counters",
           {"workload": f"c4: {w4.m} transactions x {w4.n} items, Poisson(15), Zipf(1.2); "
                        "pairs i < j; 2^20 counters per partition, P = 256, 2^16 reserved "
@@ -421,7 +422,8 @@ def run_c4(args, np, torch, crp, ci, stream):
            "terms_per_step": terms, "exact_reference_ms": exact_ms,
            "training": {"samples": int(len(y)), "steps": 300, "first_loss": losses[0],
                         "last_loss": losses[-1], "seconds": train_s},
-           "variants": results, "paper_regime": regime})
+           "variants": results, "paper_regime": regime},
+          {"cpu_baseline": cpu})
     ex.close()
 
 
@@ -436,8 +438,33 @@ def _bound_metrics(np, tw, tl):
     return ratio, until
 
 
+def regime_cpu_baseline(T, budget_s: float):
+    """The oracle, as it stands, on a prefix of the workload: one Space-Saving
+    summary of 2 counters per bucket over 2^20 buckets, the canonical stream
+    order (pairs i < j), and beside it the exact product and its per-bucket
+    Count-Sketch; the prefix doubles until one pass takes 2/3 of budget_s."""
+    from oracle import crp_oracle as O
+    import crp_inputs as ci
+    m = 1000
+    while True:
+        sub = O.Compressed(T.ptr[:m + 1], T.idx[:T.ptr[m]], None, T.n_minor)
+        t0 = time.perf_counter()
+        O.bucket_summaries(sub, sub, 1 << 20, 2, ci.SEED_A, ci.SEED_B, O.UPPER)
+        t1 = time.perf_counter()
+        prod = O.exact_product(sub, sub, O.UPPER)
+        O.count_sketch(prod, 1 << 20, ci.SEED_A, ci.SEED_B)
+        t2 = time.perf_counter()
+        if t2 - t0 >= budget_s * 2 / 3 or m * 2 > T.n_major:
+            break
+        m *= 2
+    return {"value": prod.terms / (t1 - t0), "unit": "terms/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {m} transactions ({prod.terms} pairs i < j): bucket summaries "
+                      f"{t1 - t0:.2f} s; exact product + Count-Sketch {t2 - t1:.2f} s "
+                      f"({prod.terms / (t2 - t1):.3g} terms/s), single-threaded numpy"}
+
+
 def c4_paper_regime(args, np, torch, crp, ci, stream, d, n, terms, ri, rj, rw, top_sum,
-                    true_weight):
+                    true_weight, T):
     """The paper's own summary regime (Section 6): many buckets (partitions)
     of two Space-Saving counters each, locked buckets updated in arrival
     order, with the Count-Sketch beside them.  Timed passes of P = 2^20,
@@ -512,6 +539,8 @@ def c4_paper_regime(args, np, torch, crp, ci, stream, d, n, terms, ri, rj, rw, t
         if len(reports.get(k, [])) >= (t + 1) // 2:
             got_ss[q] = np.median(reports[k])
             got_cs[q] = cs_med[q]
+    if not args.no_cpu:
+        out["cpu_baseline"] = regime_cpu_baseline(T, args.cpu_seconds)
     out["majority_11"] = {
         "top_k_per_instance": K,
         "exact_top1000_reported": float(np.mean(got_ss > 0)),

@@ -21,7 +21,8 @@ Sections of the paper each function follows:
   :func:`interval_terms` (tests every pair; it does not use the two-pointer
   scan, so that scan is checked against the definition).
 * Preliminaries, Space-Saving, with weighted positive updates
-  -> :func:`space_saving`.
+  -> :func:`space_saving`; one summary per bucket (Figure 1, Section 6's
+  many-bucket regime) -> :func:`partition_streams`, :func:`bucket_summaries`.
 * Preliminaries, Count-Sketch, and Figure 1 (``CS[h(e)] += e s(e)``); the
   median of t instances
   -> :func:`side_sign`, :func:`sign_of`, :func:`count_sketch_terms`,
@@ -493,6 +494,35 @@ def partition_streams(A: Compressed, B: Compressed, P: int, seed_a: int, seed_b:
         m = p == q
         out.append(list(zip((i[m] * n_cols + j[m]).tolist(), w[m].tolist())))
     return out
+
+
+def bucket_summaries(A: Compressed, B: Compressed, P: int, ell: int, seed_a: int, seed_b: int,
+                     mode: int = FULL):
+    """Figure 1 with one Space-Saving summary of ``ell`` counters per bucket
+    (the paper's regime of many buckets): every partition's stream, in stream
+    order, through :func:`space_saving`.  The streams are grouped with one
+    stable sort by partition rather than one scan per partition, so many
+    buckets stay affordable.  Returns (p, key, count, overestimation) arrays
+    over every recorded key, key = i * n_cols + j."""
+    ks, i, j, w = outer_product_terms(A, B, 0, A.n_major, mode)
+    order = np.lexsort((j, i, ks))
+    i, j, w = i[order], j[order], w[order]
+    p = partition_of(i, j, P, seed_a, seed_b)
+    grp = np.argsort(p, kind="stable")
+    p, key, w = p[grp], (i * B.n_minor + j)[grp], w[grp]
+    cuts = np.flatnonzero(np.diff(p)) + 1
+    P_out, K_out, C_out, O_out = [], [], [], []
+    for lo, hi in zip(np.concatenate([[0], cuts]), np.concatenate([cuts, [len(p)]])):
+        if lo == hi:
+            continue
+        summ = space_saving(zip(key[lo:hi].tolist(), w[lo:hi].tolist()), ell)
+        for k, (c, o) in summ.items():
+            P_out.append(int(p[lo]))
+            K_out.append(k)
+            C_out.append(c)
+            O_out.append(o)
+    return (np.array(P_out, np.int64), np.array(K_out, np.int64), np.array(C_out, np.float64),
+            np.array(O_out, np.float64))
 
 
 # ---------------------------------------------------------------------------
