@@ -293,7 +293,9 @@ __device__ __forceinline__ void locked_update_warp(const TableView &tv, bool has
                 __syncwarp();   // each member sees the previous member's counters
             }
             if (served) {
-                __threadfence();   // every member's counters before the hand-on
+                // a group of one: its release orders its own counter writes; a
+                // larger group's members wrote too, so fence before the hand-on
+                if (size > 1) __threadfence();
                 red_release_add_u32(serving, 1u);
             }
             pending &= ~srv;
