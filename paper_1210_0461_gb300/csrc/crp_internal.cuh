@@ -200,7 +200,7 @@ cudaError_t launch_sketch_estimate(const SketchSet &S, const int32_t *i, const i
 constexpr uint32_t kSketchSmemMaxP = 4096;
 
 // Two-phase (routed) accumulation: bins of records per partition group.
-constexpr uint32_t kChunkRecs = 256;   // records per chunk of the routed pool
+constexpr uint32_t kChunkRecs = 512;   // records per chunk of the routed pool
 struct RouteArgs {
     AccumulateArgs acc;        // enumeration inputs, hash and table view
     void *pool;                // n_chunks chunks of kChunkRecs records: u64 keys (int)

@@ -455,21 +455,23 @@ k_apply(RouteArgs RA) {
         if (item >= total) break;
         const R *chunk = pool + (size_t)RA.order[item] * kChunkRecs;
         if constexpr (VT == CRP_I32) {
-            // lane takes 8 consecutive records in two 32-byte loads that skip L1
-            // and leave L2 first (records are read once)
-            unsigned long long r[8];
-            const unsigned long long *src = chunk + lane * 8;
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
+            // lane takes kChunkRecs / 32 consecutive records, four at a time, in
+            // 32-byte loads that skip L1 and leave L2 first (records are read once)
+            constexpr int kPer = kChunkRecs / 32;
+            const unsigned long long *src = chunk + lane * kPer;
+#pragma unroll 1
+            for (int h = 0; h < kPer / 4; ++h) {
+                unsigned long long r[4];
                 asm volatile(
                     "ld.global.L1::no_allocate.L2::evict_first.v4.u64 {%0, %1, %2, %3}, [%4];"
-                    : "=l"(r[4 * h]), "=l"(r[4 * h + 1]), "=l"(r[4 * h + 2]), "=l"(r[4 * h + 3])
+                    : "=l"(r[0]), "=l"(r[1]), "=l"(r[2]), "=l"(r[3])
                     : "l"(src + 4 * h));
 #pragma unroll
-            for (int x = 0; x < 8; ++x) {
-                if (r[x] == kEmptyKey) continue;
-                apply_record(RA, r[x]);
-                ++applied;
+                for (int x = 0; x < 4; ++x) {
+                    if (r[x] == kEmptyKey) continue;
+                    apply_record(RA, r[x]);
+                    ++applied;
+                }
             }
         } else {
 #pragma unroll 2
