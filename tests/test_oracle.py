@@ -165,6 +165,27 @@ def test_cooccurrence_closed_forms():
     assert ud == {k: v for k, v in fd.items() if k[0] < k[1]}
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_entries_are_bounded_by_row_and_column_degrees(seed):
+    # for {0,1} inputs C(i,j) = #{k : i in a_k and j in b_k} <= min(deg_A(i),
+    # deg_B(j)), with equality when one item always occurs with the other: the
+    # bound the top-k uses to answer from the pairs of frequent items
+    rng = np.random.default_rng(seed)
+    A = _rand_sparse(rng, 300, 40, 0.15, values=False)
+    B = _rand_sparse(rng, 300, 50, 0.15, values=False)
+    prod = O.exact_product(A, B, O.FULL)
+    deg_a = np.bincount(A.idx, minlength=A.n_minor)
+    deg_b = np.bincount(B.idx, minlength=B.n_minor)
+    assert (prod.w <= np.minimum(deg_a[prod.i], deg_b[prod.j])).all()
+    # tight case: every vector of B holds item 0, so C(i, 0) = deg_A(i)
+    rows = [np.union1d([0], B.idx[B.ptr[k]:B.ptr[k + 1]]) for k in range(B.n_major)]
+    B0 = O.Compressed(np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64),
+                      np.concatenate(rows).astype(np.int32), None, B.n_minor)
+    p0 = O.exact_product(A, B0, O.FULL)
+    col0 = p0.j == 0
+    assert np.array_equal(p0.w[col0], deg_a[p0.i[col0]].astype(float))
+
+
 def test_entry_definition_matches_product():
     T = _tx(9, 2000, 150, 6.0, 1, 20, 1.0)
     full = O.exact_product(T, T, O.FULL)
