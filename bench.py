@@ -622,6 +622,7 @@ def main():
     torch.cuda.set_device(local)
     pkg.build()
     from paper_1210_0461_gb300 import crp
+    from paper_1210_0461_gb300.sharding import job_rate
 
     w = workload(args)
     t0 = time.time()
@@ -705,12 +706,9 @@ def main():
     clk = clocks.stop()
     launches = plan.timing()[1] - launches0
     st = plan.stats(per_partition=False)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
-    value = terms_step * world / (ms_step / 1e3)
+    # the ranks split one product (each enumerates its own partition
+    # interval): the job's terms are terms_step, over the slowest rank's time
+    value, ms_step = job_rate(terms_step, ms_total / args.steps)
 
     # ---- roofline of the dominant kernel (k_accumulate) ----
     hbm, peak_src = peaks()
@@ -757,8 +755,8 @@ def main():
         for _ in range(args.steps):
             e2e_step()
         torch.cuda.synchronize()
-        e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-        e2e = {"value": terms_step * world / (e_ms / 1e3), "unit": "terms/s",
+        e_rate, e_ms = job_rate(terms_step, (time.perf_counter() - t0) * 1e3 / args.steps)
+        e2e = {"value": e_rate, "unit": "terms/s",
                "h2d_bytes_per_step": int(hp.numel() * 8 + hi.numel() * 4),
                "d2h_bytes_per_step": int(args.topk * (4 + 4 + 8 + 8)), "ms_per_step": e_ms}
 

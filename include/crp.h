@@ -350,15 +350,21 @@ crp_status crp_probe_update_rate(uint64_t region_bytes, uint64_t n_updates, int 
  *   A, B: device inputs as for crp_outer_accumulate.
  *   i_out, j_out, w_out: device arrays of `capacity` entries (caller-owned);
  *     the entries are written unordered.  *n_out (host) = number of nonzero
- *     entries, also when it exceeds capacity (then CRP_EINVAL).
- *   stream: a cudaStream_t; the call synchronises it.
+ *     entries, also when it exceeds capacity (then CRP_EINVAL and nothing
+ *     beyond capacity is written).
+ *   stream: a cudaStream_t; the call synchronises it before returning.
  * Errors: CRP_EINVAL for P > 1024 or not a power of two, mismatched shapes or
  * a too small output; CRP_ETABLE_FULL when a partition of the static table
- * overflows (the product has too many entries for this entry point).
- * The first call on a device looks up the static array's address with
- * cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture.  Every call clears and reuses the same array,
- * so calls whose work overlaps on the GPU race: serialise them. */
+ * overflows (the product has too many entries for this entry point; the
+ * updates that met the full partition are lost, so *n_out is set to 0 and
+ * the output arrays hold no usable result).
+ * The first call in a CUDA context (per device: the primary context, or one
+ * the caller made current) looks up the static array's device address with
+ * cudaGetSymbolAddress, that device current, and keeps it for that context;
+ * make that first call before any stream capture.  A call in another context
+ * (after cudaDeviceReset, say) looks the address up again.  Every call
+ * clears and reuses the same array, so calls whose work overlaps on the GPU
+ * race: serialise them. */
 crp_status crp_outer_product_noalloc(const crp_plan_desc *desc, const crp_sparse *A,
                                      const crp_sparse *B, int32_t *i_out, int32_t *j_out,
                                      double *w_out, int64_t capacity, int64_t *n_out,

@@ -31,6 +31,10 @@ Sections of the paper each function follows:
 * Section 6 (case study): support of a pair = number of transactions holding
   it, i.e. the entries above the diagonal of ``T^T T``; heaviest entries
   -> :func:`topk`.
+* Not in the paper: the heavy-pair predictor (a 2 -> 64 -> 64 -> 1 network
+  on the marginal counts of a prefix) -> :func:`mlp_forward`,
+  :func:`mlp_loss_grad`, :func:`adam_step`, :func:`prefix_item_counts`,
+  :func:`top_items`, :func:`candidate_pairs`, :func:`marginal_features`.
 
 Readings where the paper is silent:
 
@@ -581,7 +585,9 @@ def mlp_loss_grad(theta, X, t, rounding: bool = True, n_total: int | None = None
     """Mean squared error L = sum((y - t)^2) / n_total and its gradient with
     respect to the master parameters (straight through the bf16 copies).  With
     ``rounding`` the backward products use bf16 operands (dZ2, dZ1, the
-    saved activations) like the kernels do."""
+    saved activations) like the kernels do; the bias gradients of the hidden
+    layers are the sums over the batch of those same bf16 dZ2 and dZ1 (the
+    kernels form them as products with a row of ones)."""
     y, c = mlp_forward(theta, X, rounding)
     rd = bf16_round if rounding else (lambda a: np.asarray(a, np.float64))
     n = len(y) if n_total is None else n_total
@@ -592,13 +598,13 @@ def mlp_loss_grad(theta, X, t, rounding: bool = True, n_total: int | None = None
     dw3 = c["H2"].T @ dy
     db3 = np.array([dy.sum()])
     dZ2 = np.outer(dy, p["w3"]) * (c["Z2"] > 0)
-    db2 = dZ2.sum(axis=0)
     dZ2b = rd(dZ2)
+    db2 = dZ2b.sum(axis=0)
     dW2 = dZ2b.T @ c["H1b"]
     dH1 = dZ2b @ c["W2b"]
     dZ1 = dH1 * (c["Z1"] > 0)
-    db1 = dZ1.sum(axis=0)
     dZ1b = rd(dZ1)
+    db1 = dZ1b.sum(axis=0)
     dW1 = dZ1b.T @ c["Xb"]
     g = mlp_pack(dict(W1=dW1, b1=db1, W2=dW2, b2=db2, w3=dw3, b3=db3))
     return L, g, y
@@ -626,3 +632,29 @@ def marginal_features(counts_i, counts_j, scale):
     """Predictor inputs of a pair: log(1 + c_i) / scale, log(1 + c_j) / scale,
     the items' counts in a prefix of the stream."""
     return np.stack([np.log1p(counts_i) / scale, np.log1p(counts_j) / scale], axis=1)
+
+
+def prefix_item_counts(prefix: Compressed) -> np.ndarray:
+    """c_x: how many vectors (transactions) of the prefix hold item x."""
+    return np.bincount(prefix.idx.astype(np.int64), minlength=prefix.n_minor).astype(np.int64)
+
+
+def top_items(counts: np.ndarray, R: int) -> np.ndarray:
+    """The R items of largest count, by count descending, ties by the smaller
+    item id (a reading: which of several items tied at the R-th count is
+    taken is not fixed by anything)."""
+    order = np.lexsort((np.arange(len(counts)), -np.asarray(counts)))
+    return order[:R]
+
+
+def candidate_pairs(prefix: Compressed, R: int):
+    """Candidate heavy pairs from a prefix of the stream: every pair i < j of
+    the R items of largest prefix count, sorted by (i, j), with features
+    (log(1 + c_i), log(1 + c_j)) / log(1 + max c).  Returns (i, j, X, c)."""
+    c = prefix_item_counts(prefix)
+    items = np.sort(top_items(c, R))
+    a, b = np.triu_indices(len(items), k=1)
+    i, j = items[a], items[b]
+    scale = np.log1p(c.max()) if len(c) else 0.0
+    X = marginal_features(c[i], c[j], scale) if scale > 0 else np.zeros((len(i), 2))
+    return i, j, X, c

@@ -494,6 +494,12 @@ def mlp_init(seed: int, device="cuda"):
     return torch.tensor(np.concatenate(parts), dtype=torch.float32, device=device)
 
 
+def mlp_adam(params, m, v, grad, lr: float, step: int):
+    """One Adam step on device tensors (params, m, v updated in place)."""
+    _check(lib().crp_mlp_adam(params.data_ptr(), m.data_ptr(), v.data_ptr(), grad.data_ptr(),
+                              lr, step, _stream_handle(None)), "crp_mlp_adam")
+
+
 class MLPTrainer:
     """Adam on the fp32 master parameters with the tensor-core gradient kernel."""
 
@@ -508,9 +514,7 @@ class MLPTrainer:
     def step(self, x, t):
         loss, g = mlp_grad(self.params, x, t)
         self.step_n += 1
-        _check(lib().crp_mlp_adam(self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(),
-                                  g.data_ptr(), self.lr, self.step_n, _stream_handle(None)),
-               "crp_mlp_adam")
+        mlp_adam(self.params, self.m, self.v, g, self.lr, self.step_n)
         return loss
 
 

@@ -62,20 +62,63 @@ __global__ void k_noalloc_emit(NoallocScratch *sc, uint64_t n_slots, int value_t
     }
 }
 
-// Device address of the static scratch, looked up once per device (with that
-// device current) by cudaGetSymbolAddress.
-static NoallocScratch *g_scratch_addr[kNoallocMaxDevices];
+// Device address of the static scratch.  A __device__ variable lives in the
+// module loaded into one CUDA context, so its address is looked up (with
+// cudaGetSymbolAddress, the device current) once per device and context: the
+// cache holds the unique id of the context the address belongs to, and a
+// call made in another context (after cudaDeviceReset, or in a context the
+// caller created with the driver API) looks the address up again.
+struct ScratchAddr {
+    unsigned long long ctx_id;
+    NoallocScratch *addr;
+};
+static ScratchAddr g_scratch_addr[kNoallocMaxDevices];
 static std::mutex g_scratch_mu;
+
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+// Unique id of the calling thread's current context (driver API, reached
+// through the runtime's entry-point query so the library needs no -lcuda).
+static cudaError_t current_context_id(unsigned long long *id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f0 = nullptr, *f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000,
+                                                         cudaEnableDefault, &q0);
+        if (e == cudaSuccess)
+            e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1);
+        if (e != cudaSuccess) return e;
+        if (q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+            return cudaErrorSymbolNotFound;
+        get_current = (CtxGetCurrentFn)f0;
+        get_id = (CtxGetIdFn)f1;
+    }
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return cudaErrorInvalidResourceHandle;
+    if (get_id(ctx, id) != 0) return cudaErrorInvalidResourceHandle;
+    return cudaSuccess;
+}
 
 static cudaError_t scratch_address(int dev, NoallocScratch **out) {
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    ScratchAddr &c = g_scratch_addr[dev];
+    unsigned long long id = 0;
+    // no current context yet (a first call before any other CUDA work), or
+    // another context than the cached address belongs to: look it up; the
+    // lookup also makes the device's primary context current
+    if (current_context_id(&id) != cudaSuccess || !c.addr || c.ctx_id != id) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = (NoallocScratch *)p;
+        e = current_context_id(&id);
+        if (e != cudaSuccess) return e;
+        c.addr = (NoallocScratch *)p;
+        c.ctx_id = id;
     }
-    *out = g_scratch_addr[dev];
+    *out = c.addr;
     return cudaSuccess;
 }
 
@@ -195,12 +238,14 @@ extern "C" crp_status crp_outer_product_noalloc(const crp_plan_desc *desc, const
     NA_CUDA(cudaMemcpyAsync(&status, &sc->dc.status, sizeof status, cudaMemcpyDeviceToHost, s));
     NA_CUDA(cudaStreamSynchronize(s));
 #undef NA_CUDA
-    *n_out = (int64_t)count;
     if (status & (kStatusTableFull | kStatusSpillFull))
+        // updates that met a full partition were dropped, so the cursor
+        // undercounts the product's entries: report no count at all
         return noalloc_fail(CRP_ETABLE_FULL,
                             "the product has more entries than a partition of the static table "
                             "holds (2^20 slots over P partitions)");
     if (status) return noalloc_fail(CRP_ECUDA, "device status " + std::to_string(status));
+    *n_out = (int64_t)count;
     if ((int64_t)count > capacity)
         return noalloc_fail(CRP_EINVAL, "output capacity too small; *n_out holds the size needed");
     return CRP_OK;

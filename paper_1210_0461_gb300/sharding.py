@@ -53,3 +53,25 @@ def gather_sketch(local, group=None):
     t = torch.from_numpy(np.ascontiguousarray(local)).clone()
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     return t.numpy()
+
+
+def job_rate(units_total: float, ms_local: float, group=None) -> tuple[float, float]:
+    """Whole-job throughput of a strong-scaling run: the ranks split one fixed
+    product (each enumerates only its own partition interval, so the product's
+    terms are counted once, not once per rank), and the job takes as long as
+    its slowest rank.  Returns (units_total / slowest time in s, slowest time
+    in ms); without an initialised process group, the local figures."""
+    ms = float(ms_local)
+    try:
+        import torch.distributed as dist
+        active = dist.is_available() and dist.is_initialized()
+    except Exception:
+        active = False
+    if active:
+        import torch
+        backend = dist.get_backend(group)
+        dev = "cuda" if backend == "nccl" else "cpu"
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+        ms = float(t.item())
+    return units_total / (ms / 1e3), ms

@@ -100,6 +100,52 @@ def test_partition_hash_is_close_to_uniform_on_entries():
     assert chi2 < 60  # 15 d.o.f.; p ~ 1e-6 threshold
 
 
+GAMMA = 0x9E3779B97F4A7C15
+
+
+def test_partition_hash_worked_values():
+    # hand-worked from the published SplitMix64 outputs (golden fixture)
+    rows = [l.strip().split("|") for l in open(os.path.join(GOLD, "partition_hash_worked.txt"))
+            if l.strip() and not l.startswith("#")]
+    n = 0
+    for r in rows:
+        if r[0] == "S":
+            P, x, ha, hb = map(int, r[1:])
+            lg = P.bit_length() - 1
+            assert int(O.side_hash(np.array([x]), 0, lg)[0]) == ha
+            assert int(O.side_hash(np.array([x]), GAMMA, lg)[0]) == hb
+        else:
+            P, i, j, h = map(int, r[1:])
+            assert int(O.partition_of(np.array([i]), np.array([j]), P, 0, GAMMA)[0]) == h
+        n += 1
+    assert n == 23
+
+
+@pytest.mark.parametrize("P", [2, 8, 64, 4096])
+@pytest.mark.parametrize("seeds", [(ci.SEED_A, ci.SEED_B), (1, 2), (0, GAMMA)])
+def test_partition_hash_is_additive_mod_P(P, seeds):
+    # Lemma 1's cyclic windows rest on h(i,j) = h_a(i) + h_b(j) mod P: for two
+    # rows i1, i2 the difference h(i1, j) - h(i2, j) mod P is the same for every
+    # column j and equals h_a(i1) - h_a(i2); likewise for two columns.  XOR,
+    # subtraction or a swapped side would break one of the two identities.
+    sa, sb = seeds
+    lg = P.bit_length() - 1
+    rng = np.random.default_rng(P)
+    i = rng.integers(0, 2**31, 40)
+    j = rng.integers(0, 2**31, 250)
+    H = O.partition_of(i[:, None], j[None, :], P, sa, sb)
+    ha = np.array([O.mas_hash_scalar(int(x), *O.hash_params(sa), lg) for x in i])
+    hb = np.array([O.mas_hash_scalar(int(x), *O.hash_params(sb), lg) for x in j])
+    rows = (H - H[:1, :]) % P
+    assert (rows == ((ha - ha[0]) % P)[:, None]).all()
+    cols = (H - H[:, :1]) % P
+    assert (cols == ((hb - hb[0]) % P)[None, :]).all()
+    # every pair against the scalar definition
+    for x in range(0, len(i), 7):
+        for y in range(0, len(j), 11):
+            assert H[x, y] == (int(ha[x]) + int(hb[y])) % P
+
+
 # ---------------------------------------------------------------------------
 # Exact product: dense brute force and closed forms
 # ---------------------------------------------------------------------------

@@ -57,3 +57,47 @@ def test_adam_minimises_quadratic():
     for s in range(1, 2001):
         theta, m, v = O.adam_step(theta, m, v, 2 * theta, 0.05, s)
     assert np.abs(theta).max() < 1e-2
+
+
+def test_marginal_features_closed_form():
+    # log(1 + c) / log(1 + max c) at counts 0, 9, 99 with max 99:
+    # log 1 = 0, log 10 / log 100 = 1/2, log 100 / log 100 = 1
+    X = O.marginal_features(np.array([0, 9, 99]), np.array([99, 0, 9]), np.log(100.0))
+    np.testing.assert_allclose(X, [[0.0, 1.0], [0.5, 0.0], [1.0, 0.5]], rtol=1e-15, atol=0)
+
+
+def test_prefix_counts_and_candidate_pairs_against_dense_and_brute_force():
+    rng = np.random.default_rng(3)
+    m, n, R = 300, 40, 9
+    ptr = [0]
+    idx = []
+    for _ in range(m):
+        L = rng.integers(0, 8)
+        # Zipf-like item draws so that counts differ and some tie
+        sel = np.unique(np.minimum(rng.zipf(1.6, L) - 1, n - 1))
+        idx.extend(sel.tolist())
+        ptr.append(len(idx))
+    T = O.Compressed(np.array(ptr, np.int64), np.array(idx, np.int32), None, n)
+    c = O.prefix_item_counts(T)
+    assert np.array_equal(c, O.dense(T).sum(axis=0).astype(np.int64))   # column sums
+    top = O.top_items(c, R)
+    brute = sorted(range(n), key=lambda x: (-c[x], x))[:R]
+    assert top.tolist() == brute
+    i, j, X, c2 = O.candidate_pairs(T, R)
+    assert np.array_equal(c2, c)
+    assert len(i) == R * (R - 1) // 2 and (i < j).all()
+    assert set(i.tolist()) | set(j.tolist()) == set(brute)
+    assert len(set(zip(i.tolist(), j.tolist()))) == len(i)
+    mx = c.max()
+    # the most frequent item's feature is 1; an item of count 0 would be 0
+    for a, b, x in zip(i, j, X):
+        if c[a] == mx:
+            assert x[0] == 1.0
+        if c[b] == mx:
+            assert x[1] == 1.0
+        assert 0.0 <= x[0] <= 1.0 and 0.0 <= x[1] <= 1.0
+    # monotone in the count: a larger count never gets a smaller feature
+    f = np.concatenate([X[:, 0], X[:, 1]])
+    cc = np.concatenate([c[i], c[j]])
+    o = np.argsort(cc, kind="stable")
+    assert (np.diff(f[o]) >= 0).all()

@@ -109,3 +109,39 @@ def test_gathered_sketch_equals_the_whole_sketch_two_ranks():
     want = O.count_sketch(O.exact_product(T, T, O.FULL), P, ci.SEED_A, ci.SEED_B)
     for r in range(world):
         assert np.array_equal(np.array(got[r]), want)
+
+
+def _rate_worker(rank, world, port, out):
+    import torch.distributed as dist
+    from paper_1210_0461_gb300.sharding import job_rate
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # rank r took 100 + 50 r ms for its interval of a 3e9-term product
+    out.put((rank, job_rate(3e9, 100.0 + 50.0 * rank)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_job_rate_counts_the_product_once_over_the_slowest_rank():
+    """Strong scaling by partition interval: two ranks split one product of
+    3e9 terms; the job's rate is 3e9 terms over the slower rank's 150 ms on
+    every rank, not twice that."""
+    import torch.multiprocessing as mp
+    from paper_1210_0461_gb300.sharding import job_rate
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    world = 2
+    port = _free_port()
+    procs = [ctx.Process(target=_rate_worker, args=(r, world, port, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    got = dict(q.get(timeout=120) for _ in range(world))
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    for r in range(world):
+        rate, ms = got[r]
+        assert ms == 150.0
+        assert rate == 3e9 / 0.150
+    assert job_rate(3e9, 100.0) == (3e9 / 0.1, 100.0)     # one process, no group

@@ -111,3 +111,103 @@ def test_noalloc_rejects_sizes_beyond_its_limits(crp):
                                              None, None, None, 0, ctypes.byref(n), None)
     assert st == crp.CRP_EINVAL
     assert b"1024" in crp.lib().crp_last_error()
+
+
+def _raw_call(crp, desc, a, b, i, j, w, capacity):
+    """One call of the entry point on prepared device buffers; returns the
+    status and *n_out."""
+    import torch
+    n = ctypes.c_int64(-1)
+    stream = torch.cuda.current_stream().cuda_stream
+    st = crp.lib().crp_outer_product_noalloc(
+        ctypes.byref(desc), ctypes.byref(a), ctypes.byref(b),
+        i.data_ptr() if i is not None else None, j.data_ptr() if j is not None else None,
+        w.data_ptr() if w is not None else None, capacity, ctypes.byref(n), stream)
+    return st, n.value
+
+
+def _desc(crp, n_rows, n_cols, P, value_type=0, mode=0):
+    d = crp.crp_plan_desc()
+    d.n_rows, d.n_cols, d.P = n_rows, n_cols, P
+    d.seed_a, d.seed_b = ci.SEED_A, ci.SEED_B
+    d.value_type, d.mode = value_type, mode
+    return d
+
+
+def test_noalloc_allocates_nothing_and_handles_one_partition(crp):
+    """The point of the entry point: a call moves neither the device's free
+    memory (cudaMemGetInfo) nor PyTorch's allocator.  The second and third
+    calls are measured (the first may load the library's kernels).  P = 1 puts
+    every entry into one partition of 2^20 slots."""
+    import torch
+    T = ci.C1.generate()
+    want = _sorted(*_with_plan(crp, T, T, 1000, 1000, 1, crp.CRP_I32, crp.CRP_FULL))
+    dT = crp.to_device(T)
+    a = dT.c_struct()
+    cap = len(want[0]) + 5
+    i = torch.empty(cap, dtype=torch.int32, device="cuda")
+    j = torch.empty(cap, dtype=torch.int32, device="cuda")
+    w = torch.empty(cap, dtype=torch.float64, device="cuda")
+    d = _desc(crp, 1000, 1000, 1)
+    st, n = _raw_call(crp, d, a, a, i, j, w, cap)
+    assert st == crp.CRP_OK, crp.lib().crp_last_error()
+    torch.cuda.synchronize()
+    for _ in range(2):
+        free0, _ = torch.cuda.mem_get_info()
+        stats0 = torch.cuda.memory_stats()
+        st, n = _raw_call(crp, d, a, a, i, j, w, cap)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        stats1 = torch.cuda.memory_stats()
+        assert st == crp.CRP_OK, crp.lib().crp_last_error()
+        assert free1 == free0
+        for key in ("allocation.all.allocated", "segment.all.allocated"):
+            assert stats1.get(key, 0) == stats0.get(key, 0), key
+        assert n == len(want[0])
+        got = _sorted(i[:n].cpu().numpy(), j[:n].cpu().numpy(), w[:n].cpu().numpy())
+        for g, x in zip(got, want):
+            assert np.array_equal(g, x)
+
+
+def test_noalloc_short_output_reports_the_size_needed(crp):
+    """capacity below the entry count: CRP_EINVAL, *n_out = the number of
+    entries the plan path finds, and nothing written past the capacity."""
+    import torch
+    T = ci.C1.generate()
+    want = _with_plan(crp, T, T, 1000, 1000, 64, crp.CRP_I32, crp.CRP_FULL)
+    dT = crp.to_device(T)
+    a = dT.c_struct()
+    i = torch.full((4,), -7, dtype=torch.int32, device="cuda")
+    j = torch.full((4,), -7, dtype=torch.int32, device="cuda")
+    w = torch.full((4,), -7.0, dtype=torch.float64, device="cuda")
+    st, n = _raw_call(crp, _desc(crp, 1000, 1000, 64), a, a, i, j, w, 1)
+    assert st == crp.CRP_EINVAL
+    assert n == len(want[0])
+    assert (i[1:].cpu().numpy() == -7).all() and (j[1:].cpu().numpy() == -7).all()
+    assert (w[1:].cpu().numpy() == -7.0).all()
+
+
+def test_noalloc_reports_a_full_partition_and_recovers(crp):
+    """A product with more entries than a partition of the static table holds
+    (100,000 transactions of the 10M-transaction recipe, P = 1024: ~1,000
+    slots per partition, ~10^4 entries per partition) returns
+    CRP_ETABLE_FULL with *n_out = 0; the next call, on a product that fits,
+    is exact again (the full marks are cleared)."""
+    import torch
+    big = ci.C2.scaled(m=100_000).generate()
+    dB = crp.to_device(big)
+    b = dB.c_struct()
+    cap = 1 << 20
+    i = torch.empty(cap, dtype=torch.int32, device="cuda")
+    j = torch.empty(cap, dtype=torch.int32, device="cuda")
+    w = torch.empty(cap, dtype=torch.float64, device="cuda")
+    st, n = _raw_call(crp, _desc(crp, big.n_minor, big.n_minor, 1024), b, b, i, j, w, cap)
+    assert st == crp.CRP_ETABLE_FULL
+    assert n == 0
+    assert b"static table" in crp.lib().crp_last_error()
+    T = ci.C1.generate()
+    want = _sorted(*_with_plan(crp, T, T, 1000, 1000, 64, crp.CRP_I32, crp.CRP_UPPER))
+    got = _sorted(*_noalloc(crp, T, T, 1000, 1000, 64, crp.CRP_I32, crp.CRP_UPPER,
+                            capacity=len(want[0])))
+    for g, x in zip(got, want):
+        assert np.array_equal(g, x)
