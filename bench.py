@@ -796,6 +796,7 @@ def main():
                                    + ("+k_hot_flush" if args.hot else "")
                                    + ("+k_warm_flush" if args.warm else ""),
                          "kernel_ms": acc,
+                         "route_ms": st.get("last_route_ms"),
                          "bytes_model": f"{BYTES_PER_TERM_UPDATE:g} B/term + input + "
                                         f"{SLOT_BYTES:g} B/entry",
                          "peak_source": f"{peak_src} hbm_gbs"},

@@ -185,6 +185,20 @@ typedef struct {
                                      after the hot block; W is lowered so the
                                      stripes fit 64 MB.  Same selection and
                                      flush as hot_items. */
+    uint32_t route_pool_chunks;   /* CRP_PLAN_ROUTED: at most this many record
+                                     chunks (512 records each) in the pool,
+                                     overflow chunks included (0: sized from
+                                     each call's count of routed records).  A
+                                     pool too small for the records sends the
+                                     rest to the overflow chunks and, once
+                                     those fill, straight to the tables:
+                                     slower, the same result.  For exercising
+                                     those paths; no paper counterpart. */
+    uint32_t lock_wait_us;        /* CRP_PLAN_LOCKED_SUMMARY: how long a warp
+                                     waits for a bucket's lock, in
+                                     microseconds of SM clock at 2 GHz, before
+                                     it drops the update and the call reports
+                                     CRP_ETIMEOUT (0: about 4 s) */
 } crp_plan_desc;
 
 typedef struct crp_plan crp_plan;
@@ -277,6 +291,15 @@ uint64_t crp_topk_certified_calls(const crp_plan *plan);
  * reserved stays in its partition's summary.  crp_reset keeps the reserved
  * keys and zeroes their counts.  Synchronises. */
 crp_status crp_reserve(crp_plan *plan, const uint64_t *keys, int32_t n);
+
+/* Test hook for the bounded lock wait of locked-bucket plans
+ * (CRP_PLAN_LOCKED_SUMMARY); the paper has no counterpart.  Takes partition
+ * p's bucket lock on behalf of the host and never hands it on (the next
+ * ticket is advanced on the device, stream-ordered): every later update of
+ * p waits lock_wait_us, gives up, and crp_sync returns CRP_ETIMEOUT; other
+ * waiters of the plan give up at once after the first timeout.  crp_reset
+ * releases it.  CRP_EINVAL for other plans or p >= P. */
+crp_status crp_debug_hold_lock(crp_plan *plan, uint32_t p);
 
 /* Partition of entry (i,j): (h_a(i) + h_b(j)) mod P, computed on the host. */
 uint32_t crp_partition_of(const crp_plan *plan, int32_t i, int32_t j);

@@ -52,7 +52,8 @@ class crp_plan_desc(ctypes.Structure):
                 ("smem_slots", ctypes.c_uint32), ("flags", ctypes.c_uint32),
                 ("hot_items", ctypes.c_uint32), ("target_load_pct", ctypes.c_uint32),
                 ("part_begin", ctypes.c_uint32), ("part_end", ctypes.c_uint32),
-                ("warm_items", ctypes.c_uint32)]
+                ("warm_items", ctypes.c_uint32), ("route_pool_chunks", ctypes.c_uint32),
+                ("lock_wait_us", ctypes.c_uint32)]
 
 
 class crp_stats_t(ctypes.Structure):
@@ -119,6 +120,7 @@ _SIGS = {
                                     ctypes.POINTER(ctypes.c_double), _P]),
     "crp_sketch_read": (ctypes.c_int, [_P, _P]),
     "crp_sketch_estimate": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int64, _P]),
+    "crp_debug_hold_lock": (ctypes.c_int, [_P, ctypes.c_uint32]),
     "crp_version": (ctypes.c_char_p, []),
     "crp_last_error": (ctypes.c_char_p, []),
 }
@@ -221,7 +223,7 @@ class Plan:
                  auto_grow: bool = False, flags: int = 0, stream=None,
                  summary_counters: int = 0, reserved_counters: int = 0, hot_items: int = 0,
                  target_load_pct: int = 0, part_begin: int = 0, part_end: int = 0,
-                 warm_items: int = 0):
+                 warm_items: int = 0, route_pool_chunks: int = 0, lock_wait_us: int = 0):
         self._lib = lib()
         d = crp_plan_desc()
         d.n_rows, d.n_cols, d.P = n_rows, n_cols, P
@@ -233,6 +235,7 @@ class Plan:
         d.target_load_pct = target_load_pct
         d.part_begin, d.part_end = part_begin, part_end
         d.warm_items = warm_items
+        d.route_pool_chunks, d.lock_wait_us = route_pool_chunks, lock_wait_us
         d.auto_grow = 1 if auto_grow else 0
         d.groups, d.tile_vectors, d.smem_slots, d.flags = groups, tile_vectors, smem_slots, flags
         self.desc = d
@@ -281,6 +284,10 @@ class Plan:
         k = np.ascontiguousarray(keys, dtype=np.uint64)
         _check(self._lib.crp_reserve(self._h, k.ctypes.data if len(k) else None, len(k)),
                "crp_reserve")
+
+    def debug_hold_lock(self, p: int):
+        """Test hook: hold partition p's bucket lock (crp_debug_hold_lock)."""
+        _check(self._lib.crp_debug_hold_lock(self._h, p), "crp_debug_hold_lock")
 
     def partition_of(self, i: int, j: int) -> int:
         return int(self._lib.crp_partition_of(self._h, i, j))

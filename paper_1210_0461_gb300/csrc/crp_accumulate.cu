@@ -243,7 +243,8 @@ k_accumulate(AccumulateArgs A, const uint32_t *__restrict__ b_hash) {
                         uint32_t slot;
                         is_new = smem_find(keys, smask, key, slot, &A.tv.dc->status);
                         if (slot != 0xffffffffu)
-                            smem_add_comp(&((unsigned long long *)vals)[slot], p, e);
+                            smem_add_comp(&((unsigned long long *)vals)[slot], p, e,
+                                          &A.tv.dc->status);
                     }
                 }
                 const unsigned nnew = __popc(__ballot_sync(kFull, is_new));

@@ -470,6 +470,17 @@ extern "C" crp_status crp_reset(crp_plan *pl) {
     return CRP_OK;
 }
 
+__global__ void k_take_ticket(unsigned int *next) { atomicAdd(next, 1u); }
+
+extern "C" crp_status crp_debug_hold_lock(crp_plan *pl, uint32_t p) {
+    if (!pl || !pl->locked || !pl->d_locks || p >= pl->d.P)
+        return fail(CRP_EINVAL, "crp_debug_hold_lock: a locked-bucket plan and p < P are needed");
+    k_take_ticket<<<1, 1, 0, pl->stream>>>(pl->d_locks + 2 * (size_t)p);
+    CRP_CUDA(cudaGetLastError());
+    pl->launches += 1;
+    return CRP_OK;
+}
+
 extern "C" uint32_t crp_partition_of(const crp_plan *pl, int32_t i, int32_t j) {
     if (!pl) return 0;
     return partition_hash(pl->hp, (uint32_t)i, (uint32_t)j);
@@ -525,6 +536,7 @@ static TableView table_view(crp_plan *pl, Slot *slots, const unsigned long long 
     tv.value_type = pl->d.value_type;
     tv.summary = pl->summary ? (pl->locked ? 2 : 1) : 0;
     tv.locks = pl->d_locks;
+    if (pl->d.lock_wait_us) tv.lock_wait = (long long)pl->d.lock_wait_us * 2000;
     tv.bucket_ell = pl->ell;
     tv.live = pl->d_live;
     tv.floor = pl->d_floor;
@@ -770,9 +782,9 @@ static crp_status summary_accumulate(crp_plan *pl, const crp_sparse *A, const cr
 
 // Routed mode: enumerate every term once into per-group bins, then apply the
 // bins group by group so each group's table region stays in L2.
-// Size the record pool and bins of the routed path for up to `terms`
-// records and fill RA's routing fields (RA.acc is the caller's).
-static crp_status routed_prepare(crp_plan *pl, uint64_t terms, RouteArgs &RA) {
+// Size the record pool and bins of the routed path for `records` records
+// and fill RA's routing fields (RA.acc is the caller's).
+static crp_status routed_prepare(crp_plan *pl, uint64_t records, RouteArgs &RA) {
     const uint32_t P = pl->d.P;
     // groups of partitions whose table region is about 96 MB or more (the
     // record chunks of every CTA stay open in L2 for each group, so more
@@ -787,14 +799,18 @@ static crp_status routed_prepare(crp_plan *pl, uint64_t terms, RouteArgs &RA) {
     Bn = std::min<uint32_t>(Bn, 8192);   // per-CTA chunk state lives in shared memory
     const int grid = 2 * pl->sm_count;
     const uint64_t rec = pl->d.value_type == CRP_I32 ? 8 : 16;
-    // every term may become a record; each CTA also holds a partly filled
-    // chunk and a spare per bin; overflow chunks for appends that find no
-    // chunk slot: 1/256 of the chunks, at least 256
+    // every record, 1/64 more for spares reserved ahead but never installed;
+    // each CTA also holds a partly filled chunk and a spare per bin; overflow
+    // chunks for appends that find no chunk slot: 1/256 of the chunks, at
+    // least 256 (a pool that still runs dry sends records to the overflow
+    // chunks, then straight to the tables)
     const uint32_t ovc = (uint32_t)std::min<uint64_t>(
-        std::max<uint64_t>(terms / kChunkRecs / 256, 256), 1u << 20);
-    const uint64_t chunks_needed =
-        (terms + kChunkRecs - 1) / kChunkRecs + 2ull * Bn * grid + ovc + 1;
-    const uint32_t chunks = (uint32_t)std::min<uint64_t>(chunks_needed, 0xFFFFFFF0ull);
+        std::max<uint64_t>(records / kChunkRecs / 256, 256), 1u << 20);
+    const uint64_t chunks_needed = (records + records / 64 + kChunkRecs - 1) / kChunkRecs +
+                                   2ull * Bn * grid + ovc + 1;
+    uint32_t chunks = (uint32_t)std::min<uint64_t>(chunks_needed, 0xFFFFFFF0ull);
+    if (pl->d.route_pool_chunks)   // a capped pool (the overflow paths take the rest)
+        chunks = std::min<uint32_t>(chunks, std::max<uint32_t>(pl->d.route_pool_chunks, ovc + 1));
     if (Bn != pl->B) {
         cudaFree(pl->d_route_ctl);
         pl->d_route_ctl = nullptr;
@@ -816,8 +832,7 @@ static crp_status routed_prepare(crp_plan *pl, uint64_t terms, RouteArgs &RA) {
             if (cudaMalloc(&pl->pool, (size_t)c * kChunkRecs * rec) == cudaSuccess) break;
             cudaGetLastError();
             pl->pool = nullptr;
-            if (c <= chunks / 16 || c <= 2u * Bn * grid + ovc + 1)
-                return fail(CRP_ENOMEM, "routed pool");
+            if (c <= chunks / 16 || c <= ovc + 1) return fail(CRP_ENOMEM, "routed pool");
             c /= 2;
         }
         CRP_CUDA(cudaMalloc(&pl->d_chunk_bin, (size_t)c * 4));
@@ -827,7 +842,8 @@ static crp_status routed_prepare(crp_plan *pl, uint64_t terms, RouteArgs &RA) {
     }
     // chunks [0, ovc): overflow, bin 0, empty; the pool hands out chunks from ovc
     pl->ov_chunks = ovc;
-    CRP_CUDA(cudaMemsetAsync(pl->d_chunk_bin, 0xFF, (size_t)pl->pool_chunks * 4, pl->stream));
+    const uint32_t n_chunks = std::min<uint32_t>(pl->pool_chunks, chunks);
+    CRP_CUDA(cudaMemsetAsync(pl->d_chunk_bin, 0xFF, (size_t)n_chunks * 4, pl->stream));
     CRP_CUDA(cudaMemsetAsync(pl->d_chunk_bin, 0, (size_t)ovc * 4, pl->stream));
     CRP_CUDA(cudaMemsetAsync(pl->pool, 0xFF, (size_t)ovc * kChunkRecs * rec, pl->stream));
     CRP_CUDA(cudaMemsetAsync(pl->d_route_ctl, 0, (2 * (size_t)Bn + 1) * 4, pl->stream));
@@ -840,7 +856,7 @@ static crp_status routed_prepare(crp_plan *pl, uint64_t terms, RouteArgs &RA) {
     RA.chunk_next = ctl;
     RA.order = pl->d_order;
     RA.start = ctl + 1 + 2 * Bn;
-    RA.n_chunks = pl->pool_chunks;
+    RA.n_chunks = n_chunks;
     RA.B = Bn;
     uint32_t lgB = 0;
     while ((1u << lgB) < Bn) ++lgB;
@@ -862,25 +878,10 @@ static crp_status routed_run(crp_plan *pl, const RouteArgs &RA) {
     return CRP_OK;
 }
 
-static unsigned long long count_terms(crp_plan *pl, const crp_sparse *A, const crp_sparse *B,
-                                      crp_status &st) {
-    unsigned long long terms = 0;
-    st = CRP_OK;
-    if (launch_count_terms(A->ptr, B->ptr, A->n_major, pl->d_scratch64, pl->stream) != cudaSuccess ||
-        cudaMemcpyAsync(&terms, pl->d_scratch64, 8, cudaMemcpyDeviceToHost, pl->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(pl->stream) != cudaSuccess)
-        st = fail(CRP_ECUDA, "counting terms failed");
-    pl->launches += 1;
-    return terms;
-}
-
 // Routed mode: enumerate every term once into per-group bins, then apply the
 // bins group by group so each group's table region stays in L2.
 static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp_sparse *B) {
     crp_status st;
-    const unsigned long long terms = count_terms(pl, A, B, st);
-    if (st != CRP_OK) return st;
     RouteArgs RA;
     RA.acc = make_args(pl, A, B, B->idx, B->val, 1);
     RA.acc.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
@@ -889,7 +890,14 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
         if (st != CRP_OK) return st;
         set_dense_args(pl, RA.acc);
     }
-    st = routed_prepare(pl, terms, RA);
+    // the records this call routes (the terms outside the dense tiers) size
+    // the pool: an exact count in CRP_FULL mode, an upper bound otherwise
+    unsigned long long records = 0;
+    CRP_CUDA(launch_count_records(RA.acc, pl->d_scratch64, pl->stream));
+    CRP_CUDA(cudaMemcpyAsync(&records, pl->d_scratch64, 8, cudaMemcpyDeviceToHost, pl->stream));
+    CRP_CUDA(cudaStreamSynchronize(pl->stream));
+    pl->launches += 1;
+    st = routed_prepare(pl, records, RA);
     if (st != CRP_OK) return st;
     CRP_CUDA(cudaEventRecord(pl->ev0, pl->stream));
     st = routed_run(pl, RA);

@@ -88,9 +88,9 @@ __device__ __forceinline__ void summary_update(const TableView &tv, uint32_t p,
 // takes (key, v, 0); else the counter of least count (ties: smallest key)
 // becomes (key, min + v, min).  Counters hold the count in the low 32 bits
 // of val and the overestimation in the high 32 (the summary slot format).
-// The wait for the lock is bounded (about 4 s of SM clock); past it the
-// update is dropped and the status records a timeout.
-constexpr long long kLockWaitCycles = 8ll << 30;
+// The wait for the lock is bounded (TableView::lock_wait cycles of SM clock,
+// about 4 s by default); past it the update is dropped and the status
+// records a timeout.
 
 // The counters of the locked bucket at b after one weighted update (the
 // caller holds the bucket's lock).
@@ -161,7 +161,7 @@ __device__ __forceinline__ bool bucket_lock(const TableView &tv, uint32_t p) {
         const unsigned int now = ld_acquire_u32(serving);
         if (now == ticket) return true;
         if (ld_relaxed_u32(&tv.dc->status) & kStatusTimeout) return false;
-        if (clock64() - t0 > kLockWaitCycles) {
+        if (clock64() - t0 > tv.lock_wait) {
             atomicOr(&tv.dc->status, kStatusTimeout);
             return false;
         }
@@ -200,6 +200,21 @@ __device__ __forceinline__ void load_bucket_keys(const Slot *s, unsigned long lo
     (void)v1;
 }
 
+// The same with an evict-last hint: the routed apply phase works through one
+// group's table region at a time, and its lines should outlast the records
+// streaming past them in L2 until the group is done.
+__device__ __forceinline__ void load_bucket_keys_keep(const Slot *s, unsigned long long *k4) {
+    unsigned long long v0, v1;
+    asm volatile("ld.global.L1::no_allocate.L2::evict_last.v4.u64 {%0, %1, %2, %3}, [%4];"
+                 : "=l"(k4[0]), "=l"(v0), "=l"(k4[1]), "=l"(v1)
+                 : "l"(s));
+    asm volatile("ld.global.L1::no_allocate.L2::evict_last.v4.u64 {%0, %1, %2, %3}, [%4];"
+                 : "=l"(k4[2]), "=l"(v0), "=l"(k4[3]), "=l"(v1)
+                 : "l"(s + 2));
+    (void)v0;
+    (void)v1;
+}
+
 // Add v (u32 count, or the bits of a double) to entry `key` of partition p.
 __device__ __forceinline__ void table_update(const TableView &tv, uint32_t p,
                                              unsigned long long key, unsigned long long v) {
@@ -228,7 +243,8 @@ __device__ __forceinline__ void table_update(const TableView &tv, uint32_t p,
     for (unsigned long long probe = 0; probe <= mask; probe += 4) {
         Slot *s = tv.slots + off + h;
         unsigned long long k4[4];
-        load_bucket_keys(s, k4);
+        if (tv.keep_in_l2) load_bucket_keys_keep(s, k4);
+        else load_bucket_keys(s, k4);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             unsigned long long k = k4[q];
@@ -306,7 +322,7 @@ __device__ __forceinline__ void locked_update_warp(const TableView &tv, bool has
         bool stop = false;
         if (lane == 0)
             stop = (ld_relaxed_u32(&tv.dc->status) & kStatusTimeout) ||
-                   clock64() - t0 > kLockWaitCycles;
+                   clock64() - t0 > tv.lock_wait;
         if (__shfl_sync(0xffffffffu, stop, 0)) {
             if (lane == 0) atomicOr(&tv.dc->status, kStatusTimeout);
             return;
@@ -360,7 +376,8 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &t) {
 }
 
 // Add the exact product p + e into a packed (sum, compensation) fp32 pair.
-__device__ __forceinline__ void smem_add_comp(unsigned long long *cell, float p, float e) {
+__device__ __forceinline__ void smem_add_comp(unsigned long long *cell, float p, float e,
+                                              unsigned int *status) {
     unsigned long long old = *(volatile unsigned long long *)cell;
     for (int guard = 0; guard < (1 << 20); ++guard) {
         float s = __uint_as_float((unsigned int)(old >> 32));
@@ -373,6 +390,8 @@ __device__ __forceinline__ void smem_add_comp(unsigned long long *cell, float p,
         if (prev == old) return;
         old = prev;
     }
+    // the guard ran out: the term is lost, so the call must not succeed
+    atomicOr(status, kStatusSmemProbe);
 }
 
 // ---------------------------------------------------------------------------

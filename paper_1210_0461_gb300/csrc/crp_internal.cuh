@@ -112,12 +112,15 @@ struct TableView {
     unsigned long long spill_cap = 0;
     DevCounters *dc = nullptr;
     int value_type = 0;
+    int keep_in_l2 = 0;                       // bucket loads hint evict-last (routed apply)
     // summary mode (Space-Saving semantics per partition)
     int summary = 0;                          // 1: tables are counter summaries;
                                               // 2: one locked bucket of bucket_ell
                                               //    counters per partition
     unsigned int *locks = nullptr;            // summary 2: a ticket lock per partition
                                               //    (next ticket, now serving)
+    long long lock_wait = 8ll << 30;          // summary 2: SM-clock cycles a waiter
+                                              //    waits for a lock before giving up
     uint32_t bucket_ell = 0;
     unsigned int *live = nullptr;             // occupied slots per partition
     const unsigned int *floor = nullptr;      // current floor (min count) per partition
@@ -216,6 +219,10 @@ struct RouteArgs {
     uint32_t ov_cap;
 };
 cudaError_t launch_route(const RouteArgs &RA, int grid, cudaStream_t s);
+// Records the routing phase will append: per outer product, the terms outside
+// the dense tiers (hot pairs, warm rows, warm columns), summed into *out.
+cudaError_t launch_count_records(const AccumulateArgs &A, unsigned long long *out,
+                                 cudaStream_t s);
 cudaError_t launch_apply(const RouteArgs &RA, unsigned int *count, unsigned int *fill, int grid,
                          cudaStream_t s);
 size_t route_smem_bytes(uint32_t B, uint32_t core_H);

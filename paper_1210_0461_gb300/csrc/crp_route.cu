@@ -531,10 +531,63 @@ cudaError_t launch_apply(const RouteArgs &RA, unsigned int *count, unsigned int 
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(&RA.acc.tv.dc->work_next, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
+    RouteArgs AA = RA;
+    AA.acc.tv.keep_in_l2 = 1;   // the current group's table lines outlast the records
     if (RA.acc.tv.value_type == CRP_I32)
-        k_apply<CRP_I32><<<grid, kThreads, 0, s>>>(RA);
+        k_apply<CRP_I32><<<grid, kThreads, 0, s>>>(AA);
     else
-        k_apply<CRP_F32_COMP><<<grid, kThreads, 0, s>>>(RA);
+        k_apply<CRP_F32_COMP><<<grid, kThreads, 0, s>>>(AA);
+    return cudaGetLastError();
+}
+
+// Records of the routing phase, counted per outer product from the dense
+// tiers' rank arrays: a term (i, j) is routed unless both are hot, or i or j
+// is warm, so with a_k's counts L (entries), W (warm) and H (hot, not warm)
+// and b_k's likewise, the records number (La - Wa)(Lb - Wb) - Ha Hb.  (An
+// upper bound in CRP_UPPER mode and for interval plans.)
+__device__ __forceinline__ void tier_counts(const int32_t *idx, int64_t lo, int64_t hi,
+                                            const uint16_t *hot, uint32_t R, const uint16_t *warm,
+                                            uint32_t W, int32_t n, long long &w, long long &h) {
+    w = 0;
+    h = 0;
+    for (int64_t x = lo; x < hi; ++x) {
+        const int32_t v = idx[x];
+        if (v < 0 || v >= n) continue;
+        const bool is_w = warm && warm[v] < W;
+        const bool is_h = hot && hot[v] < R;
+        w += is_w;
+        h += is_h && !is_w;
+    }
+}
+
+__global__ void k_count_records(AccumulateArgs A, unsigned long long *out) {
+    unsigned long long sum = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < A.K;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a0 = A.a_ptr[k], a1 = A.a_ptr[k + 1], b0 = A.b_ptr[k], b1 = A.b_ptr[k + 1];
+        long long wa = 0, ha = 0, wb = 0, hb = 0;
+        if (A.hot_R || A.warm_W) {
+            tier_counts(A.a_idx, a0, a1, A.hot_rank_a, A.hot_R, A.warm_rank_a, A.warm_W,
+                        A.n_rows, wa, ha);
+            tier_counts(A.b_idx, b0, b1, A.hot_rank_b, A.hot_R, A.warm_rank_b, A.warm_W,
+                        A.n_cols, wb, hb);
+        }
+        const long long r = ((a1 - a0) - wa) * ((b1 - b0) - wb) - ha * hb;
+        sum += (unsigned long long)(r > 0 ? r : 0);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) sum += __shfl_down_sync(kFull, sum, d);
+    if ((threadIdx.x & 31) == 0 && sum) atomicAdd(out, sum);
+}
+
+cudaError_t launch_count_records(const AccumulateArgs &A, unsigned long long *out,
+                                 cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (A.K + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_count_records<<<(int)blocks, 256, 0, s>>>(A, out);
     return cudaGetLastError();
 }
 

@@ -55,8 +55,38 @@ def test_version_and_struct_sizes(libcrp):
     from paper_1210_0461_gb300 import crp
     assert libcrp.crp_version().startswith(b"crp ")
     assert ctypes.sizeof(crp.crp_sparse) == 48
-    assert ctypes.sizeof(crp.crp_plan_desc) == 96
+    assert ctypes.sizeof(crp.crp_plan_desc) == 104
     assert ctypes.sizeof(crp.crp_stats_t) == 80
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the sizes and field offsets the C
+    compiler gives the header's structs."""
+    import shutil
+    import subprocess
+    from paper_1210_0461_gb300 import crp
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    checks = []
+    for cname, ct in (("crp_sparse", crp.crp_sparse), ("crp_plan_desc", crp.crp_plan_desc),
+                      ("crp_stats_t", crp.crp_stats_t)):
+        checks.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in ct._fields_:
+            checks.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "crp.h"\nint main(void){\n'
+                   + "\n".join(checks) + "\nreturn 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for cname, ct in (("crp_sparse", crp.crp_sparse), ("crp_plan_desc", crp.crp_plan_desc),
+                      ("crp_stats_t", crp.crp_stats_t)):
+        assert int(got[cname]) == ctypes.sizeof(ct), cname
+        for f, _ in ct._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(ct, f).offset, (cname, f)
 
 
 def test_sm103a_only_build_flags():

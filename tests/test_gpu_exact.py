@@ -374,3 +374,20 @@ def test_disjoint_intervals_union_is_the_product(crp, cfg):
     i, j, w = map(np.concatenate, (got_i, got_j, got_w))
     gi, gj, gw = _sorted(i, j, w)
     assert np.array_equal(gi, ref.i) and np.array_equal(gj, ref.j) and np.array_equal(gw, ref.w)
+
+
+@pytest.mark.parametrize("pool", [1, 3000], ids=["one-chunk", "3000-chunks"])
+def test_routed_pool_exhaustion_paths(crp, pool):
+    """The routed pool capped below the records it needs (route_pool_chunks):
+    appends that find the pool dry go to the overflow chunks (256 chunks of
+    512 records here) and, once those fill, straight to the tables; the
+    product stays bit-exact.  pool = 1 leaves one chunk besides the overflow
+    chunks; 3000 leaves about one per (CTA, bin), so it runs dry part way."""
+    T = ci.C1.generate()
+    Tc = O.Compressed.of(T)
+    ref = O.exact_product(Tc, Tc, O.FULL)
+    for hot, warm in ((0, 0), (64, 16)):
+        plan = _run(crp, T, T, 1000, 1000, 64, groups=16, flags=8 | 2, hot_items=hot,
+                    warm_items=warm, route_pool_chunks=pool)
+        _check_exact(crp, plan, ref, 64)
+        plan.close()

@@ -138,3 +138,39 @@ def test_invalid_locked_plans_are_rejected(crp):
         kw.setdefault("flags", F)
         with pytest.raises(crp.CrpError):
             crp.Plan(100, 100, 16, 1, 2, **kw)
+
+
+@pytest.mark.parametrize("flags", [0, 4], ids=["on-chip-table", "direct"])
+def test_lock_wait_runs_out_and_the_plan_recovers(crp, flags):
+    """A bucket lock that is never handed on (taken on the host through
+    crp_debug_hold_lock, a failure injected without a GPU fault): the waits
+    for it give up after lock_wait_us, crp_sync reports CRP_ETIMEOUT, and
+    after crp_reset the same plan runs the product with every bucket check
+    passing (the context stays usable)."""
+    import time
+    T = ci.C1.generate()
+    Tc = O.Compressed.of(T)
+    # P = 1024 buckets and a 200 ms bound: without the held lock no wait
+    # comes near the bound (with few buckets and a lock per term, the queue
+    # on one bucket can legitimately take tens of ms)
+    P, ell = 1024, 2
+    ref, part, true, W, distinct = _truth(Tc, Tc, P)
+    plan = crp.Plan(1000, 1000, P, ci.SEED_A, ci.SEED_B, summary_counters=ell,
+                    flags=crp.CRP_PLAN_LOCKED_SUMMARY | flags, lock_wait_us=200_000)
+    d = crp.to_device(T)
+    plan.debug_hold_lock(5)
+    t0 = time.time()
+    plan.accumulate(d, d)
+    with pytest.raises(crp.CrpError) as e:
+        plan.sync()
+    assert e.value.status == crp.CRP_ETIMEOUT
+    assert time.time() - t0 < 30
+    plan.reset()
+    plan.accumulate(d, d)
+    plan.sync()
+    i, j, up, lo = plan.export()
+    _check_buckets(i, j, up, lo, P, ell, 1000, true, W, distinct, ref, part)
+    with pytest.raises(crp.CrpError) as e:
+        plan.debug_hold_lock(P)
+    assert e.value.status == crp.CRP_EINVAL
+    plan.close()
