@@ -54,8 +54,14 @@ typedef enum {
 
 /* value_type */
 enum { CRP_I32 = 0,          /* {0,1} inputs (val == NULL), exact int32 counts */
-       CRP_F32_COMP = 1 };   /* fp32 inputs, exact fp32 products, compensated
-                                fp32 (TwoSum) on chip, fp64 per-entry result */
+       CRP_F32_COMP = 1 };   /* fp32 inputs; each term is the exact product
+                                p + e (fp32 TwoProduct); the on-chip-table
+                                variant sums an entry's terms per CTA as a
+                                compensated fp32 pair (TwoSum) and adds the
+                                pair to the fp64 entry at its flush; the
+                                direct and routed variants add each p + e
+                                (exact in fp64) to the fp64 entry with an
+                                atomic.  fp64 per-entry result. */
 /* mode */
 enum { CRP_FULL = 0,         /* every entry (i,j) */
        CRP_UPPER = 1 };      /* only i < j: pairs above the diagonal, the
@@ -224,7 +230,10 @@ typedef struct {
 
 /* Create a plan: validates desc, derives the hash parameters and allocates
  * the partition tables (exact mode) or summaries (summary mode) on the
- * current device.  stream: a cudaStream_t (NULL = legacy default stream).
+ * current device.  The P partitions are the paper's hash buckets, h the
+ * pairwise independent h(i,j) = (h_a(i) + h_b(j)) mod P of Lemma 1, and the
+ * choice of P, like the paper's number of buckets, is a tuning parameter
+ * (Section 4, "Parameters"; P = 0 tunes it).  stream: a cudaStream_t (NULL = legacy default stream).
  * Returns CRP_EINVAL for a P that is not a power of two, n_rows/n_cols <= 0,
  * an unknown value_type/mode, or smem_slots not a power of two. */
 crp_status crp_plan_create(crp_plan **out, const crp_plan_desc *desc, void *stream);
@@ -245,13 +254,18 @@ crp_status crp_reset(crp_plan *plan);
  * is reported by crp_sync. */
 crp_status crp_outer_accumulate(crp_plan *plan, const crp_sparse *A_csc, const crp_sparse *B_csr);
 
-/* Wait for the plan's stream and return the status the device recorded
- * (CRP_ETABLE_FULL, CRP_EINVAL for an index >= n_minor when
+/* Wait for the plan's stream and return the status the device recorded --
+ * the end of one CRoP pass over the input (Figure 1), after which every
+ * partition holds its entries -- (CRP_ETABLE_FULL, CRP_EINVAL for an index
+ * >= n_minor when
  * CRP_PLAN_DEBUG_CHECKS is set, CRP_ETIMEOUT).  With auto_grow, full
  * partitions are grown and their spilled updates re-inserted first. */
 crp_status crp_sync(crp_plan *plan);
 
-/* The k heaviest entries (largest |weight|; ties by i then j ascending),
+/* The k heaviest entries (largest |weight|; ties by i then j ascending): the
+ * query the paper's case study answers, the most frequent pairs of items
+ * (Section 6; in summary mode the entries the summaries guarantee,
+ * Preliminaries),
  * written in that order to i_out, j_out, w_out (host or device, k entries
  * each); w_lower (nullable) receives the lower bound in summary mode and the
  * weight itself in exact mode.  *n_out (host) = entries written (< k when C
@@ -476,6 +490,21 @@ crp_status crp_predict_reserve(crp_plan *plan, const crp_sparse *prefix, int32_t
 crp_status crp_autotune(const crp_plan_desc *base, const crp_sparse *A, const crp_sparse *B,
                         int64_t sample_vectors, const char *cache_path, crp_plan_desc *best,
                         double *best_terms_per_s, void *stream);
+
+/* Autotuner of batched products (crp_batch_create): times the persistent
+ * launch of a sample of the problems -- every (nprob / sample_probs)-th
+ * problem, sample_probs <= 0 meaning all -- for P in {64, 256, 1024, 4096}
+ * and tile_vectors in {16, 32, 64, 128}, and writes into *best a copy of
+ * *base with the fastest P and tile_vectors (*best_terms_per_s, nullable:
+ * its rate on the sample).  The paper leaves the number of hash buckets and
+ * the work per processor to tuning (Section 4, "Parameters"); this is that
+ * choice made by measurement.  A, B: host arrays of nprob descriptors as for
+ * crp_batch_create.  cache_path as for crp_autotune (key: device, sample
+ * size, terms per problem, mode).  Creates and destroys batches;
+ * synchronises. */
+crp_status crp_autotune_batch(const crp_plan_desc *base, int32_t nprob, const crp_sparse *A,
+                              const crp_sparse *B, int32_t sample_probs, const char *cache_path,
+                              crp_plan_desc *best, double *best_terms_per_s, void *stream);
 
 /* Library version string. */
 const char *crp_version(void);

@@ -19,7 +19,8 @@ Sections of the paper each function follows:
   outer product ``ab`` hashing into an interval ``L = [q, r)``
   -> :func:`hash_params`, :func:`side_hash`, :func:`partition_of`,
   :func:`interval_terms` (tests every pair; it does not use the two-pointer
-  scan, so that scan is checked against the definition).
+  scan, so that scan is checked against the definition),
+  :func:`partition_entries` (one partition's entries of a large product).
 * Preliminaries, Space-Saving, with weighted positive updates
   -> :func:`space_saving`; one summary per bucket (Figure 1, Section 6's
   many-bucket regime) -> :func:`partition_streams`, :func:`bucket_summaries`.
@@ -30,7 +31,9 @@ Sections of the paper each function follows:
   :func:`sketch_median`.
 * Section 6 (case study): support of a pair = number of transactions holding
   it, i.e. the entries above the diagonal of ``T^T T``; heaviest entries
-  -> :func:`topk`.
+  -> :func:`topk`; the heaviest pairs of a large ``T^T T`` from the exact
+  counts of the pairs of frequent items and the support bound
+  -> :func:`certified_topk_pairs`.
 * Not in the paper: the heavy-pair predictor (a 2 -> 64 -> 64 -> 1 network
   on the marginal counts of a prefix) -> :func:`mlp_forward`,
   :func:`mlp_loss_grad`, :func:`adam_step`, :func:`prefix_item_counts`,
@@ -387,6 +390,48 @@ def split_by_partition(prod: Product, P: int, seed_a: int, seed_b: int) -> list[
     return out
 
 
+def partition_entries(A: Compressed, B: Compressed, P: int, p: int, seed_a: int, seed_b: int,
+                      chunk: int = 1_000_000) -> Product:
+    """All entries of partition p, exactly, without the rest of the product
+    (FULL mode, {0,1} or real values).  A term a_k(i) b_k(j) lands in p when
+    ``h_b(j) = (p - h_a(i)) mod P`` (Lemma 1: the partition of a pair is fixed
+    by its two side hashes).  So for each outer product, every entry i of a_k
+    is joined with the entries j of b_k whose side hash equals its target:
+    the (k, h_b(j)) pairs of B are sorted once per chunk of outer products and
+    each (k, target) is looked up; equal (i, j) are then summed."""
+    lg = log2_exact(P)
+    n_cols = B.n_minor
+    keys_all, w_all = [], []
+    for k0 in range(0, A.n_major, chunk):
+        k1 = min(A.n_major, k0 + chunk)
+        a_lo, a_hi = int(A.ptr[k0]), int(A.ptr[k1])
+        b_lo, b_hi = int(B.ptr[k0]), int(B.ptr[k1])
+        ka = np.repeat(np.arange(k0, k1, dtype=np.int64), np.diff(A.ptr[k0:k1 + 1]))
+        kb = np.repeat(np.arange(k0, k1, dtype=np.int64), np.diff(B.ptr[k0:k1 + 1]))
+        ia = A.idx[a_lo:a_hi].astype(np.int64)
+        jb = B.idx[b_lo:b_hi].astype(np.int64)
+        va = np.ones(len(ia)) if A.val is None else A.val[a_lo:a_hi].astype(np.float64)
+        vb = np.ones(len(jb)) if B.val is None else B.val[b_lo:b_hi].astype(np.float64)
+        target = (p - side_hash(ia, seed_a, lg)) % P
+        bkey = kb * P + side_hash(jb, seed_b, lg)
+        order = np.argsort(bkey, kind="stable")
+        bkey, jb, vb = bkey[order], jb[order], vb[order]
+        akey = ka * P + target
+        lo = np.searchsorted(bkey, akey, side="left")
+        hi = np.searchsorted(bkey, akey, side="right")
+        cnt = hi - lo
+        rep = np.repeat(np.arange(len(ia)), cnt)
+        off = np.arange(int(cnt.sum())) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+        pos = np.repeat(lo, cnt) + off
+        keys_all.append(ia[rep] * n_cols + jb[pos])
+        w_all.append(va[rep] * vb[pos])
+    if keys_all:
+        uk, uw = _reduce(np.concatenate(keys_all), np.concatenate(w_all))
+    else:
+        uk, uw = np.zeros(0, np.int64), np.zeros(0)
+    return Product(uk // n_cols, uk % n_cols, uw, -1, n_cols)
+
+
 def partition_term_counts(A: Compressed, B: Compressed, P: int, seed_a: int, seed_b: int,
                           mode: int = FULL, chunk_terms: int = 20_000_000) -> np.ndarray:
     """Number of terms (not entries) of all outer products landing in each
@@ -445,6 +490,53 @@ def topk(i: np.ndarray, j: np.ndarray, w: np.ndarray, k: int, upper_only: bool =
         i, j, w = i[m], j[m], w[m]
     order = np.lexsort((j, i, -np.abs(w)))[:k]
     return i[order], j[order], w[order]
+
+
+def certified_topk_pairs(T: Compressed, k: int, n_hot: int = 2048, chunk: int = 2_000_000):
+    """The k heaviest pairs i < j of ``T^T T`` for a {0,1} matrix T (rows =
+    transactions), exactly, without the whole product.  Every entry satisfies
+    ``C(i,j) <= min(C(i,i), C(j,j))`` (a pair occurs only in transactions that
+    hold both items), so once the pairs among the n_hot most frequent items are
+    counted exactly (``H^T H`` with H the columns of those items, a sparse
+    matrix product, summed over chunks of transactions), any pair with an item
+    outside that set weighs at most the largest support outside it.  If the
+    k-th heaviest counted pair is heavier than that bound, the counted pairs'
+    top k (weight descending, then i, then j) is the product's top k;
+    otherwise n_hot doubles.  Returns (i, j, w, certificate dict)."""
+    import scipy.sparse as sp
+    deg = prefix_item_counts(T)
+    n = T.n_minor
+    while True:
+        h = min(n_hot, n)
+        hot = top_items(deg, h)
+        rank = np.full(n, -1, dtype=np.int64)
+        rank[hot] = np.arange(h)
+        C = np.zeros((h, h), dtype=np.int64)
+        K = T.n_major
+        for k0 in range(0, K, chunk):
+            k1 = min(K, k0 + chunk)
+            lo, hi = int(T.ptr[k0]), int(T.ptr[k1])
+            idx = T.idx[lo:hi].astype(np.int64)
+            row = np.repeat(np.arange(k1 - k0), np.diff(T.ptr[k0:k1 + 1]))
+            r = rank[idx]
+            m = r >= 0
+            H = sp.csr_matrix((np.ones(int(m.sum()), dtype=np.int64), (row[m], r[m])),
+                              shape=(k1 - k0, h))
+            C += (H.T @ H).toarray()
+        a, b = np.triu_indices(h, k=1)
+        i, j = hot[a], hot[b]
+        sw = np.where(i < j, 0, 1)          # order each pair as i < j
+        i, j = np.where(sw == 0, i, j), np.where(sw == 0, j, i)
+        w = C[a, b].astype(np.float64)
+        ti, tj, tw = topk(i, j, w, k)
+        outside = np.ones(n, dtype=bool)
+        outside[hot] = False
+        bound = float(deg[outside].max()) if outside.any() else 0.0
+        if len(tw) == k and tw[-1] > bound:
+            return ti, tj, tw, dict(n_hot=h, bound=bound, kth=float(tw[-1]))
+        if h >= n:
+            return ti, tj, tw, dict(n_hot=h, bound=bound, kth=float(tw[-1]) if len(tw) else 0.0)
+        n_hot *= 2
 
 
 # ---------------------------------------------------------------------------

@@ -118,6 +118,10 @@ _SIGS = {
                                     ctypes.POINTER(crp_sparse), ctypes.c_int64, ctypes.c_char_p,
                                     ctypes.POINTER(crp_plan_desc),
                                     ctypes.POINTER(ctypes.c_double), _P]),
+    "crp_autotune_batch": (ctypes.c_int, [ctypes.POINTER(crp_plan_desc), ctypes.c_int32, _P,
+                                          _P, ctypes.c_int32, ctypes.c_char_p,
+                                          ctypes.POINTER(crp_plan_desc),
+                                          ctypes.POINTER(ctypes.c_double), _P]),
     "crp_sketch_read": (ctypes.c_int, [_P, _P]),
     "crp_sketch_estimate": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int64, _P]),
     "crp_debug_hold_lock": (ctypes.c_int, [_P, ctypes.c_uint32]),
@@ -569,3 +573,24 @@ def autotune(A: DeviceSparse, B: DeviceSparse, n_rows: int, n_cols: int, seed_a:
               smem_slots=best.smem_slots, flags=best.flags, hot_items=best.hot_items,
               warm_items=best.warm_items)
     return kw, tps.value
+
+
+def autotune_batch(problems, seed_a: int, seed_b: int, mode: int = CRP_FULL,
+                   sample_probs: int = 256, cache_path: str | None = None, stream=None):
+    """Fastest (P, tile_vectors) of the batched launch for these problems
+    (crp_autotune_batch): returns (dict of Batch keyword arguments, terms/s on
+    the sample)."""
+    d = crp_plan_desc()
+    d.n_rows = d.n_cols = 1
+    d.P, d.seed_a, d.seed_b = 256, seed_a & (2**64 - 1), seed_b & (2**64 - 1)
+    d.value_type, d.mode = CRP_I32, mode
+    n = len(problems)
+    A = (crp_sparse * n)(*[a.c_struct() for a, _ in problems])
+    B = (crp_sparse * n)(*[b.c_struct() for _, b in problems])
+    best = crp_plan_desc()
+    tps = ctypes.c_double(0)
+    _check(lib().crp_autotune_batch(ctypes.byref(d), n, ctypes.cast(A, _P), ctypes.cast(B, _P),
+                                    sample_probs, cache_path.encode() if cache_path else None,
+                                    ctypes.byref(best), ctypes.byref(tps),
+                                    _stream_handle(stream)), "crp_autotune_batch")
+    return dict(P=best.P, tile_vectors=best.tile_vectors), tps.value

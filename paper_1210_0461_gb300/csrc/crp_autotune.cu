@@ -176,3 +176,89 @@ extern "C" crp_status crp_autotune(const crp_plan_desc *base, const crp_sparse *
     cache_store(cache_path, key, *best, best_tps);
     return CRP_OK;
 }
+
+// Batched products: the partition count and the outer products per work item
+// of the one persistent launch, timed on a sample of the problems (every
+// stride-th problem, so the sample spans the batch's sizes).  The cache key
+// is the device, the sample's problem count and its terms per problem
+// (log2 buckets) and the mode.
+extern "C" crp_status crp_autotune_batch(const crp_plan_desc *base, int32_t nprob,
+                                         const crp_sparse *A, const crp_sparse *B,
+                                         int32_t sample_probs, const char *cache_path,
+                                         crp_plan_desc *best, double *best_terms_per_s,
+                                         void *stream) {
+    if (!base || !A || !B || !best || nprob <= 0) {
+        set_last_error("crp_autotune_batch: bad argument");
+        return CRP_EINVAL;
+    }
+    *best = *base;
+    const int32_t ns = sample_probs > 0 && sample_probs < nprob ? sample_probs : nprob;
+    std::vector<crp_sparse> SA, SB;
+    for (int32_t x = 0; x < ns; ++x) {
+        const int64_t q = (int64_t)x * nprob / ns;
+        SA.push_back(A[q]);
+        SB.push_back(B[q]);
+    }
+    // terms of the sample, from the host copies of the vector lengths
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t terms = 0;
+    {
+        unsigned long long *d_t = nullptr;
+        if (cudaMalloc(&d_t, 8) != cudaSuccess) return CRP_ENOMEM;
+        for (int32_t x = 0; x < ns; ++x) {
+            unsigned long long t = 0;
+            if (SA[x].n_major > 0) {
+                launch_count_terms(SA[x].ptr, SB[x].ptr, SA[x].n_major, d_t, s);
+                cudaMemcpyAsync(&t, d_t, 8, cudaMemcpyDeviceToHost, s);
+                cudaStreamSynchronize(s);
+            }
+            terms += t;
+        }
+        cudaFree(d_t);
+    }
+    char key[320];
+    {
+        cudaDeviceProp prop;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaGetDeviceProperties(&prop, dev);
+        std::string name = prop.name;
+        for (auto &c : name) if (c == ' ') c = '_';
+        snprintf(key, sizeof key, "batch:%s:N%d:T%d:t%d:m%d", name.c_str(), ilog2u((uint64_t)ns),
+                 ilog2u(terms + 1), ilog2u(terms / (uint64_t)ns + 1), base->mode);
+    }
+    if (cache_lookup(cache_path, key, best, best_terms_per_s)) return CRP_OK;
+    const uint32_t Ps[] = {64, 256, 1024, 4096};
+    const uint32_t tiles[] = {16, 32, 64, 128};
+    double best_tps = -1.0;
+    for (uint32_t P : Ps) {
+        for (uint32_t t : tiles) {
+            crp_plan_desc d = *base;
+            d.P = P;
+            d.tile_vectors = t;
+            crp_batch *b = nullptr;
+            if (crp_batch_create(&b, &d, ns, SA.data(), SB.data(), 0, stream) != CRP_OK) continue;
+            double ms_best = 1e30;
+            bool ok = true;
+            for (int rep = 0; rep < 3 && ok; ++rep) {
+                double ms = 0;
+                ok = crp_batch_run(b) == CRP_OK && crp_batch_sync(b, &ms, nullptr) == CRP_OK;
+                if (ok && rep > 0 && ms > 0) ms_best = std::min(ms_best, ms);
+            }
+            crp_batch_destroy(b);
+            if (!ok || ms_best >= 1e29) continue;
+            const double tps = (double)terms / (ms_best * 1e-3);
+            if (tps > best_tps) {
+                best_tps = tps;
+                *best = d;
+            }
+        }
+    }
+    if (best_tps < 0) {
+        set_last_error("crp_autotune_batch: no candidate configuration ran");
+        return CRP_ECUDA;
+    }
+    if (best_terms_per_s) *best_terms_per_s = best_tps;
+    cache_store(cache_path, key, *best, best_tps);
+    return CRP_OK;
+}

@@ -94,3 +94,23 @@ def test_withheld_problem_times_out_then_completes(crp, problems):
     batch.sync()
     _check(batch, 3, _exact(problems[3], O.FULL))
     batch.close()
+
+
+def test_batch_autotuned_choice_is_bit_exact(crp, problems, tmp_path):
+    """crp_autotune_batch picks P and tile_vectors on a sample of the problems;
+    the batch built with its choice is bit-exact on every problem, and a
+    second call with the same cache file returns the cached choice."""
+    dev = [crp.to_device(T) for T in problems]
+    pairs = [(d, d) for d in dev]
+    cache = str(tmp_path / "tune.txt")
+    kw, tps = crp.autotune_batch(pairs, ci.SEED_A, ci.SEED_B, sample_probs=16, cache_path=cache)
+    assert kw["P"] in (64, 256, 1024, 4096) and kw["tile_vectors"] in (16, 32, 64, 128)
+    assert tps > 0
+    kw2, tps2 = crp.autotune_batch(pairs, ci.SEED_A, ci.SEED_B, sample_probs=16, cache_path=cache)
+    assert kw2 == kw and tps2 == tps
+    batch = crp.Batch(pairs, kw["P"], ci.SEED_A, ci.SEED_B, tile_vectors=kw["tile_vectors"])
+    batch.run()
+    batch.sync()
+    for q, T in enumerate(problems):
+        _check(batch, q, _exact(T, O.FULL))
+    batch.close()

@@ -1,10 +1,12 @@
 """Parity at the full size of the 10,000,000-transaction x 100,000-item
 co-occurrence workload, in the launch configuration bench.py times (routed,
-bins sized by the plan, hot block of 2048 items, warm stripes of 32 items):
+bins sized by the plan, hot block of 2048 items, warm stripes of 64 items):
 properties that hold at any size (every term stored exactly once, every
-entry in its own partition, the diagonal equal to the item supports), and
+entry in its own partition, the diagonal equal to the item supports),
 sampled entries -- present and absent -- computed one by one by the oracle
-from the definition of an entry as an inner product."""
+from the definition of an entry as an inner product, whole partitions
+against the oracle's entries of that partition, and the top 1000 pairs
+against the oracle's certified heaviest pairs of this input."""
 import numpy as np
 import pytest
 
@@ -25,7 +27,7 @@ def full():
     L = T.lengths().astype(np.int64)
     d = crp.to_device(T)
     plan = crp.Plan(T.n_minor, T.n_minor, P, ci.SEED_A, ci.SEED_B, groups=0,
-                    flags=crp.CRP_PLAN_ROUTED, hot_items=2048, warm_items=32, auto_grow=True)
+                    flags=crp.CRP_PLAN_ROUTED, hot_items=2048, warm_items=64, auto_grow=True)
     plan.accumulate(d, d)
     plan.sync()
     inv = O.Compressed.of(ci.transpose(T))   # item -> transactions (rows of A, columns of B)
@@ -87,3 +89,42 @@ def test_top_pairs(full):
         up = (i < j) & (w > tw[-1])
         for a, b in zip(i[up].tolist(), j[up].tolist()):
             assert a * T.n_minor + b in top
+
+
+def test_whole_partitions_equal_the_oracle(full):
+    """Two partitions, every entry: the oracle's partition_entries (the terms
+    whose side hashes put them in partition p, summed) against the export,
+    bit for bit -- offsetting errors inside a partition would show here."""
+    crp, T, L, plan, inv = full
+    Tc = O.Compressed.of(T)
+    for p in (0, 517):
+        want = O.partition_entries(Tc, Tc, P, p, ci.SEED_A, ci.SEED_B)
+        i, j, w, _ = plan.export(p, p + 1)
+        o = np.lexsort((j, i))
+        assert np.array_equal(i[o].astype(np.int64), want.i)
+        assert np.array_equal(j[o].astype(np.int64), want.j)
+        assert np.array_equal(w[o], want.w)
+
+
+def test_top1000_equals_the_oracle_certified_list(full):
+    """The returned top 1000 (pairs i < j) equal, in order, the oracle's
+    certified heaviest pairs of this very input (tests/golden/c2_top2000.txt,
+    written by tests/golden/make_topk_fixtures.py; the fixture records the
+    input's SHA-256)."""
+    import hashlib
+    import os
+    crp, T, L, plan, inv = full
+    path = os.path.join(os.path.dirname(__file__), "golden", "c2_top2000.txt")
+    rows, digest = [], None
+    for line in open(path):
+        if line.startswith("# input sha256 "):
+            digest = line.split()[-1]
+        elif line.strip() and not line.startswith("#"):
+            rows.append(tuple(int(x) for x in line.split()))
+    h = hashlib.sha256()
+    h.update(T.ptr.tobytes())
+    h.update(T.idx.tobytes())
+    assert h.hexdigest() == digest, "the generator made a different input"
+    ti, tj, tw, _ = plan.topk(1000, upper=True)
+    got = list(zip(ti.tolist(), tj.tolist(), [int(x) for x in tw]))
+    assert got == rows[:1000]

@@ -365,3 +365,34 @@ def test_topk_order_and_ties():
     assert list(zip(ti, tj, tw)) == [(2, 9, 9.), (1, 1, 7.), (1, 2, 7.), (3, 3, 7.)]
     ti, tj, tw = O.topk(i, j, w, 10, upper_only=True)
     assert list(zip(ti, tj)) == [(2, 9), (1, 2), (0, 4)]
+
+
+@pytest.mark.parametrize("k,n_hot", [(10, 16), (100, 64), (1000, 8), (1000, 4096)])
+def test_certified_topk_pairs_equals_brute_force(k, n_hot):
+    # against the whole exact product (UPPER) and its top k; n_hot = 8 cannot
+    # certify 1000 pairs, so the hot set grows until it does
+    T = O.Compressed.of(ci.C1.scaled(m=6000).generate())
+    ref = O.exact_product(T, T, O.UPPER)
+    ri, rj, rw = O.topk(ref.i, ref.j, ref.w, k)
+    gi, gj, gw, cert = O.certified_topk_pairs(T, k, n_hot, chunk=1000)
+    assert gi.tolist() == ri.tolist() and gj.tolist() == rj.tolist() and gw.tolist() == rw.tolist()
+    assert cert["kth"] > cert["bound"] or cert["n_hot"] >= T.n_minor
+    assert cert["n_hot"] >= min(n_hot, T.n_minor)
+
+
+@pytest.mark.parametrize("P,values", [(64, False), (8, True), (1, False), (1024, False)])
+def test_partition_entries_equal_the_split_product(P, values):
+    # every partition's entries, found by the side-hash join, against the
+    # whole product split by partition (and, with values, the fp64 sums)
+    if values:
+        rng = np.random.default_rng(3)
+        A = _rand_sparse(rng, 300, 40, 0.2, True, [(0, 0), (1, 40)])
+        B = _rand_sparse(rng, 300, 50, 0.2, True, [(0, 50), (2, 0)])
+    else:
+        A = B = O.Compressed.of(ci.C1.scaled(m=3000).generate())
+    parts = O.split_by_partition(O.exact_product(A, B, O.FULL), P, ci.SEED_A, ci.SEED_B)
+    for p in sorted(set([0, P - 1, P // 3, P // 2])):
+        got = O.partition_entries(A, B, P, p, ci.SEED_A, ci.SEED_B, chunk=777)
+        want = parts[p]
+        assert got.i.tolist() == want.i.tolist() and got.j.tolist() == want.j.tolist()
+        np.testing.assert_allclose(got.w, want.w, rtol=1e-12, atol=0)
