@@ -226,6 +226,12 @@ typedef struct {
     uint64_t launches;            /* kernels this plan has launched */
     double last_route_ms;         /* routed mode: device time of the routing
                                      phase within last_accumulate_ms */
+    uint64_t estimated_entries;   /* the nonzero entries of A B estimated
+                                     before the tables were sized (distinct
+                                     entries of one sampled partition group,
+                                     times the number of groups; Section 4,
+                                     "Parameters": estimating the size of the
+                                     output); 0 when not sampled */
 } crp_stats_t;
 
 /* Create a plan: validates desc, derives the hash parameters and allocates

@@ -62,7 +62,7 @@ class crp_stats_t(ctypes.Structure):
                 ("spilled", ctypes.c_uint64), ("full_partitions", ctypes.c_uint32),
                 ("P", ctypes.c_uint32), ("max_over_mean_terms", ctypes.c_double),
                 ("last_accumulate_ms", ctypes.c_double), ("launches", ctypes.c_uint64),
-                ("last_route_ms", ctypes.c_double)]
+                ("last_route_ms", ctypes.c_double), ("estimated_entries", ctypes.c_uint64)]
 
 
 _lock = threading.Lock()

@@ -173,6 +173,9 @@ struct crp_plan {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;
     bool timed = false, timed_mid = false;
     uint64_t launches = 0;
+    // distinct entries of the whole product estimated from the sampled
+    // partition group (0: the tables were not sized from a sample)
+    uint64_t est_entries = 0;
 };
 
 static bool is_pow2(uint64_t x) { return x && !(x & (x - 1)); }
@@ -682,6 +685,7 @@ static crp_status estimate_and_allocate(crp_plan *pl, const crp_sparse *A, const
             unsigned long long mx = 0, sum = 0;
             for (auto v : live) { mx = std::max(mx, v); sum += v; }
             distinct = std::max<uint64_t>((uint64_t)mx * P, (uint64_t)sum * Gs);
+            pl->est_entries = (uint64_t)sum * Gs;
         }
     }
     // target load per partition (default 60%)
@@ -1503,6 +1507,7 @@ extern "C" crp_status crp_stats(crp_plan *pl, crp_stats_t *out, uint64_t *terms_
     out->spilled = dc.spill_n;
     out->table_slots = pl->n_slots;
     out->launches = pl->launches;
+    out->estimated_entries = pl->est_entries;
     if (pl->timed) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, pl->ev0, pl->ev1) == cudaSuccess) out->last_accumulate_ms = ms;

@@ -56,7 +56,7 @@ def test_version_and_struct_sizes(libcrp):
     assert libcrp.crp_version().startswith(b"crp ")
     assert ctypes.sizeof(crp.crp_sparse) == 48
     assert ctypes.sizeof(crp.crp_plan_desc) == 104
-    assert ctypes.sizeof(crp.crp_stats_t) == 80
+    assert ctypes.sizeof(crp.crp_stats_t) == 88
 
 
 def test_struct_layouts_match_the_header(tmp_path):

@@ -391,3 +391,28 @@ def test_routed_pool_exhaustion_paths(crp, pool):
                     warm_items=warm, route_pool_chunks=pool)
         _check_exact(crp, plan, ref, 64)
         plan.close()
+
+
+@pytest.mark.parametrize("w,P,tol", [(ci.C2.scaled(m=300_000), 1024, 0.02),
+                                     (ci.C1.scaled(m=100_000), 64, 0.05)],
+                         ids=["10M-recipe-300k-prefix", "20k-recipe-100k"])
+def test_distinct_count_estimate_against_the_oracle(crp, w, P, tol):
+    """The tables are sized from an estimate of the product's distinct
+    entries: the entries of the partitions [0, P / G) (G = min(P, 64) groups)
+    counted exactly on the GPU, times G.  h is pairwise independent, so each
+    group holds ~1/G of the entries; against the oracle's exact count the
+    estimate is within `tol` (a few standard deviations of the sampled share:
+    16 partitions of ~40,000 entries, or one of ~20,000)."""
+    T = w.generate()
+    Tc = O.Compressed.of(T)
+    ref = O.exact_product(Tc, Tc, O.FULL)
+    d = crp.to_device(T)
+    plan = crp.Plan(T.n_minor, T.n_minor, P, ci.SEED_A, ci.SEED_B, flags=4, auto_grow=True)
+    plan.accumulate(d, d)
+    plan.sync()
+    st = plan.stats()
+    assert st["entries"] == len(ref.i)
+    est = st["estimated_entries"]
+    assert est > 0
+    assert abs(est - len(ref.i)) <= tol * len(ref.i), (est, len(ref.i))
+    plan.close()
