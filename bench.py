@@ -701,6 +701,8 @@ def run_c5(args, np, torch, crp, ci, stream):
     ms = _timed(step, args.steps, args.warmup, stream)
     ev_ms, ev_terms = batch.sync()
     entries = [batch.count(q) for q in range(len(Ts))]
+    batch.close()
+    del batch
     # the same launch with the fixed choice used before tuning (P 256, 32 outer
     # products per work item), for comparison
     fixed = crp.Batch([(x, x) for x in dev], 256, ci.SEED_A, ci.SEED_B, tile_vectors=32,
@@ -712,8 +714,6 @@ def run_c5(args, np, torch, crp, ci, stream):
     ms_fixed = _timed(step_fixed, args.steps, args.warmup, stream)
     fixed.close()
     del fixed
-    batch.close()
-    del batch
     # baseline: one plan per problem, launched back to back (plans built first,
     # each sized from its problem's entry count)
     plans = [crp.Plan(T.n_minor, T.n_minor, 256, ci.SEED_A, ci.SEED_B, flags=crp.CRP_PLAN_DIRECT,

@@ -895,12 +895,24 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
         set_dense_args(pl, RA.acc);
     }
     // the records this call routes (the terms outside the dense tiers) size
-    // the pool: an exact count in CRP_FULL mode, an upper bound otherwise
-    unsigned long long records = 0;
-    CRP_CUDA(launch_count_records(RA.acc, pl->d_scratch64, pl->stream));
-    CRP_CUDA(cudaMemcpyAsync(&records, pl->d_scratch64, 8, cudaMemcpyDeviceToHost, pl->stream));
+    // the pool: counted exactly on the first outer products (the sample the
+    // tiers were chosen from), their routed share of the terms scaled to all
+    // terms with a 10 % margin (a pool that still runs dry sends records to
+    // the overflow chunks, then straight to the tables)
+    const int64_t K = A->n_major;
+    const int64_t S = std::min<int64_t>(K, std::max<int64_t>(65536, K / 64));
+    AccumulateArgs sample = RA.acc;
+    sample.K = S;
+    unsigned long long cnt[3] = {0, 0, 0};   // sample records, sample terms, all terms
+    CRP_CUDA(launch_count_records(sample, pl->d_scratch64, pl->stream));
+    CRP_CUDA(launch_count_terms(A->ptr, B->ptr, S, pl->d_scratch64 + 1, pl->stream));
+    CRP_CUDA(launch_count_terms(A->ptr, B->ptr, K, pl->d_scratch64 + 2, pl->stream));
+    CRP_CUDA(cudaMemcpyAsync(cnt, pl->d_scratch64, 24, cudaMemcpyDeviceToHost, pl->stream));
     CRP_CUDA(cudaStreamSynchronize(pl->stream));
-    pl->launches += 1;
+    pl->launches += 3;
+    const double share = cnt[1] ? (double)cnt[0] / (double)cnt[1] : 1.0;
+    const uint64_t records =
+        std::min<uint64_t>(cnt[2], (uint64_t)(share * 1.1 * (double)cnt[2]) + 65536);
     st = routed_prepare(pl, records, RA);
     if (st != CRP_OK) return st;
     CRP_CUDA(cudaEventRecord(pl->ev0, pl->stream));

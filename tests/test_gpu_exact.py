@@ -394,15 +394,17 @@ def test_routed_pool_exhaustion_paths(crp, pool):
 
 
 @pytest.mark.parametrize("w,P,tol", [(ci.C2.scaled(m=300_000), 1024, 0.02),
-                                     (ci.C1.scaled(m=100_000), 64, 0.05)],
-                         ids=["10M-recipe-300k-prefix", "20k-recipe-100k"])
+                                     (ci.C2.scaled(m=100_000), 256, 0.05)],
+                         ids=["300k-tx-P1024", "100k-tx-P256"])
 def test_distinct_count_estimate_against_the_oracle(crp, w, P, tol):
     """The tables are sized from an estimate of the product's distinct
     entries: the entries of the partitions [0, P / G) (G = min(P, 64) groups)
     counted exactly on the GPU, times G.  h is pairwise independent, so each
     group holds ~1/G of the entries; against the oracle's exact count the
     estimate is within `tol` (a few standard deviations of the sampled share:
-    16 partitions of ~40,000 entries, or one of ~20,000)."""
+    16 partitions of ~40,000 entries, or 4 of ~60,000).  (Products with at
+    most 2^22 possible entries are not sampled: their tables are sized from
+    the bound.)"""
     T = w.generate()
     Tc = O.Compressed.of(T)
     ref = O.exact_product(Tc, Tc, O.FULL)
