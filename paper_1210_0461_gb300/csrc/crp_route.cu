@@ -488,6 +488,122 @@ k_apply(RouteArgs RA) {
     if (lane == 0 && applied) atomicAdd(&RA.acc.tv.dc->flushed, applied);
 }
 
+// The same apply phase with each chunk's records brought into shared memory
+// by the bulk-copy engine (cp.async.bulk, completion on an mbarrier), two
+// half-chunk buffers per warp: the copy of the next half is in flight while
+// the warp applies the current one.  Every wait is bounded; a wait that
+// gives up records a timeout and the warp stops (after waiting, again
+// bounded, for its copies in flight).
+constexpr bool kApplyBulk = true;
+constexpr uint32_t kHalfRecs = kChunkRecs / 2;
+constexpr uint32_t kHalfBytes = kHalfRecs * 8;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void bulk_issue(uint32_t buf, const void *src, uint32_t mbar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar),
+                 "r"(kHalfBytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(buf), "l"(src), "r"(kHalfBytes), "r"(mbar) : "memory");
+}
+
+// Bounded wait for an mbarrier phase (~0.5 s); false when it gave up.
+__device__ __forceinline__ bool bulk_wait(uint32_t mbar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+        __nanosleep(32);
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_apply_bulk(RouteArgs RA) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long *buf = (unsigned long long *)smem_raw + (size_t)warp * 2 * kHalfRecs;
+    __shared__ __align__(8) unsigned long long mbar_store[kWarps * 2];
+    const uint32_t mb0 = smem_addr(&mbar_store[2 * warp]), mb1 = smem_addr(&mbar_store[2 * warp + 1]);
+    const uint32_t b0 = smem_addr(buf), b1 = smem_addr(buf + kHalfRecs);
+    const unsigned long long *pool = (const unsigned long long *)RA.pool;
+    const unsigned int total = RA.start[RA.B];
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    auto grab = [&]() {
+        unsigned int item = 0;
+        if (lane == 0) item = atomicAdd(&RA.acc.tv.dc->work_next, 1u);
+        return __shfl_sync(kFull, item, 0);
+    };
+    unsigned long long applied = 0;
+    uint32_t ph0 = 0, ph1 = 0;
+    int in_flight0 = 0, in_flight1 = 0;
+    unsigned int item = grab();
+    if (item < total && lane == 0) {
+        const unsigned long long *c = pool + (size_t)RA.order[item] * kChunkRecs;
+        bulk_issue(b0, c, mb0);
+        bulk_issue(b1, c + kHalfRecs, mb1);
+    }
+    in_flight0 = in_flight1 = item < total;
+    bool ok = true;
+    while (item < total) {
+        // first half
+        if (!bulk_wait(mb0, ph0)) { ok = false; break; }
+        ph0 ^= 1u;
+        in_flight0 = 0;
+#pragma unroll 1
+        for (uint32_t x = lane; x < kHalfRecs; x += 32) {
+            const unsigned long long r = buf[x];
+            if (r == kEmptyKey) continue;
+            apply_record(RA, r);
+            ++applied;
+        }
+        __syncwarp();
+        const unsigned int next = grab();
+        if (next < total && lane == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            bulk_issue(b0, pool + (size_t)RA.order[next] * kChunkRecs, mb0);
+        }
+        in_flight0 = next < total;
+        // second half
+        if (!bulk_wait(mb1, ph1)) { ok = false; break; }
+        ph1 ^= 1u;
+        in_flight1 = 0;
+#pragma unroll 1
+        for (uint32_t x = lane; x < kHalfRecs; x += 32) {
+            const unsigned long long r = buf[kHalfRecs + x];
+            if (r == kEmptyKey) continue;
+            apply_record(RA, r);
+            ++applied;
+        }
+        __syncwarp();
+        if (next < total && lane == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            bulk_issue(b1, pool + (size_t)RA.order[next] * kChunkRecs + kHalfRecs, mb1);
+        }
+        in_flight1 = next < total;
+        item = next;
+    }
+    if (!ok) {
+        if (lane == 0) atomicOr(&RA.acc.tv.dc->status, kStatusTimeout);
+        // let the copies in flight land before the warp (and its buffers) go
+        if (in_flight0) bulk_wait(mb0, ph0);
+        if (in_flight1) bulk_wait(mb1, ph1);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) applied += __shfl_down_sync(kFull, applied, d);
+    if (lane == 0 && applied) atomicAdd(&RA.acc.tv.dc->flushed, applied);
+}
+
 size_t route_smem_bytes(uint32_t B, uint32_t core_H) {
     return (size_t)B * 12 + (size_t)core_H * (core_H + 1) * 4;
 }
@@ -533,7 +649,12 @@ cudaError_t launch_apply(const RouteArgs &RA, unsigned int *count, unsigned int 
     if (e != cudaSuccess) return e;
     RouteArgs AA = RA;
     AA.acc.tv.keep_in_l2 = 1;   // the current group's table lines outlast the records
-    if (RA.acc.tv.value_type == CRP_I32)
+    if (RA.acc.tv.value_type == CRP_I32 && kApplyBulk) {
+        const size_t sm = (size_t)kWarps * 2 * kHalfBytes;
+        e = cudaFuncSetAttribute(k_apply_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_apply_bulk<<<grid, kThreads, sm, s>>>(AA);
+    } else if (RA.acc.tv.value_type == CRP_I32)
         k_apply<CRP_I32><<<grid, kThreads, 0, s>>>(AA);
     else
         k_apply<CRP_F32_COMP><<<grid, kThreads, 0, s>>>(AA);
