@@ -809,8 +809,14 @@ def main():
     if args.autotune:
         t0 = time.time()
         if rank == 0:
+            # results are cached per kernel version in the temp directory, so a
+            # second run of the same command (under a profiler, say) times the
+            # same configuration
+            import tempfile
+            cache = os.path.join(tempfile.gettempdir(), f"crp_tune_{kernel_source_hash()}.txt")
             kw, tps = crp.autotune(dT, dT, T.n_minor, T.n_minor, ci.SEED_A, ci.SEED_B,
-                                   sample_vectors=min(args.autotune, T.n_major), stream=stream)
+                                   sample_vectors=min(args.autotune, T.n_major),
+                                   cache_path=cache, stream=stream)
         if world > 1:   # every rank runs rank 0's choice
             box = [(kw, tps) if rank == 0 else None]
             torch.distributed.broadcast_object_list(box, src=0)

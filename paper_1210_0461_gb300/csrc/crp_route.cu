@@ -524,7 +524,8 @@ __device__ __forceinline__ bool bulk_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
-__global__ void __launch_bounds__(kThreads, 2) k_apply_bulk(RouteArgs RA) {
+constexpr int kApplyBulkPerSM = 3;   // CTAs per SM (64 KB of stage buffers each)
+__global__ void __launch_bounds__(kThreads, kApplyBulkPerSM) k_apply_bulk(RouteArgs RA) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long *buf = (unsigned long long *)smem_raw + (size_t)warp * 2 * kHalfRecs;
@@ -653,7 +654,7 @@ cudaError_t launch_apply(const RouteArgs &RA, unsigned int *count, unsigned int 
         const size_t sm = (size_t)kWarps * 2 * kHalfBytes;
         e = cudaFuncSetAttribute(k_apply_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_apply_bulk<<<grid, kThreads, sm, s>>>(AA);
+        k_apply_bulk<<<grid / 2 * kApplyBulkPerSM, kThreads, sm, s>>>(AA);
     } else if (RA.acc.tv.value_type == CRP_I32)
         k_apply<CRP_I32><<<grid, kThreads, 0, s>>>(AA);
     else
