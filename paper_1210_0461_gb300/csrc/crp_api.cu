@@ -967,21 +967,31 @@ static crp_status select_hot_items(crp_plan *pl, const crp_sparse *A, const crp_
     int64_t ea = 0, eb = 0;
     CRP_CUDA(cudaMemcpyAsync(&ea, A->ptr + S, 8, cudaMemcpyDeviceToHost, s));
     CRP_CUDA(cudaMemcpyAsync(&eb, B->ptr + S, 8, cudaMemcpyDeviceToHost, s));
+    // A and B the same arrays (T^T T): one count and one selection serve
+    // both sides, the B side a copy of the A side's items and ranks
+    const bool mirror = A->idx == B->idx && A->ptr == B->ptr && pl->d.n_rows == pl->d.n_cols;
     CRP_CUDA(cudaMemsetAsync(pl->d_cnt_a, 0, (size_t)pl->d.n_rows * 4, s));
-    CRP_CUDA(cudaMemsetAsync(pl->d_cnt_b, 0, (size_t)pl->d.n_cols * 4, s));
+    if (!mirror) CRP_CUDA(cudaMemsetAsync(pl->d_cnt_b, 0, (size_t)pl->d.n_cols * 4, s));
     CRP_CUDA(cudaStreamSynchronize(s));
     CRP_CUDA(launch_item_counts(A->idx, ea, pl->d.n_rows, pl->d_cnt_a, s));
-    CRP_CUDA(launch_item_counts(B->idx, eb, pl->d.n_cols, pl->d_cnt_b, s));
-    pl->launches += 2;
+    if (!mirror) CRP_CUDA(launch_item_counts(B->idx, eb, pl->d.n_cols, pl->d_cnt_b, s));
+    pl->launches += mirror ? 1 : 2;
     if (pl->hot_R) {
         CRP_CUDA(select_top(pl->d_cnt_a, pl->d.n_rows, pl->hot_R, pl->d_items_a, pl->d_sel, s));
-        CRP_CUDA(select_top(pl->d_cnt_b, pl->d.n_cols, pl->hot_R, pl->d_items_b, pl->d_sel, s));
         // ranks in order of frequency: the lowest ranks are the heaviest items
         CRP_CUDA(order_by_count(pl->d_items_a, pl->d_cnt_a, pl->hot_R, s));
-        CRP_CUDA(order_by_count(pl->d_items_b, pl->d_cnt_b, pl->hot_R, s));
         CRP_CUDA(launch_hot_ranks(pl->d_rank_a, pl->d.n_rows, pl->d_items_a, pl->hot_R, s));
-        CRP_CUDA(launch_hot_ranks(pl->d_rank_b, pl->d.n_cols, pl->d_items_b, pl->hot_R, s));
-        pl->launches += 2 * 5 + 6;
+        if (mirror) {
+            CRP_CUDA(cudaMemcpyAsync(pl->d_items_b, pl->d_items_a, (size_t)pl->hot_R * 8,
+                                     cudaMemcpyDeviceToDevice, s));
+            CRP_CUDA(cudaMemcpyAsync(pl->d_rank_b, pl->d_rank_a, (size_t)pl->d.n_cols * 2,
+                                     cudaMemcpyDeviceToDevice, s));
+        } else {
+            CRP_CUDA(select_top(pl->d_cnt_b, pl->d.n_cols, pl->hot_R, pl->d_items_b, pl->d_sel, s));
+            CRP_CUDA(order_by_count(pl->d_items_b, pl->d_cnt_b, pl->hot_R, s));
+            CRP_CUDA(launch_hot_ranks(pl->d_rank_b, pl->d.n_cols, pl->d_items_b, pl->hot_R, s));
+        }
+        pl->launches += mirror ? 5 + 3 : 2 * 5 + 6;
         if (!pl->summary && pl->d.value_type == CRP_I32) {
             // degrees of every row and column over all calls since the reset:
             // the bound that lets crp_topk answer from the hot pairs
@@ -1012,10 +1022,18 @@ static crp_status select_hot_items(crp_plan *pl, const crp_sparse *A, const crp_
     }
     if (pl->warm_W) {
         CRP_CUDA(select_top(pl->d_cnt_a, pl->d.n_rows, pl->warm_W, pl->d_witems_a, pl->d_sel, s));
-        CRP_CUDA(select_top(pl->d_cnt_b, pl->d.n_cols, pl->warm_W, pl->d_witems_b, pl->d_sel, s));
         CRP_CUDA(launch_hot_ranks(pl->d_wrank_a, pl->d.n_rows, pl->d_witems_a, pl->warm_W, s));
-        CRP_CUDA(launch_hot_ranks(pl->d_wrank_b, pl->d.n_cols, pl->d_witems_b, pl->warm_W, s));
-        pl->launches += 2 * 5 + 4;
+        if (mirror) {
+            CRP_CUDA(cudaMemcpyAsync(pl->d_witems_b, pl->d_witems_a, (size_t)pl->warm_W * 8,
+                                     cudaMemcpyDeviceToDevice, s));
+            CRP_CUDA(cudaMemcpyAsync(pl->d_wrank_b, pl->d_wrank_a, (size_t)pl->d.n_cols * 2,
+                                     cudaMemcpyDeviceToDevice, s));
+        } else {
+            CRP_CUDA(select_top(pl->d_cnt_b, pl->d.n_cols, pl->warm_W, pl->d_witems_b, pl->d_sel,
+                                s));
+            CRP_CUDA(launch_hot_ranks(pl->d_wrank_b, pl->d.n_cols, pl->d_witems_b, pl->warm_W, s));
+        }
+        pl->launches += mirror ? 5 + 2 : 2 * 5 + 4;
     }
     return CRP_OK;
 }
