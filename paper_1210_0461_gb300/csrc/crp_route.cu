@@ -489,14 +489,18 @@ k_apply(RouteArgs RA) {
 }
 
 // The same apply phase with each chunk's records brought into shared memory
-// by the bulk-copy engine (cp.async.bulk, completion on an mbarrier), two
-// half-chunk buffers per warp: the copy of the next half is in flight while
-// the warp applies the current one.  Every wait is bounded; a wait that
-// gives up records a timeout and the warp stops (after waiting, again
-// bounded, for its copies in flight).
+// by the bulk-copy engine (cp.async.bulk, completion on an mbarrier).  A chunk
+// is read in pieces of kStageRecs records; each warp has two piece buffers, and
+// the copy of its next piece (of this chunk or of the next chunk it takes) is
+// in flight while it applies the current one.  Every wait is bounded; a wait
+// that gives up records a timeout and the warp stops (after waiting, again
+// bounded, for its copy in flight).
 constexpr bool kApplyBulk = true;
-constexpr uint32_t kHalfRecs = kChunkRecs / 2;
-constexpr uint32_t kHalfBytes = kHalfRecs * 8;
+constexpr uint32_t kStageRecs = 256;
+constexpr uint32_t kStageBytes = kStageRecs * 8;
+constexpr uint32_t kPiecesPerChunk = kChunkRecs / kStageRecs;
+constexpr int kApplyBulkPerSM = 3;   // CTAs per SM (2 x kStageBytes per warp each)
+static_assert(kChunkRecs % kStageRecs == 0 && kStageBytes % 16 == 0, "piece size");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -504,10 +508,10 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
 
 __device__ __forceinline__ void bulk_issue(uint32_t buf, const void *src, uint32_t mbar) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar),
-                 "r"(kHalfBytes) : "memory");
+                 "r"(kStageBytes) : "memory");
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(buf), "l"(src), "r"(kHalfBytes), "r"(mbar) : "memory");
+        ::"r"(buf), "l"(src), "r"(kStageBytes), "r"(mbar) : "memory");
 }
 
 // Bounded wait for an mbarrier phase (~0.5 s); false when it gave up.
@@ -524,81 +528,90 @@ __device__ __forceinline__ bool bulk_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
-constexpr int kApplyBulkPerSM = 3;   // CTAs per SM (64 KB of stage buffers each)
 __global__ void __launch_bounds__(kThreads, kApplyBulkPerSM) k_apply_bulk(RouteArgs RA) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long *buf = (unsigned long long *)smem_raw + (size_t)warp * 2 * kHalfRecs;
+    unsigned long long *buf = (unsigned long long *)smem_raw + (size_t)warp * 2 * kStageRecs;
     __shared__ __align__(8) unsigned long long mbar_store[kWarps * 2];
-    const uint32_t mb0 = smem_addr(&mbar_store[2 * warp]), mb1 = smem_addr(&mbar_store[2 * warp + 1]);
-    const uint32_t b0 = smem_addr(buf), b1 = smem_addr(buf + kHalfRecs);
+    // buffer b's mbarrier and shared address: base + b * step (kept in registers)
+    const uint32_t mb0 = smem_addr(&mbar_store[2 * warp]), sb0 = smem_addr(buf);
     const unsigned long long *pool = (const unsigned long long *)RA.pool;
     const unsigned int total = RA.start[RA.B];
     if (lane == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0 + 8) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
+    // a piece: (position in order[], piece of that chunk); item >= total: none
     auto grab = [&]() {
         unsigned int item = 0;
         if (lane == 0) item = atomicAdd(&RA.acc.tv.dc->work_next, 1u);
         return __shfl_sync(kFull, item, 0);
     };
+    auto issue = [&](int b, unsigned int item, uint32_t part) {
+        if (lane == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            bulk_issue(sb0 + b * kStageBytes,
+                       pool + (size_t)RA.order[item] * kChunkRecs + part * kStageRecs,
+                       mb0 + 8 * b);
+        }
+    };
     unsigned long long applied = 0;
-    uint32_t ph0 = 0, ph1 = 0;
-    int in_flight0 = 0, in_flight1 = 0;
-    unsigned int item = grab();
-    if (item < total && lane == 0) {
-        const unsigned long long *c = pool + (size_t)RA.order[item] * kChunkRecs;
-        bulk_issue(b0, c, mb0);
-        bulk_issue(b1, c + kHalfRecs, mb1);
+    uint32_t phases = 0u;   // bit b: the parity buffer b waits for next
+    unsigned int cur_item = grab(), nxt_item = 0;
+    uint32_t cur_part = 0, nxt_part = 0;
+    bool pending = false;   // the next piece's copy is in flight
+    if (cur_item < total) issue(0, cur_item, 0);
+    if (cur_item < total) {
+        nxt_item = kPiecesPerChunk > 1 ? cur_item : grab();
+        nxt_part = kPiecesPerChunk > 1 ? 1u : 0u;
+        if (nxt_item < total) {
+            issue(1, nxt_item, nxt_part);
+            pending = true;
+        }
     }
-    in_flight0 = in_flight1 = item < total;
+    int b = 0;
     bool ok = true;
-    while (item < total) {
-        // first half
-        if (!bulk_wait(mb0, ph0)) { ok = false; break; }
-        ph0 ^= 1u;
-        in_flight0 = 0;
+    while (cur_item < total) {
+        if (!bulk_wait(mb0 + 8 * b, (phases >> b) & 1u)) { ok = false; break; }
+        phases ^= 1u << b;
+        const unsigned long long *rec = buf + b * kStageRecs;
 #pragma unroll 1
-        for (uint32_t x = lane; x < kHalfRecs; x += 32) {
-            const unsigned long long r = buf[x];
+        for (uint32_t x = lane; x < kStageRecs; x += 32) {
+            const unsigned long long r = rec[x];
             if (r == kEmptyKey) continue;
             apply_record(RA, r);
             ++applied;
         }
         __syncwarp();
-        const unsigned int next = grab();
-        if (next < total && lane == 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            bulk_issue(b0, pool + (size_t)RA.order[next] * kChunkRecs, mb0);
+        // the piece after the next one goes into the buffer just freed
+        cur_item = nxt_item;
+        cur_part = nxt_part;
+        const bool had_next = pending;
+        pending = false;
+        if (had_next) {
+            if (cur_part + 1 < kPiecesPerChunk) {
+                nxt_item = cur_item;
+                nxt_part = cur_part + 1;
+            } else {
+                nxt_item = grab();
+                nxt_part = 0;
+            }
+            if (nxt_item < total) {
+                issue(b, nxt_item, nxt_part);
+                pending = true;
+            }
+        } else {
+            cur_item = total;   // nothing was in flight: done
         }
-        in_flight0 = next < total;
-        // second half
-        if (!bulk_wait(mb1, ph1)) { ok = false; break; }
-        ph1 ^= 1u;
-        in_flight1 = 0;
-#pragma unroll 1
-        for (uint32_t x = lane; x < kHalfRecs; x += 32) {
-            const unsigned long long r = buf[kHalfRecs + x];
-            if (r == kEmptyKey) continue;
-            apply_record(RA, r);
-            ++applied;
-        }
-        __syncwarp();
-        if (next < total && lane == 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            bulk_issue(b1, pool + (size_t)RA.order[next] * kChunkRecs + kHalfRecs, mb1);
-        }
-        in_flight1 = next < total;
-        item = next;
+        b ^= 1;
     }
     if (!ok) {
         if (lane == 0) atomicOr(&RA.acc.tv.dc->status, kStatusTimeout);
         // let the copies in flight land before the warp (and its buffers) go
-        if (in_flight0) bulk_wait(mb0, ph0);
-        if (in_flight1) bulk_wait(mb1, ph1);
+        bulk_wait(mb0 + 8 * b, (phases >> b) & 1u);
+        if (pending) bulk_wait(mb0 + 8 * (b ^ 1), (phases >> (b ^ 1)) & 1u);
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) applied += __shfl_down_sync(kFull, applied, d);
@@ -651,7 +664,7 @@ cudaError_t launch_apply(const RouteArgs &RA, unsigned int *count, unsigned int 
     RouteArgs AA = RA;
     AA.acc.tv.keep_in_l2 = 1;   // the current group's table lines outlast the records
     if (RA.acc.tv.value_type == CRP_I32 && kApplyBulk) {
-        const size_t sm = (size_t)kWarps * 2 * kHalfBytes;
+        const size_t sm = (size_t)kWarps * 2 * kStageBytes;
         e = cudaFuncSetAttribute(k_apply_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         k_apply_bulk<<<grid / 2 * kApplyBulkPerSM, kThreads, sm, s>>>(AA);
