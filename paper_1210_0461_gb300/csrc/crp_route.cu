@@ -6,8 +6,8 @@
 // matters is the 126 MB L2, shared by all SMs: random atomics into an
 // L2-resident region run several times faster than into HBM.  So:
 //
-//  1. k_route enumerates every term once (one row of a_k per lane, the
-//     columns of b_k in turn).  Terms of hot and warm items go to the dense
+//  1. k_route enumerates every term once (blocks of up to 32 x 32 terms of
+//     a_k b_k staged in shared memory, 32 terms per warp step).  Terms of hot and warm items go to the dense
 //     counters; every other term becomes a record appended to the bin of its
 //     partition group b = h(i,j) >> shift.  (Pairs of the most frequent
 //     items count first in per-CTA shared-memory counters, added into the
@@ -140,31 +140,6 @@ __device__ __forceinline__ void bin_append(const RouteArgs &RA, unsigned long lo
     overflow_append(RA, r);
 }
 
-// Row-per-lane enumeration of the terms of a_k b_k.  A warp holds a batch of
-// up to 32 entries of a_k (one per lane; a batch of L < 32 rows is held
-// G = 32 / L times, so G columns run per step) and a batch of up to 32
-// entries of b_k, each with its side hash and dense-tier ranks.  A step
-// pairs every row with column m + sub of the batch, taking the column's
-// values from its lane by shuffle.  The warp takes tiles of outer products
-// from a global counter, so warps never wait on each other for work.
-struct RowLane {
-    int64_t k;                    // current outer product
-    int64_t a0, b0;               // first entries of a_k and b_k
-    int32_t left;                 // outer products left in the tile after k
-    int32_t na, nb;               // lengths of a_k and b_k
-    int32_t abase, bbase;         // first row / column of the batches (offsets in a_k, b_k)
-    int32_t m, mcount, G;         // next column of the batch, its size, columns per step
-    bool done;
-    // this lane's row of the batch
-    uint32_t i, ha, rank, wrank;
-    float wa;
-    int32_t sub, rpos;            // column offset within a step; row position in a_k
-    bool va;
-    // this lane's entry of the column batch (j = ~0u: none)
-    uint32_t jl, hbl, rwl;        // rwl: hot rank | warm rank << 16 (0xFFFF: none)
-    float bl;
-};
-
 // An input index read that does not allocate in L1 (L1 keeps the rank
 // arrays of the dense tiers; the index arrays stream through once).
 __device__ __forceinline__ uint32_t ld_idx(const int32_t *p) {
@@ -173,76 +148,96 @@ __device__ __forceinline__ uint32_t ld_idx(const int32_t *p) {
     return v;
 }
 
-__device__ __forceinline__ void rl_load_rows(RowLane &st, const AccumulateArgs &A, int lane) {
-    const int32_t L = min(32, st.na - st.abase);
-    st.G = 32 / L;
-    st.sub = lane / L;
-    st.rpos = st.abase + (lane - st.sub * L);
-    const int64_t x = st.a0 + st.rpos;
-    st.va = false;
-    st.i = 0;
-    st.ha = 0;
-    st.rank = st.wrank = 0xFFFFu;
-    st.wa = 1.0f;
-    if (st.sub < st.G) {
+// Flattened enumeration of the terms of a_k b_k: a block of up to 32 entries
+// of a_k (rows) and 32 of b_k (columns), with their side hashes, dense-tier
+// ranks and values, is staged in the warp's shared memory, and the lanes take
+// the block's mr x mc terms in order, 32 per step (term t: row t / mc, column
+// t mod mc), so every lane has a term in every step but a block's last --
+// where one row per lane left a lane idle for every row short of 32 (c2's
+// vectors hold ~20 entries).  The warp takes tiles of outer products from a
+// global counter, so warps never wait on each other for work.
+// Shared memory of a route CTA: per bin its open chunk (u64) and spare (u32),
+// the core counters, then (flattened enumeration) 64 staged entries per warp.
+__host__ __device__ __forceinline__ size_t route_stage_offset(uint32_t B, uint32_t core_H) {
+    return ((size_t)B * 12 + (size_t)core_H * (core_H + 1) * 4 + 15) & ~(size_t)15;
+}
+struct RowData { uint32_t i, ha, ranks; float w; };   // i = ~0u: no row; ranks: hot | warm << 16
+struct ColData { uint32_t j, hb, ranks; float w; };   // j = ~0u: no column
+struct FlatState {
+    int64_t k, a0, b0;
+    int32_t left, na, nb;
+    int32_t abase, bbase;   // first row / column of the block (offsets in a_k, b_k)
+    int32_t mr, mc, q;      // block size; first term of the next step
+    uint32_t inv_mc;        // ceil(2^16 / mc): t / mc = (t inv_mc) >> 16 for t < 1024
+    bool done;
+};
+
+__device__ __forceinline__ void fl_load_rows(FlatState &st, const AccumulateArgs &A, int lane,
+                                             RowData *rows) {
+    __syncwarp();   // the previous block has been read by every lane
+    st.mr = min(32, st.na - st.abase);
+    if (lane < st.mr) {
+        const int64_t x = st.a0 + st.abase + lane;
         const uint32_t i = ld_idx(A.a_idx + x);
+        RowData d = {~0u, 0u, 0xFFFFFFFFu, 1.0f};
         if (i < (uint32_t)A.n_rows) {
-            st.va = true;
-            st.i = i;
-            st.ha = side_hash(A.hp.ha, i);
-            if (A.hot_rank_a) st.rank = __ldg(A.hot_rank_a + i);
-            if (A.warm_rank_a) st.wrank = __ldg(A.warm_rank_a + i);
-            if (A.a_val) st.wa = __ldg(A.a_val + x);
+            d.i = i;
+            d.ha = side_hash(A.hp.ha, i);
+            const uint32_t r = A.hot_rank_a ? __ldg(A.hot_rank_a + i) : 0xFFFFu;
+            const uint32_t w = A.warm_rank_a ? __ldg(A.warm_rank_a + i) : 0xFFFFu;
+            d.ranks = r | (w << 16);
+            if (A.a_val) d.w = __ldg(A.a_val + x);
         } else if (A.debug_checks) {
             atomicOr(&A.tv.dc->status, kStatusBadIndex);
         }
+        rows[lane] = d;
     }
+    __syncwarp();
 }
 
-__device__ __forceinline__ void rl_load_cols(RowLane &st, const AccumulateArgs &A, int lane) {
-    st.mcount = min(32, st.nb - st.bbase);
-    st.m = 0;
-    st.jl = ~0u;
-    st.hbl = 0;
-    st.rwl = 0xFFFFFFFFu;
-    st.bl = 1.0f;
-    if (lane < st.mcount) {
+__device__ __forceinline__ void fl_load_cols(FlatState &st, const AccumulateArgs &A, int lane,
+                                             ColData *cols) {
+    __syncwarp();
+    st.mc = min(32, st.nb - st.bbase);
+    st.inv_mc = (65536u + (uint32_t)st.mc - 1u) / (uint32_t)st.mc;
+    st.q = 0;
+    if (lane < st.mc) {
         const int64_t y = st.b0 + st.bbase + lane;
         const uint32_t j = ld_idx(A.b_idx + y);
+        ColData d = {~0u, 0u, 0xFFFFFFFFu, 1.0f};
         if (j < (uint32_t)A.n_cols) {
-            st.jl = j;
-            st.hbl = side_hash(A.hp.hb, j);
-            const uint32_t rb = A.hot_rank_b ? __ldg(A.hot_rank_b + j) : 0xFFFFu;
-            const uint32_t wb = A.warm_rank_b ? __ldg(A.warm_rank_b + j) : 0xFFFFu;
-            st.rwl = rb | (wb << 16);
-            if (A.b_val) st.bl = __ldg(A.b_val + y);
+            d.j = j;
+            d.hb = side_hash(A.hp.hb, j);
+            const uint32_t r = A.hot_rank_b ? __ldg(A.hot_rank_b + j) : 0xFFFFu;
+            const uint32_t w = A.warm_rank_b ? __ldg(A.warm_rank_b + j) : 0xFFFFu;
+            d.ranks = r | (w << 16);
+            if (A.b_val) d.w = __ldg(A.b_val + y);
         } else if (A.debug_checks) {
             atomicOr(&A.tv.dc->status, kStatusBadIndex);
         }
+        cols[lane] = d;
     }
+    __syncwarp();
 }
 
-// First column of the batch for the current row batch: with T^T T above the
-// diagonal on sorted lists, only columns after the batch's first row.
-__device__ __forceinline__ int32_t rl_col_start(const RowLane &st, const AccumulateArgs &A) {
-    return A.sym_upper ? st.abase + 1 : 0;
-}
-
-// Make (m < mcount) hold for a loaded row and column batch; false when the
-// warp's work is exhausted.  Warp-uniform.
-__device__ __forceinline__ bool rl_advance(RowLane &st, const AccumulateArgs &A, int lane) {
+// Make (q < mr mc) hold for a staged block; false when the warp's work is
+// exhausted.  Warp-uniform.
+__device__ __forceinline__ bool fl_advance(FlatState &st, const AccumulateArgs &A, int lane,
+                                           RowData *rows, ColData *cols) {
     while (true) {
-        if (st.m < st.mcount) return true;
+        if (st.q < st.mr * st.mc) return true;
         if (st.abase < st.na) {
             st.bbase += 32;
             if (st.bbase >= st.nb) {
                 st.abase += 32;
                 if (st.abase >= st.na) continue;
-                rl_load_rows(st, A, lane);
-                st.bbase = rl_col_start(st, A);
-                if (st.bbase >= st.nb) { st.mcount = 0; st.m = 0; continue; }
+                fl_load_rows(st, A, lane, rows);
+                // with T^T T above the diagonal on sorted lists, only columns
+                // after the block's first row
+                st.bbase = A.sym_upper ? st.abase + 1 : 0;
+                if (st.bbase >= st.nb) { st.mc = 0; st.q = 0; continue; }
             }
-            rl_load_cols(st, A, lane);
+            fl_load_cols(st, A, lane, cols);
             continue;
         }
         if (st.left > 0) {
@@ -261,13 +256,13 @@ __device__ __forceinline__ bool rl_advance(RowLane &st, const AccumulateArgs &A,
         st.b0 = __ldg(A.b_ptr + st.k);
         st.nb = (int32_t)(__ldg(A.b_ptr + st.k + 1) - st.b0);
         st.abase = st.na;                       // inactive until both sides are non-empty
-        st.mcount = st.m = 0;
+        st.mr = st.mc = st.q = 0;
         if (st.na == 0 || st.nb == 0) continue;
         st.abase = 0;
-        rl_load_rows(st, A, lane);
-        st.bbase = rl_col_start(st, A);
+        fl_load_rows(st, A, lane, rows);
+        st.bbase = A.sym_upper ? 1 : 0;
         if (st.bbase >= st.nb) continue;
-        rl_load_cols(st, A, lane);
+        fl_load_cols(st, A, lane, cols);
     }
 }
 
@@ -290,50 +285,56 @@ __global__ void __launch_bounds__(kRouteThreads, 1) k_route(RouteArgs RA) {
     const uint32_t pmask = A.hp.ha.mask;
     const bool filter = A.part_lo != 0u || A.part_hi != 0xFFFFFFFFu;
     uint32_t my_terms = 0;   // terms of this lane (fewer than 2^32 per thread)
-    RowLane st;
-    st.k = st.a0 = st.b0 = 0;
-    st.left = st.na = st.nb = st.abase = st.bbase = 0;
-    st.m = st.mcount = 0;
-    st.G = 1;
-    st.done = false;
-    while (rl_advance(st, A, lane)) {
-        const int32_t c = st.m + st.sub;
-        const int src = c & 31;
-        const uint32_t j = __shfl_sync(kFull, st.jl, src);
-        const uint32_t hb = __shfl_sync(kFull, st.hbl, src);
-        const uint32_t rw = __shfl_sync(kFull, st.rwl, src);
-        const uint32_t rb = rw & 0xFFFFu, wbk = rw >> 16;
-        float bv = 1.0f;
-        if constexpr (VT != CRP_I32) bv = __shfl_sync(kFull, st.bl, src);
-        const int32_t cpos = st.bbase + c;
-        st.m += st.G;
-        bool valid = st.va && c < st.mcount && j != ~0u;
-        if (A.mode == CRP_UPPER && !(st.i < j)) valid = false;
-        if (A.sym_upper && cpos <= st.rpos) valid = false;
-        const uint32_t p = (st.ha + hb) & pmask;
+    // this warp's staged block: 32 rows then 32 columns
+    RowData *rows = (RowData *)(smem_raw + route_stage_offset(RA.B, H)) + warp * 64;
+    ColData *cols = (ColData *)(rows + 32);
+    FlatState fs;
+    fs.k = fs.a0 = fs.b0 = 0;
+    fs.left = fs.na = fs.nb = fs.abase = fs.bbase = 0;
+    fs.mr = fs.mc = fs.q = 0;
+    fs.inv_mc = 0;
+    fs.done = false;
+    while (fl_advance(fs, A, lane, rows, cols)) {
+        const int32_t t = fs.q + lane;
+        const int32_t nt = fs.mr * fs.mc;
+        fs.q += 32;
+        int32_t r = 0, c = 0;
+        if (t < nt) {
+            r = (int32_t)(((uint32_t)t * fs.inv_mc) >> 16);
+            c = t - r * fs.mc;
+        }
+        const RowData rd = rows[r];
+        const ColData cd = cols[c];
+        const uint32_t i = rd.i, j = cd.j;
+        bool valid = t < nt && i != ~0u && j != ~0u;
+        if (A.mode == CRP_UPPER && !(i < j)) valid = false;
+        if (A.sym_upper && fs.bbase + c <= fs.abase + r) valid = false;
+        const uint32_t p = (rd.ha + cd.hb) & pmask;
         if (filter && (p < A.part_lo || p >= A.part_hi)) valid = false;
         my_terms += valid ? 1 : 0;
         if (VT == CRP_I32 && valid) {
-            if (st.rank < A.hot_R && rb < A.hot_R) {
-                if (st.rank < H && rb < H) atomicAdd(&core[st.rank * Hp + rb], 1u);
-                else atomicAdd(&A.hot_block[st.rank * A.hot_R + rb], 1u);
+            const uint32_t rank = rd.ranks & 0xFFFFu, wrank = rd.ranks >> 16;
+            const uint32_t rb = cd.ranks & 0xFFFFu, wbk = cd.ranks >> 16;
+            if (rank < A.hot_R && rb < A.hot_R) {
+                if (rank < H && rb < H) atomicAdd(&core[rank * Hp + rb], 1u);
+                else atomicAdd(&A.hot_block[rank * A.hot_R + rb], 1u);
                 valid = false;
-            } else if (st.wrank < A.warm_W) {
-                atomicAdd(&A.warm_a[(size_t)st.wrank * A.n_cols + j], 1u);
+            } else if (wrank < A.warm_W) {
+                atomicAdd(&A.warm_a[(size_t)wrank * A.n_cols + j], 1u);
                 valid = false;
             } else if (wbk < A.warm_W) {
-                atomicAdd(&A.warm_b[(size_t)wbk * A.n_rows + st.i], 1u);
+                atomicAdd(&A.warm_b[(size_t)wbk * A.n_rows + i], 1u);
                 valid = false;
             }
         }
         if (valid) {
             R rec;
             if constexpr (VT == CRP_I32) {
-                rec = make_key(st.i, j);
+                rec = make_key(i, j);
             } else {
-                rec.key = make_key(st.i, j);
-                rec.p = __fmul_rn(st.wa, bv);
-                rec.e = __fmaf_rn(st.wa, bv, -rec.p);
+                rec.key = make_key(i, j);
+                rec.p = __fmul_rn(rd.w, cd.w);
+                rec.e = __fmaf_rn(rd.w, cd.w, -rec.p);
             }
             bin_append(RA, cur, nxt, p >> RA.B_shift, rec);
         }
@@ -619,7 +620,8 @@ __global__ void __launch_bounds__(kThreads, kApplyBulkPerSM) k_apply_bulk(RouteA
 }
 
 size_t route_smem_bytes(uint32_t B, uint32_t core_H) {
-    return (size_t)B * 12 + (size_t)core_H * (core_H + 1) * 4;
+    return route_stage_offset(B, core_H) +
+           (size_t)kRouteWarps * 32 * (sizeof(RowData) + sizeof(ColData));
 }
 
 cudaError_t launch_route(const RouteArgs &RA, int grid, cudaStream_t s) {
