@@ -176,7 +176,7 @@ typedef struct {
                                      at the end of the call.  R <= 4096. */
     uint32_t target_load_pct;     /* exact tables sized by the library: at most
                                      this % of a partition's slots occupied per
-                                     the estimate (0 = 60; <= 90) */
+                                     the estimate (0 = 65; <= 90) */
     uint32_t part_begin, part_end;/* the plan's interval [q, r) of partitions
                                      (Figure 1, CRoP run on one interval;
                                      Theorem 1's K instances use disjoint equal

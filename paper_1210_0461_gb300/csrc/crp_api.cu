@@ -688,8 +688,9 @@ static crp_status estimate_and_allocate(crp_plan *pl, const crp_sparse *A, const
             pl->est_entries = (uint64_t)sum * Gs;
         }
     }
-    // target load per partition (default 60%)
-    const double load = pl->d.target_load_pct ? pl->d.target_load_pct / 100.0 : 0.6;
+    // target load per partition (default 65%: capacities are powers of two, so
+    // the tables hold between a third and two thirds of their slots)
+    const double load = pl->d.target_load_pct ? pl->d.target_load_pct / 100.0 : 0.65;
     uint64_t per = (uint64_t)((double)distinct / P / load) + 64;
     return alloc_tables(pl, per);
 }
