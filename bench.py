@@ -297,10 +297,15 @@ def run_other(args):
             plan.sync()
             plan.topk(1000, upper=True)
         ms = _timed(step, args.steps, args.warmup, stream)
+        acc_ms = plan.timing()[0]
+        entries = plan.stats()["entries"]
+        cpu = None if args.no_cpu else cpu_baseline(T, args.cpu_seconds)
         _line(terms / (ms / 1e3), ms, args, "i32",
               {"workload": "c1: 20000 transactions x 1000 items, Poisson(10) in [2,40], "
                            "Zipf(1.1); exact T^T T, P = 64, direct updates",
-               "terms_per_step": terms, "accumulate_ms": plan.timing()[0]})
+               "terms_per_step": terms, "accumulate_ms": acc_ms, "entries": entries},
+              {"cpu_baseline": cpu,
+               "roofline": _roofline(terms, d.nbytes(), entries, acc_ms, "k_accumulate (direct)")})
     elif args.workload == "c3":
         run_c3(args, np, torch, crp, ci, stream)
     elif args.workload == "c4":
