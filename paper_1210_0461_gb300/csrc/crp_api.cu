@@ -162,6 +162,11 @@ struct crp_plan {
     unsigned long long *d_deg_a = nullptr, *d_deg_b = nullptr;
     bool deg_b_mirrors_a = true;   // every call since the reset had B == A: d_deg_b unused
     TopkCand *d_hot_cand = nullptr;
+    // top-k scratch kept across calls
+    TopkCand *d_cand_keep = nullptr, *d_cand_sel = nullptr, *d_cand_tmp = nullptr;
+    uint64_t cand_keep_cap = 0, cand_sel_cap = 0, cand_tmp_cap = 0;
+    unsigned char *d_topk_stage = nullptr;
+    uint64_t topk_stage_cap = 0;
     uint64_t topk_certified = 0;
     // locked-bucket summaries: a lock word per partition
     bool locked = false;
@@ -437,6 +442,10 @@ extern "C" void crp_plan_destroy(crp_plan *pl) {
     cudaFree(pl->d_deg_a);
     cudaFree(pl->d_deg_b);
     cudaFree(pl->d_hot_cand);
+    cudaFree(pl->d_cand_keep);
+    cudaFree(pl->d_cand_sel);
+    cudaFree(pl->d_cand_tmp);
+    cudaFree(pl->d_topk_stage);
     if (pl->ev0) cudaEventDestroy(pl->ev0);
     if (pl->ev1) cudaEventDestroy(pl->ev1);
     if (pl->evm) cudaEventDestroy(pl->evm);
@@ -1265,6 +1274,19 @@ static bool is_device_ptr(const void *p) {
 // The k heaviest of n_c candidates (an MSD radix select first when more than
 // one CTA can sort), sorted and written out; *n_out = entries written and
 // *kth_w (nullable) = the weight of the last one.  cand stays the caller's.
+// Grow a plan-owned scratch buffer (kept across calls: an allocation and a
+// free per top-k call would each synchronise the device).
+template <typename T>
+static crp_status plan_scratch(T *&buf, uint64_t &cap, uint64_t need) {
+    if (need <= cap) return CRP_OK;
+    cudaFree(buf);
+    buf = nullptr;
+    cap = 0;
+    CRP_CUDA(cudaMalloc(&buf, need * sizeof(T)));
+    cap = need;
+    return CRP_OK;
+}
+
 static crp_status topk_from_candidates(crp_plan *pl, const TopkCand *cand, uint64_t n_c, int32_t k,
                                        int32_t *i_out, int32_t *j_out, double *w_out,
                                        double *w_lower, int32_t *n_out, double *kth_w) {
@@ -1277,58 +1299,89 @@ static crp_status topk_from_candidates(crp_plan *pl, const TopkCand *cand, uint6
             st = fail(CRP_ECUDA, std::string("topk: ") + cudaGetErrorString(e));
         return st == CRP_OK;
     };
-    TopkCand *sel = nullptr, *keep = nullptr;
     const TopkCand *final_c = cand;
     unsigned int final_sort = (unsigned int)n_c;  // candidates to sort
     unsigned int final_n = (unsigned int)std::min<uint64_t>(n_c, (uint64_t)k);
-    if (st == CRP_OK && n_c > (uint64_t)kTopkSortMax) {
-        // MSD radix select on the candidates down to exactly k
-        cuda_ok(cudaMalloc(&sel, (size_t)k * sizeof(TopkCand)));
-        cuda_ok(cudaMalloc(&keep, n_c * sizeof(TopkCand)));
-        TopkCand *und = const_cast<TopkCand *>(cand), *nxt = keep;
-        unsigned int n_und = (unsigned int)n_c, n_sel = 0, need = (unsigned int)k;
-        cuda_ok(cudaMemsetAsync(cnt + 1, 0, 4, s));  // sel count
-        for (int d = 0; d < 16 && st == CRP_OK && need > 0; ++d) {
-            unsigned int h[256];
-            cuda_ok(launch_topk_digit_hist(und, n_und, d, dhist, s));
-            cuda_ok(cudaMemcpyAsync(h, dhist, sizeof h, cudaMemcpyDeviceToHost, s));
-            cuda_ok(cudaStreamSynchronize(s));
-            if (st != CRP_OK) break;
-            unsigned int above = 0;
-            int pivot = 255;
-            for (; pivot >= 0; --pivot) {
-                if (above + h[pivot] >= need) break;
-                above += h[pivot];
-            }
-            cuda_ok(launch_topk_digit_split(und, n_und, d, (unsigned)pivot, sel, cnt + 1, nxt,
-                                            cnt + 2, s));
-            pl->launches += 2;
-            unsigned int kn = 0;
-            cuda_ok(cudaMemcpyAsync(&kn, cnt + 2, 4, cudaMemcpyDeviceToHost, s));
-            cuda_ok(cudaStreamSynchronize(s));
-            n_sel += above;
-            need -= above;
-            std::swap(und, nxt);
-            n_und = kn;
-            if (n_und == need) {  // everything left at this prefix is in
-                cuda_ok(cudaMemcpyAsync(sel + n_sel, und, (size_t)n_und * sizeof(TopkCand),
-                                        cudaMemcpyDeviceToDevice, s));
-                n_sel += n_und;
-                need = 0;
-            }
+    if (n_c > (uint64_t)kTopkSortMax) {
+        st = plan_scratch(pl->d_cand_keep, pl->cand_keep_cap, n_c);
+        if (st == CRP_OK) st = plan_scratch(pl->d_cand_sel, pl->cand_sel_cap, (uint64_t)kTopkSortMax);
+        if (st != CRP_OK) return st;
+        TopkCand *sel = pl->d_cand_sel, *keep = pl->d_cand_keep;
+        // first cut: the candidates at or above the log-linear bucket that
+        // holds the k-th largest weight (usually a few more than k)
+        std::vector<unsigned int> hist(kTopkBuckets);
+        cuda_ok(launch_cand_hist(cand, (unsigned int)n_c, pl->d_topk_hist, s));
+        cuda_ok(cudaMemcpyAsync(hist.data(), pl->d_topk_hist, kTopkBuckets * 4,
+                                cudaMemcpyDeviceToHost, s));
+        cuda_ok(cudaStreamSynchronize(s));
+        if (st != CRP_OK) return st;
+        uint64_t cum = 0;
+        int b = kTopkBuckets - 1;
+        for (; b > 0; --b) {
+            cum += hist[b];
+            if (cum >= (uint64_t)k) break;
         }
-        final_c = sel;
-        final_n = n_sel;
-        final_sort = n_sel;
+        cuda_ok(launch_cand_collect(cand, (unsigned int)n_c, (unsigned int)b, keep, cnt + 2, s));
+        pl->launches += 2;
+        unsigned int n1 = 0;
+        cuda_ok(cudaMemcpyAsync(&n1, cnt + 2, 4, cudaMemcpyDeviceToHost, s));
+        cuda_ok(cudaStreamSynchronize(s));
+        if (st != CRP_OK) return st;
+        final_c = keep;
+        final_sort = n1;
+        final_n = std::min<unsigned int>(n1, (unsigned int)k);
+        if (n1 > (unsigned int)kTopkSortMax) {
+            // MSD radix select on the remaining candidates down to exactly k
+            // (the collected ones move between keep and cand_tmp)
+            st = plan_scratch(pl->d_cand_tmp, pl->cand_tmp_cap, (uint64_t)n1);
+            if (st != CRP_OK) return st;
+            TopkCand *und = keep, *nxt = pl->d_cand_tmp;
+            unsigned int n_und = n1, n_sel = 0, need = (unsigned int)k;
+            cuda_ok(cudaMemsetAsync(cnt + 1, 0, 4, s));  // sel count
+            for (int d = 0; d < 16 && st == CRP_OK && need > 0; ++d) {
+                unsigned int h[256];
+                cuda_ok(launch_topk_digit_hist(und, n_und, d, dhist, s));
+                cuda_ok(cudaMemcpyAsync(h, dhist, sizeof h, cudaMemcpyDeviceToHost, s));
+                cuda_ok(cudaStreamSynchronize(s));
+                if (st != CRP_OK) break;
+                unsigned int above = 0;
+                int pivot = 255;
+                for (; pivot >= 0; --pivot) {
+                    if (above + h[pivot] >= need) break;
+                    above += h[pivot];
+                }
+                if (above == 0 && h[pivot] == n_und) continue;   // one digit value: next digit
+                cuda_ok(launch_topk_digit_split(und, n_und, d, (unsigned)pivot, sel, cnt + 1, nxt,
+                                                cnt + 2, s));
+                pl->launches += 2;
+                unsigned int kn = 0;
+                cuda_ok(cudaMemcpyAsync(&kn, cnt + 2, 4, cudaMemcpyDeviceToHost, s));
+                cuda_ok(cudaStreamSynchronize(s));
+                n_sel += above;
+                need -= above;
+                std::swap(und, nxt);
+                n_und = kn;
+                if (n_und == need) {  // everything left at this prefix is in
+                    cuda_ok(cudaMemcpyAsync(sel + n_sel, und, (size_t)n_und * sizeof(TopkCand),
+                                            cudaMemcpyDeviceToDevice, s));
+                    n_sel += n_und;
+                    need = 0;
+                }
+            }
+            final_c = sel;
+            final_n = n_sel;
+            final_sort = n_sel;
+        }
     }
     // write out (through a device staging buffer when the outputs are host memory)
     const bool dev_out = is_device_ptr(i_out);
     int32_t *di = i_out, *dj = j_out;
     double *dw = w_out, *dwl = w_lower;
-    void *stage = nullptr;
     if (st == CRP_OK && !dev_out) {
-        cuda_ok(cudaMalloc(&stage, (size_t)k * (4 + 4 + 8 + 8)));
-        di = (int32_t *)stage;
+        st = plan_scratch(pl->d_topk_stage, pl->topk_stage_cap,
+                          (uint64_t)kTopkSortMax * (4 + 4 + 8 + 8));
+        if (st != CRP_OK) return st;
+        di = (int32_t *)pl->d_topk_stage;
         dj = di + k;
         dw = (double *)(dj + k);
         dwl = w_lower ? dw + k : nullptr;
@@ -1342,12 +1395,9 @@ static crp_status topk_from_candidates(crp_plan *pl, const TopkCand *cand, uint6
         cuda_ok(cudaMemcpyAsync(w_out, dw, final_n * 8, cudaMemcpyDeviceToHost, s));
         if (w_lower) cuda_ok(cudaMemcpyAsync(w_lower, dwl, final_n * 8, cudaMemcpyDeviceToHost, s));
     }
-    cuda_ok(cudaStreamSynchronize(s));
     if (st == CRP_OK && kth_w && final_n)
-        cuda_ok(cudaMemcpy(kth_w, dw + (final_n - 1), 8, cudaMemcpyDeviceToHost));
-    cudaFree(stage);
-    cudaFree(sel);
-    cudaFree(keep);
+        cuda_ok(cudaMemcpyAsync(kth_w, dw + (final_n - 1), 8, cudaMemcpyDeviceToHost, s));
+    cuda_ok(cudaStreamSynchronize(s));
     if (st == CRP_OK) *n_out = (int32_t)final_n;
     return st;
 }

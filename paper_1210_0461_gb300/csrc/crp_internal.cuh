@@ -305,6 +305,10 @@ cudaError_t launch_topk_hist(const Slot *slots, uint64_t n, int value_type, int 
 cudaError_t launch_topk_collect(const Slot *slots, uint64_t n, int value_type, int upper_only,
                                 unsigned int bucket_lo, TopkCand *out, unsigned int *count,
                                 unsigned int cap, cudaStream_t s);
+cudaError_t launch_cand_hist(const TopkCand *c, unsigned int n, unsigned int *hist,
+                             cudaStream_t s);
+cudaError_t launch_cand_collect(const TopkCand *c, unsigned int n, unsigned int b_lo,
+                                TopkCand *out, unsigned int *cnt, cudaStream_t s);
 cudaError_t launch_topk_digit_hist(const TopkCand *c, unsigned int n, int digit,
                                    unsigned int *hist, cudaStream_t s);
 cudaError_t launch_topk_digit_split(const TopkCand *c, unsigned int n, int digit,

@@ -127,6 +127,46 @@ cudaError_t launch_topk_collect(const Slot *slots, uint64_t n, int value_type, i
 }
 
 // Digit d (0 = most significant) of the descending 128-bit order key
+// Log-linear histogram of candidates' weights (the buckets of the table scan)
+// and the candidates at or above a bucket: the first cut of a selection among
+// many candidates, before any radix pass.
+__global__ void k_cand_hist(const TopkCand *__restrict__ c, unsigned int n, unsigned int *hist) {
+    __shared__ unsigned int h[kTopkBuckets];
+    for (int t = threadIdx.x; t < kTopkBuckets; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    for (unsigned int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x)
+        atomicAdd(&h[bucket_of(c[x].wkey)], 1u);
+    __syncthreads();
+    for (int t = threadIdx.x; t < kTopkBuckets; t += blockDim.x)
+        if (h[t]) atomicAdd(&hist[t], h[t]);
+}
+
+cudaError_t launch_cand_hist(const TopkCand *c, unsigned int n, unsigned int *hist,
+                             cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * kTopkBuckets, s);
+    if (e != cudaSuccess || n == 0) return e;
+    unsigned int blocks = (n + 255) / 256;
+    k_cand_hist<<<blocks < 1024 ? blocks : 1024, 256, 0, s>>>(c, n, hist);
+    return cudaGetLastError();
+}
+
+__global__ void k_cand_collect(const TopkCand *__restrict__ c, unsigned int n, unsigned int b_lo,
+                               TopkCand *out, unsigned int *cnt) {
+    for (unsigned int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        const TopkCand v = c[x];
+        if (bucket_of(v.wkey) >= b_lo) out[atomicAdd(cnt, 1u)] = v;
+    }
+}
+
+cudaError_t launch_cand_collect(const TopkCand *c, unsigned int n, unsigned int b_lo,
+                                TopkCand *out, unsigned int *cnt, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess || n == 0) return e;
+    unsigned int blocks = (n + 255) / 256;
+    k_cand_collect<<<blocks < 1024 ? blocks : 1024, 256, 0, s>>>(c, n, b_lo, out, cnt);
+    return cudaGetLastError();
+}
+
 // (wkey, ~ij): larger digit = earlier in the output.
 __device__ __forceinline__ unsigned int order_digit(const TopkCand &c, int d) {
     unsigned long long word = d < 8 ? c.wkey : ~c.ij;
