@@ -1,6 +1,7 @@
 """Parity at the full size of the 10,000,000-transaction x 100,000-item
 co-occurrence workload, in the launch configuration bench.py times (routed,
-bins sized by the plan, hot block of 2048 items, warm stripes of 64 items):
+bins sized by the plan, hot block of 2048 items, warm stripes of 32 or 64
+items, the two widths the autotuner chooses between on this workload):
 properties that hold at any size (every term stored exactly once, every
 entry in its own partition, the diagonal equal to the item supports),
 sampled entries -- present and absent -- computed one by one by the oracle
@@ -18,8 +19,8 @@ pytestmark = pytest.mark.gpu
 P = 1024
 
 
-@pytest.fixture(scope="module")
-def full():
+@pytest.fixture(scope="module", params=[32, 64], ids=["warm32", "warm64"])
+def full(request):
     import paper_1210_0461_gb300 as pkg
     pkg.build()
     from paper_1210_0461_gb300 import crp
@@ -27,7 +28,8 @@ def full():
     L = T.lengths().astype(np.int64)
     d = crp.to_device(T)
     plan = crp.Plan(T.n_minor, T.n_minor, P, ci.SEED_A, ci.SEED_B, groups=0,
-                    flags=crp.CRP_PLAN_ROUTED, hot_items=2048, warm_items=64, auto_grow=True)
+                    flags=crp.CRP_PLAN_ROUTED, hot_items=2048, warm_items=request.param,
+                    auto_grow=True)
     plan.accumulate(d, d)
     plan.sync()
     inv = O.Compressed.of(ci.transpose(T))   # item -> transactions (rows of A, columns of B)
