@@ -176,6 +176,10 @@ struct crp_plan {
     SignPair sg = {0, 0, 0, 0};
     // timing of the enumeration kernel and a count of our launches
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;
+    // pinned words for counts read back mid-call, and the event that marks
+    // their copy (the stream runs on while the host waits for it)
+    unsigned long long *h_counts = nullptr;
+    cudaEvent_t ev_counts = nullptr;
     bool timed = false, timed_mid = false;
     uint64_t launches = 0;
     // distinct entries of the whole product estimated from the sampled
@@ -449,6 +453,8 @@ extern "C" void crp_plan_destroy(crp_plan *pl) {
     if (pl->ev0) cudaEventDestroy(pl->ev0);
     if (pl->ev1) cudaEventDestroy(pl->ev1);
     if (pl->evm) cudaEventDestroy(pl->evm);
+    if (pl->ev_counts) cudaEventDestroy(pl->ev_counts);
+    if (pl->h_counts) cudaFreeHost(pl->h_counts);
     delete pl;
 }
 
@@ -705,6 +711,7 @@ static crp_status estimate_and_allocate(crp_plan *pl, const crp_sparse *A, const
 }
 
 static crp_status select_hot_items(crp_plan *pl, const crp_sparse *A, const crp_sparse *B);
+static crp_status count_degrees(crp_plan *pl, const crp_sparse *A, const crp_sparse *B);
 static void set_dense_args(crp_plan *pl, AccumulateArgs &a);
 static crp_status flush_dense(crp_plan *pl, const TableView &tv);
 
@@ -791,6 +798,15 @@ static crp_status summary_accumulate(crp_plan *pl, const crp_sparse *A, const cr
     }
     pl->summary_ms = total_ms;
     pl->timed = false;
+    return CRP_OK;
+}
+
+// The plan's pinned words and their event, made at first use.
+static crp_status ensure_pinned(crp_plan *pl) {
+    if (!pl->h_counts) {
+        CRP_CUDA(cudaMallocHost(&pl->h_counts, 4 * sizeof(unsigned long long)));
+        CRP_CUDA(cudaEventCreateWithFlags(&pl->ev_counts, cudaEventDisableTiming));
+    }
     return CRP_OK;
 }
 
@@ -913,13 +929,24 @@ static crp_status routed_accumulate(crp_plan *pl, const crp_sparse *A, const crp
     const int64_t S = std::min<int64_t>(K, std::max<int64_t>(65536, K / 64));
     AccumulateArgs sample = RA.acc;
     sample.K = S;
-    unsigned long long cnt[3] = {0, 0, 0};   // sample records, sample terms, all terms
+    // (the counts come back through pinned words while the stream goes on
+    // to count the degrees for the top-k bound)
+    st = ensure_pinned(pl);
+    if (st != CRP_OK) return st;
     CRP_CUDA(launch_count_records(sample, pl->d_scratch64, pl->stream));
     CRP_CUDA(launch_count_terms(A->ptr, B->ptr, S, pl->d_scratch64 + 1, pl->stream));
     CRP_CUDA(launch_count_terms(A->ptr, B->ptr, K, pl->d_scratch64 + 2, pl->stream));
-    CRP_CUDA(cudaMemcpyAsync(cnt, pl->d_scratch64, 24, cudaMemcpyDeviceToHost, pl->stream));
-    CRP_CUDA(cudaStreamSynchronize(pl->stream));
+    CRP_CUDA(cudaMemcpyAsync(pl->h_counts, pl->d_scratch64, 24, cudaMemcpyDeviceToHost,
+                             pl->stream));
+    CRP_CUDA(cudaEventRecord(pl->ev_counts, pl->stream));
     pl->launches += 3;
+    if (pl->d.hot_items || pl->d.warm_items) {
+        st = count_degrees(pl, A, B);
+        if (st != CRP_OK) return st;
+    }
+    CRP_CUDA(cudaEventSynchronize(pl->ev_counts));
+    // sample records, sample terms, all terms
+    const unsigned long long cnt[3] = {pl->h_counts[0], pl->h_counts[1], pl->h_counts[2]};
     const double share = cnt[1] ? (double)cnt[0] / (double)cnt[1] : 1.0;
     const uint64_t records =
         std::min<uint64_t>(cnt[2], (uint64_t)(share * 1.1 * (double)cnt[2]) + 65536);
@@ -974,17 +1001,17 @@ static crp_status select_hot_items(crp_plan *pl, const crp_sparse *A, const crp_
     }
     const int64_t K = A->n_major;
     const int64_t S = std::min<int64_t>(K, std::max<int64_t>(4096, K / 64));
-    int64_t ea = 0, eb = 0;
-    CRP_CUDA(cudaMemcpyAsync(&ea, A->ptr + S, 8, cudaMemcpyDeviceToHost, s));
-    CRP_CUDA(cudaMemcpyAsync(&eb, B->ptr + S, 8, cudaMemcpyDeviceToHost, s));
+    // the sample's nonzeros end at ptr[S], read by the counting kernel itself
+    const int64_t hint_a = K ? (int64_t)((double)A->nnz * (double)S / (double)K) : 0;
+    const int64_t hint_b = K ? (int64_t)((double)B->nnz * (double)S / (double)K) : 0;
     // A and B the same arrays (T^T T): one count and one selection serve
     // both sides, the B side a copy of the A side's items and ranks
     const bool mirror = A->idx == B->idx && A->ptr == B->ptr && pl->d.n_rows == pl->d.n_cols;
     CRP_CUDA(cudaMemsetAsync(pl->d_cnt_a, 0, (size_t)pl->d.n_rows * 4, s));
     if (!mirror) CRP_CUDA(cudaMemsetAsync(pl->d_cnt_b, 0, (size_t)pl->d.n_cols * 4, s));
-    CRP_CUDA(cudaStreamSynchronize(s));
-    CRP_CUDA(launch_item_counts(A->idx, ea, pl->d.n_rows, pl->d_cnt_a, s));
-    if (!mirror) CRP_CUDA(launch_item_counts(B->idx, eb, pl->d.n_cols, pl->d_cnt_b, s));
+    CRP_CUDA(launch_item_counts_at(A->idx, A->ptr + S, hint_a, pl->d.n_rows, pl->d_cnt_a, s));
+    if (!mirror)
+        CRP_CUDA(launch_item_counts_at(B->idx, B->ptr + S, hint_b, pl->d.n_cols, pl->d_cnt_b, s));
     pl->launches += mirror ? 1 : 2;
     if (pl->hot_R) {
         CRP_CUDA(select_top(pl->d_cnt_a, pl->d.n_rows, pl->hot_R, pl->d_items_a, pl->d_sel, s));
@@ -1001,34 +1028,7 @@ static crp_status select_hot_items(crp_plan *pl, const crp_sparse *A, const crp_
             CRP_CUDA(order_by_count(pl->d_items_b, pl->d_cnt_b, pl->hot_R, s));
             CRP_CUDA(launch_hot_ranks(pl->d_rank_b, pl->d.n_cols, pl->d_items_b, pl->hot_R, s));
         }
-        pl->launches += mirror ? 5 + 3 : 2 * 5 + 6;
-        if (!pl->summary && pl->d.value_type == CRP_I32) {
-            // degrees of every row and column over all calls since the reset:
-            // the bound that lets crp_topk answer from the hot pairs
-            if (!pl->d_deg_a) {
-                CRP_CUDA(cudaMalloc(&pl->d_deg_a, (size_t)pl->d.n_rows * 8));
-                CRP_CUDA(cudaMalloc(&pl->d_deg_b, (size_t)pl->d.n_cols * 8));
-                CRP_CUDA(cudaMemsetAsync(pl->d_deg_a, 0, (size_t)pl->d.n_rows * 8, s));
-                CRP_CUDA(cudaMemsetAsync(pl->d_deg_b, 0, (size_t)pl->d.n_cols * 8, s));
-            }
-            // (B the same arrays as A, as for T^T T: one count serves both sides
-            // for as long as every call since the reset is like that)
-            const bool same = A->idx == B->idx && A->nnz == B->nnz &&
-                              pl->d.n_rows == pl->d.n_cols;
-            if (!same && pl->deg_b_mirrors_a) {
-                CRP_CUDA(cudaMemcpyAsync(pl->d_deg_b, pl->d_deg_a, (size_t)pl->d.n_cols * 8,
-                                         cudaMemcpyDeviceToDevice, s));
-                pl->deg_b_mirrors_a = false;
-            }
-            CRP_CUDA(launch_degrees(A->idx, A->nnz, pl->d.n_rows, pl->d_rank_a, pl->hot_R,
-                                    pl->d_items_a, pl->d_deg_a, pl->sm_count, s));
-            pl->launches += 1;
-            if (!pl->deg_b_mirrors_a) {
-                CRP_CUDA(launch_degrees(B->idx, B->nnz, pl->d.n_cols, pl->d_rank_b, pl->hot_R,
-                                        pl->d_items_b, pl->d_deg_b, pl->sm_count, s));
-                pl->launches += 1;
-            }
-        }
+        pl->launches += mirror ? kSelectTopLaunches + 3 : 2 * kSelectTopLaunches + 6;
     }
     if (pl->warm_W) {
         CRP_CUDA(select_top(pl->d_cnt_a, pl->d.n_rows, pl->warm_W, pl->d_witems_a, pl->d_sel, s));
@@ -1043,7 +1043,38 @@ static crp_status select_hot_items(crp_plan *pl, const crp_sparse *A, const crp_
                                 s));
             CRP_CUDA(launch_hot_ranks(pl->d_wrank_b, pl->d.n_cols, pl->d_witems_b, pl->warm_W, s));
         }
-        pl->launches += mirror ? 5 + 2 : 2 * 5 + 4;
+        pl->launches += mirror ? kSelectTopLaunches + 2 : 2 * kSelectTopLaunches + 4;
+    }
+    return CRP_OK;
+}
+
+// Degrees of every row and column over all calls since the reset (exact
+// integer tables with a hot set): the bound that lets crp_topk answer from
+// the hot pairs. Runs after select_hot_items (it reads the hot ranks).
+static crp_status count_degrees(crp_plan *pl, const crp_sparse *A, const crp_sparse *B) {
+    if (!pl->hot_R || pl->summary || pl->d.value_type != CRP_I32) return CRP_OK;
+    cudaStream_t s = pl->stream;
+    if (!pl->d_deg_a) {
+        CRP_CUDA(cudaMalloc(&pl->d_deg_a, (size_t)pl->d.n_rows * 8));
+        CRP_CUDA(cudaMalloc(&pl->d_deg_b, (size_t)pl->d.n_cols * 8));
+        CRP_CUDA(cudaMemsetAsync(pl->d_deg_a, 0, (size_t)pl->d.n_rows * 8, s));
+        CRP_CUDA(cudaMemsetAsync(pl->d_deg_b, 0, (size_t)pl->d.n_cols * 8, s));
+    }
+    // (B the same arrays as A, as for T^T T: one count serves both sides for
+    // as long as every call since the reset is like that)
+    const bool same = A->idx == B->idx && A->nnz == B->nnz && pl->d.n_rows == pl->d.n_cols;
+    if (!same && pl->deg_b_mirrors_a) {
+        CRP_CUDA(cudaMemcpyAsync(pl->d_deg_b, pl->d_deg_a, (size_t)pl->d.n_cols * 8,
+                                 cudaMemcpyDeviceToDevice, s));
+        pl->deg_b_mirrors_a = false;
+    }
+    CRP_CUDA(launch_degrees(A->idx, A->nnz, pl->d.n_rows, pl->d_rank_a, pl->hot_R, pl->d_items_a,
+                            pl->d_deg_a, pl->sm_count, s));
+    pl->launches += 1;
+    if (!pl->deg_b_mirrors_a) {
+        CRP_CUDA(launch_degrees(B->idx, B->nnz, pl->d.n_cols, pl->d_rank_b, pl->hot_R,
+                                pl->d_items_b, pl->d_deg_b, pl->sm_count, s));
+        pl->launches += 1;
     }
     return CRP_OK;
 }
@@ -1144,6 +1175,7 @@ extern "C" crp_status crp_outer_accumulate(crp_plan *pl, const crp_sparse *A, co
     a.tv = table_view(pl, pl->slots, pl->d_off, pl->d_mask);
     if (pl->d.hot_items || pl->d.warm_items) {
         st = select_hot_items(pl, A, B);
+        if (st == CRP_OK) st = count_degrees(pl, A, B);
         if (st != CRP_OK) return st;
         set_dense_args(pl, a);
     }
@@ -1236,9 +1268,13 @@ static crp_status grow_full_partitions(crp_plan *pl) {
 
 extern "C" crp_status crp_sync(crp_plan *pl) {
     if (!pl) return fail(CRP_EINVAL, "null plan");
+    crp_status ps = ensure_pinned(pl);
+    if (ps != CRP_OK) return ps;
+    // the status word comes back behind the stream's work: one round trip
+    unsigned int *h_status = (unsigned int *)(pl->h_counts + 3);
+    CRP_CUDA(cudaMemcpyAsync(h_status, &pl->dc->status, 4, cudaMemcpyDeviceToHost, pl->stream));
     CRP_CUDA(cudaStreamSynchronize(pl->stream));
-    unsigned int status = 0;
-    CRP_CUDA(cudaMemcpy(&status, &pl->dc->status, 4, cudaMemcpyDeviceToHost));
+    const unsigned int status = *h_status;
     if (status & kStatusBadIndex)
         return fail(CRP_EINVAL, "an input index was out of range (or a vector too long to sort)");
     if (status & kStatusNotOwned)

@@ -260,10 +260,15 @@ cudaError_t launch_warm_flush(unsigned int *stripe, uint32_t W, int32_t n_other,
 // Selections (crp_select.cu)
 int select_grid_for(int64_t n);
 cudaError_t order_by_count(int64_t *items, const unsigned int *cnt, uint32_t R, cudaStream_t s);
+// kernels one select_top call launches (four histogram passes, four digit
+// picks, the emit)
+constexpr int kSelectTopLaunches = 9;
 cudaError_t select_top(const uint32_t *key, int64_t n, int64_t K, int64_t *out,
-                       unsigned int *scratch /* 258 */, cudaStream_t s);
+                       unsigned int *scratch /* 260 */, cudaStream_t s);
 cudaError_t launch_item_counts(const int32_t *idx, int64_t nnz, int32_t n_items, unsigned int *cnt,
                                cudaStream_t s);
+cudaError_t launch_item_counts_at(const int32_t *idx, const int64_t *nnz_at, int64_t nnz_hint,
+                                  int32_t n_items, unsigned int *cnt, cudaStream_t s);
 
 // Record the calling thread's error message (read by crp_last_error).
 void set_last_error(const std::string &msg);

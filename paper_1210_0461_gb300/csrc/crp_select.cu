@@ -8,7 +8,10 @@
 
 namespace crp {
 
-__global__ void k_item_counts(const int32_t *idx, int64_t nnz, int32_t n_items, unsigned int *cnt) {
+// nnz_at, when given, holds the count on the device (an entry of a ptr array)
+__global__ void k_item_counts(const int32_t *idx, int64_t nnz, const int64_t *nnz_at,
+                              int32_t n_items, unsigned int *cnt) {
+    if (nnz_at) nnz = *nnz_at;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nnz;
          x += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = idx[x];
@@ -16,9 +19,16 @@ __global__ void k_item_counts(const int32_t *idx, int64_t nnz, int32_t n_items, 
     }
 }
 
-__global__ void k_sel_hist(const uint32_t *key, int64_t n, uint32_t prefix, uint32_t pmask,
-                           int shift, unsigned int *hist) {
+// Selection state kept on the device between passes (no host round trip):
+// words 258 and 259 of the scratch hold the count still wanted at the
+// current prefix and the prefix itself.
+constexpr int kSelNeed = 258, kSelPrefix = 259;
+
+__global__ void k_sel_hist(const uint32_t *key, int64_t n, int pass, unsigned int *scratch) {
     __shared__ unsigned int h[256];
+    const int shift = 24 - 8 * pass;
+    const uint32_t prefix = pass ? scratch[kSelPrefix] : 0u;
+    const uint32_t pmask = pass ? 0xFFFFFFFFu << (shift + 8) : 0u;
     for (int t = threadIdx.x; t < 256; t += blockDim.x) h[t] = 0;
     __syncthreads();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
@@ -28,11 +38,37 @@ __global__ void k_sel_hist(const uint32_t *key, int64_t n, uint32_t prefix, uint
     }
     __syncthreads();
     for (int t = threadIdx.x; t < 256; t += blockDim.x)
-        if (h[t]) atomicAdd(&hist[t], h[t]);
+        if (h[t]) atomicAdd(&scratch[t], h[t]);
 }
 
-__global__ void k_sel_emit(const uint32_t *key, int64_t n, uint32_t tau, uint32_t need_at_tau,
+// The digit of this pass: the largest d whose keys (with the prefix so far)
+// together with those of the larger digits reach the wanted count; the
+// wanted count drops by the keys of the larger digits. Clears the histogram
+// for the next pass. One CTA of 256 threads.
+__global__ void k_sel_pick(unsigned int *scratch, int pass, uint32_t K) {
+    __shared__ uint32_t digit;
+    if (threadIdx.x == 0) {
+        const int shift = 24 - 8 * pass;
+        uint32_t need = pass ? scratch[kSelNeed] : K;
+        const uint32_t prefix = pass ? scratch[kSelPrefix] : 0u;
+        uint64_t cum = 0;
+        int d = 255;
+        for (; d > 0; --d) {
+            if (cum + scratch[d] >= need) break;
+            cum += scratch[d];
+        }
+        need -= (uint32_t)cum;
+        digit = (uint32_t)d;
+        scratch[kSelNeed] = need;
+        scratch[kSelPrefix] = prefix | ((uint32_t)d << shift);
+    }
+    __syncthreads();
+    scratch[threadIdx.x] = 0;
+}
+
+__global__ void k_sel_emit(const uint32_t *key, int64_t n, const unsigned int *scratch,
                            int64_t *out, unsigned int *cnt, unsigned int *tie) {
+    const uint32_t tau = scratch[kSelPrefix], need_at_tau = scratch[kSelNeed];
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t k = key[x];
@@ -48,33 +84,19 @@ int select_grid_for(int64_t n) {
 }
 
 // Indices (unordered) of the K largest keys.  out: device, K entries.
+// Four histogram passes and the emit run back to back on the stream; the
+// digits are picked on the device, so the host never waits.
 cudaError_t select_top(const uint32_t *key, int64_t n, int64_t K, int64_t *out,
-                              unsigned int *scratch /* 258 */, cudaStream_t s) {
-    uint32_t prefix = 0, pmask = 0;
-    uint64_t need = (uint64_t)K;
-    for (int pass = 0; pass < 4; ++pass) {
-        const int shift = 24 - 8 * pass;
-        cudaError_t e = cudaMemsetAsync(scratch, 0, 256 * 4, s);
-        if (e != cudaSuccess) return e;
-        k_sel_hist<<<select_grid_for(n), 256, 0, s>>>(key, n, prefix, pmask, shift, scratch);
-        unsigned int h[256];
-        e = cudaMemcpyAsync(h, scratch, sizeof h, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return e;
-        uint64_t cum = 0;
-        int d = 255;
-        for (; d > 0; --d) {
-            if (cum + h[d] >= need) break;
-            cum += h[d];
-        }
-        need -= cum;
-        prefix |= (uint32_t)d << shift;
-        pmask |= 255u << shift;
-    }
-    cudaError_t e = cudaMemsetAsync(scratch + 256, 0, 8, s);
+                       unsigned int *scratch /* 260 */, cudaStream_t s) {
+    if (K < 0 || K > (int64_t)0xFFFFFFFFu) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 258 * 4, s);
     if (e != cudaSuccess) return e;
-    k_sel_emit<<<select_grid_for(n), 256, 0, s>>>(key, n, prefix, (uint32_t)need, out, scratch + 256,
-                                           scratch + 257);
+    for (int pass = 0; pass < 4; ++pass) {
+        k_sel_hist<<<select_grid_for(n), 256, 0, s>>>(key, n, pass, scratch);
+        k_sel_pick<<<1, 256, 0, s>>>(scratch, pass, (uint32_t)K);
+    }
+    k_sel_emit<<<select_grid_for(n), 256, 0, s>>>(key, n, scratch, out, scratch + 256,
+                                                  scratch + 257);
     return cudaGetLastError();
 }
 
@@ -117,7 +139,15 @@ cudaError_t order_by_count(int64_t *items, const unsigned int *cnt, uint32_t R, 
 cudaError_t launch_item_counts(const int32_t *idx, int64_t nnz, int32_t n_items, unsigned int *cnt,
                                cudaStream_t s) {
     if (nnz <= 0) return cudaSuccess;
-    k_item_counts<<<select_grid_for(nnz), 256, 0, s>>>(idx, nnz, n_items, cnt);
+    k_item_counts<<<select_grid_for(nnz), 256, 0, s>>>(idx, nnz, nullptr, n_items, cnt);
+    return cudaGetLastError();
+}
+
+// The same over idx[0, *nnz_at) with the count read on the device (no host
+// round trip); nnz_hint sizes the grid only.
+cudaError_t launch_item_counts_at(const int32_t *idx, const int64_t *nnz_at, int64_t nnz_hint,
+                                  int32_t n_items, unsigned int *cnt, cudaStream_t s) {
+    k_item_counts<<<select_grid_for(nnz_hint), 256, 0, s>>>(idx, 0, nnz_at, n_items, cnt);
     return cudaGetLastError();
 }
 
