@@ -887,44 +887,61 @@ def main():
     traffic = None
 
     # ---- end to end through the C ABI from pinned host buffers ----
+    # Every step copies its input from pinned host memory and reads its top-k
+    # back to the host. The input goes into one of two device buffers: the copy
+    # for step s + 1 runs on its own stream while step s computes from the
+    # other buffer (it waits for the step that last read its buffer), so the
+    # timed region holds every step's copy, overlapped with the step before.
     e2e = None
     if not args.no_e2e:
         hp = torch.from_numpy(T.ptr).pin_memory()
         hi = torch.from_numpy(T.idx).pin_memory()
-        dptr = torch.empty_like(hp, device=f"cuda:{local}")
-        didx = torch.empty_like(hi, device=f"cuda:{local}")
-        dd = crp.DeviceSparse(dptr, didx, None, T.n_minor)
-        ti = np.zeros(args.topk, np.int32)
+        dev = f"cuda:{local}"
+        bufs = [(torch.empty_like(hp, device=dev), torch.empty_like(hi, device=dev))
+                for _ in range(2)]
+        dds = [crp.DeviceSparse(bp, bi, None, T.n_minor) for bp, bi in bufs]
+        copy_stream = torch.cuda.Stream(device=dev)
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
+        released = [torch.cuda.Event(), torch.cuda.Event()]
+        for e in released:
+            e.record(stream)
 
-        copy_stream = torch.cuda.Stream(device=f"cuda:{local}")
-
-        def e2e_step():
-            # the host-to-device copy of the step's input runs on its own stream,
-            # beside the table reset; the accumulate waits for it
+        def issue_copy(slot):
             with torch.cuda.stream(copy_stream):
-                dptr.copy_(hp, non_blocking=True)
-                didx.copy_(hi, non_blocking=True)
-                copied = torch.cuda.Event()
-                copied.record(copy_stream)
-            plan.reset()
-            stream.wait_event(copied)
-            plan.accumulate(dd, dd)
-            plan.sync()
-            top = plan.topk(args.topk, upper=True)   # host outputs: D2H inside
-            if world > 1:
-                top = gather_topk(top[:3], args.topk)
+                copy_stream.wait_event(released[slot])
+                bufs[slot][0].copy_(hp, non_blocking=True)
+                bufs[slot][1].copy_(hi, non_blocking=True)
+                copied[slot].record(copy_stream)
+
+        def e2e_run(n):
+            issue_copy(0)
+            top = None
+            for s_ in range(n):
+                slot = s_ & 1
+                if s_ + 1 < n:
+                    issue_copy(slot ^ 1)
+                plan.reset()
+                stream.wait_event(copied[slot])
+                plan.accumulate(dds[slot], dds[slot])
+                released[slot].record(stream)
+                plan.sync()
+                top = plan.topk(args.topk, upper=True)   # host outputs: D2H inside
+                if world > 1:
+                    top = gather_topk(top[:3], args.topk)
             return top
 
-        e2e_step()
+        e2e_run(2)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step()
+        e2e_run(args.steps)
         torch.cuda.synchronize()
         e_rate, e_ms = job_rate(terms_step, (time.perf_counter() - t0) * 1e3 / args.steps)
         e2e = {"value": e_rate, "unit": "terms/s",
                "h2d_bytes_per_step": int(hp.numel() * 8 + hi.numel() * 4),
-               "d2h_bytes_per_step": int(args.topk * (4 + 4 + 8 + 8)), "ms_per_step": e_ms}
+               "d2h_bytes_per_step": int(args.topk * (4 + 4 + 8 + 8)), "ms_per_step": e_ms,
+               "copies": "each step's input copied from pinned host memory into one of two "
+                         "device buffers while the step before computes; top-k read back "
+                         "to host memory every step"}
 
     ti, tj, tw, _ = plan.topk(args.topk, upper=True)
     # the top-k judged by the oracle's certified heaviest pairs of this input
