@@ -160,6 +160,7 @@ struct crp_plan {
     // certified top-k: cumulative degrees of rows and columns since the last
     // reset, the hot pairs' candidate buffer, calls answered from it
     unsigned long long *d_deg_a = nullptr, *d_deg_b = nullptr;
+    bool warm_in_hot = false;      // warm items = the first warm_W hot items
     bool deg_b_mirrors_a = true;   // every call since the reset had B == A: d_deg_b unused
     TopkCand *d_hot_cand = nullptr;
     // top-k scratch kept across calls
@@ -1030,7 +1031,26 @@ static crp_status select_hot_items(crp_plan *pl, const crp_sparse *A, const crp_
         }
         pl->launches += mirror ? kSelectTopLaunches + 3 : 2 * kSelectTopLaunches + 6;
     }
-    if (pl->warm_W) {
+    pl->warm_in_hot = pl->warm_W && pl->hot_R >= pl->warm_W;
+    if (pl->warm_in_hot) {
+        // the warm items are the first warm_W hot items (those are ordered by
+        // count), so an item's warm rank is its hot rank: one class order of
+        // the ranks serves both tiers in the routed walk
+        const size_t wb = (size_t)pl->warm_W * 8;
+        CRP_CUDA(cudaMemcpyAsync(pl->d_witems_a, pl->d_items_a, wb, cudaMemcpyDeviceToDevice, s));
+        CRP_CUDA(launch_hot_ranks(pl->d_wrank_a, pl->d.n_rows, pl->d_witems_a, pl->warm_W, s));
+        if (mirror) {
+            CRP_CUDA(cudaMemcpyAsync(pl->d_witems_b, pl->d_witems_a, wb, cudaMemcpyDeviceToDevice,
+                                     s));
+            CRP_CUDA(cudaMemcpyAsync(pl->d_wrank_b, pl->d_wrank_a, (size_t)pl->d.n_cols * 2,
+                                     cudaMemcpyDeviceToDevice, s));
+        } else {
+            CRP_CUDA(cudaMemcpyAsync(pl->d_witems_b, pl->d_items_b, wb, cudaMemcpyDeviceToDevice,
+                                     s));
+            CRP_CUDA(launch_hot_ranks(pl->d_wrank_b, pl->d.n_cols, pl->d_witems_b, pl->warm_W, s));
+        }
+        pl->launches += mirror ? 2 : 4;
+    } else if (pl->warm_W) {
         CRP_CUDA(select_top(pl->d_cnt_a, pl->d.n_rows, pl->warm_W, pl->d_witems_a, pl->d_sel, s));
         CRP_CUDA(launch_hot_ranks(pl->d_wrank_a, pl->d.n_rows, pl->d_witems_a, pl->warm_W, s));
         if (mirror) {
@@ -1092,6 +1112,7 @@ static void set_dense_args(crp_plan *pl, AccumulateArgs &a) {
         a.warm_a = pl->d_warm_a;
         a.warm_b = pl->d_warm_b;
         a.warm_W = pl->warm_W;
+        a.warm_in_hot = pl->warm_in_hot ? 1 : 0;
     }
 }
 

@@ -173,6 +173,8 @@ struct AccumulateArgs {
     unsigned int *warm_a = nullptr;   // [warm_W][n_cols]
     unsigned int *warm_b = nullptr;   // [warm_W][n_rows]
     uint32_t warm_W = 0;
+    // the warm items are the first warm_W hot ranks (warm rank == hot rank)
+    int warm_in_hot = 0;
     // interval [part_lo, part_hi) of partitions kept (Figure 1, CRoP on [q, r))
     uint32_t part_lo = 0, part_hi = 0xFFFFFFFFu;
     // pairs i < j of T^T T with a_k == b_k (same sorted list): the window of

@@ -266,6 +266,97 @@ __device__ __forceinline__ bool fl_advance(FlatState &st, const AccumulateArgs &
     }
 }
 
+// ---------------------------------------------------------------------------
+// Class-sorted enumeration (int counts, every pair, no partition interval,
+// the warm items being the first warm_W hot ranks).  A staged block of up to
+// 32 entries per side is ordered by dense-tier class -- ranks below the
+// smaller of (warm_W, core_H), below the larger, below hot_R, then the other
+// valid entries -- so the block's terms of one destination form one or two
+// rectangles:
+//   core    rows [0, nH)  x cols [0, cH)
+//   hot     rows [0, nH)  x cols [cH, cR)   and rows [nH, nR) x cols [0, cR)
+//   warm a  rows [0, nW)  x cols [cR, cn)
+//   warm b  rows [nR, m)  x cols [0, cW)
+//   record  rows [nW, nR) x cols [cR, cn)   and rows [nR, m)  x cols [cW, cn)
+// (nW, nH, nR: staged rows of rank below warm_W, core_H, hot_R; m: valid
+// rows; c* the same for columns).  The warp walks each rectangle 32 terms at
+// a time with one destination for every lane: no per-term classification
+// and no divergent branches between destinations.
+struct SortedCounts { int n1, n2, nR, m; };
+
+template <typename D>
+__device__ __forceinline__ SortedCounts stage_sorted(const AccumulateArgs &A, const int32_t *idx,
+                                                     int64_t base, int cnt, int32_t n_items,
+                                                     const uint16_t *rank_arr, const SideHash &h,
+                                                     uint32_t t1, uint32_t t2, int lane, D *dst) {
+    __syncwarp();   // the previous block has been read by every lane
+    uint32_t v = ~0u, hv = 0u, rk = 0xFFFFu;
+    int cls = 4;    // 4: no entry, or an index out of range
+    if (lane < cnt) {
+        const uint32_t x = ld_idx(idx + base + lane);
+        if (x < (uint32_t)n_items) {
+            v = x;
+            hv = side_hash(h, x);
+            rk = rank_arr ? __ldg(rank_arr + x) : 0xFFFFu;
+            cls = (rk >= t1) + (rk >= t2) + (rk >= A.hot_R);
+        } else if (A.debug_checks) {
+            atomicOr(&A.tv.dc->status, kStatusBadIndex);
+        }
+    }
+    const unsigned m0 = __ballot_sync(kFull, cls == 0), m1 = __ballot_sync(kFull, cls == 1);
+    const unsigned m2 = __ballot_sync(kFull, cls == 2), m3 = __ballot_sync(kFull, cls == 3);
+    SortedCounts c;
+    c.n1 = __popc(m0);
+    c.n2 = c.n1 + __popc(m1);
+    c.nR = c.n2 + __popc(m2);
+    c.m = c.nR + __popc(m3);
+    const unsigned below = (1u << lane) - 1u;
+    if (cls < 4) {
+        const int pos = cls == 0   ? __popc(m0 & below)
+                        : cls == 1 ? c.n1 + __popc(m1 & below)
+                        : cls == 2 ? c.n2 + __popc(m2 & below)
+                                   : c.nR + __popc(m3 & below);
+        dst[pos] = D{v, hv, rk, 1.0f};   // RowData / ColData: index, side hash, rank
+    }
+    __syncwarp();
+    return c;
+}
+
+enum { kToCore = 0, kToHot, kToWarmA, kToWarmB, kToRecord };
+
+// The terms rows [r0, r1) x cols [c0, c1) of a staged block, all bound for
+// destination DST.
+template <int DST>
+__device__ __forceinline__ void emit_rect(const RouteArgs &RA, unsigned long long *cur,
+                                          unsigned int *nxt, unsigned int *core, uint32_t Hp,
+                                          const RowData *rows, const ColData *cols, int r0, int r1,
+                                          int c0, int c1, int lane) {
+    const int nr = r1 - r0, nc = c1 - c0;
+    if (nr <= 0 || nc <= 0) return;
+    const AccumulateArgs &A = RA.acc;
+    const int n = nr * nc;
+    const uint32_t inv = (65536u + (uint32_t)nc - 1u) / (uint32_t)nc;   // t / nc for t < 1024
+    for (int q = 0; q < n; q += 32) {
+        const int t = q + lane;
+        if (t >= n) break;
+        const int rr = (int)(((uint32_t)t * inv) >> 16);
+        const RowData rd = rows[r0 + rr];
+        const ColData cd = cols[c0 + t - rr * nc];
+        if constexpr (DST == kToCore) {
+            atomicAdd(&core[rd.ranks * Hp + cd.ranks], 1u);
+        } else if constexpr (DST == kToHot) {
+            atomicAdd(&A.hot_block[rd.ranks * A.hot_R + cd.ranks], 1u);
+        } else if constexpr (DST == kToWarmA) {
+            atomicAdd(&A.warm_a[(size_t)rd.ranks * A.n_cols + cd.j], 1u);
+        } else if constexpr (DST == kToWarmB) {
+            atomicAdd(&A.warm_b[(size_t)cd.ranks * A.n_rows + rd.i], 1u);
+        } else {
+            const uint32_t p = (rd.ha + cd.hb) & A.hp.ha.mask;
+            bin_append(RA, cur, nxt, p >> RA.B_shift, (unsigned long long)make_key(rd.i, cd.j));
+        }
+    }
+}
+
 template <int VT>
 __global__ void __launch_bounds__(kRouteThreads, 1) k_route(RouteArgs RA) {
     typedef typename RecT<VT>::type R;
@@ -288,13 +379,66 @@ __global__ void __launch_bounds__(kRouteThreads, 1) k_route(RouteArgs RA) {
     // this warp's staged block: 32 rows then 32 columns
     RowData *rows = (RowData *)(smem_raw + route_stage_offset(RA.B, H)) + warp * 64;
     ColData *cols = (ColData *)(rows + 32);
+    // the class-sorted walk where it applies (warp-uniform: kernel arguments)
+    bool sorted = false;
+    unsigned long long sorted_terms = 0;   // terms of this warp on the sorted walk
+    if constexpr (VT == CRP_I32) {
+        sorted = A.mode == CRP_FULL && !A.sym_upper && !filter &&
+                 (A.warm_W == 0 || (A.warm_in_hot && A.warm_W <= A.hot_R));
+        if (sorted) {
+            const uint32_t W = A.warm_W;
+            const uint32_t t1 = min(W, H), t2 = max(W, H);
+            const bool w_first = W <= H;
+            while (true) {
+                unsigned int item = 0;
+                if (lane == 0) item = atomicAdd(&A.tv.dc->work_next, 1u);
+                item = __shfl_sync(kFull, item, 0);
+                if (item >= A.n_tiles) break;
+                const int64_t k0 = (int64_t)item * A.tile;
+                const int64_t k1 = min((int64_t)A.K, k0 + (int64_t)A.tile);
+                for (int64_t k = k0; k < k1; ++k) {
+                    const int64_t a0 = __ldg(A.a_ptr + k), b0 = __ldg(A.b_ptr + k);
+                    const int32_t na = (int32_t)(__ldg(A.a_ptr + k + 1) - a0);
+                    const int32_t nb = (int32_t)(__ldg(A.b_ptr + k + 1) - b0);
+                    if (na <= 0 || nb <= 0) continue;
+                    for (int32_t ab = 0; ab < na; ab += 32) {
+                        const SortedCounts rc =
+                            stage_sorted(A, A.a_idx, a0 + ab, min(32, na - ab), A.n_rows,
+                                         A.hot_rank_a, A.hp.ha, t1, t2, lane, rows);
+                        const int nW = w_first ? rc.n1 : rc.n2, nH = w_first ? rc.n2 : rc.n1;
+                        for (int32_t bb = 0; bb < nb; bb += 32) {
+                            const SortedCounts cc =
+                                stage_sorted(A, A.b_idx, b0 + bb, min(32, nb - bb), A.n_cols,
+                                             A.hot_rank_b, A.hp.hb, t1, t2, lane, cols);
+                            const int cW = w_first ? cc.n1 : cc.n2, cH = w_first ? cc.n2 : cc.n1;
+                            emit_rect<kToCore>(RA, cur, nxt, core, Hp, rows, cols, 0, nH, 0, cH,
+                                               lane);
+                            emit_rect<kToHot>(RA, cur, nxt, core, Hp, rows, cols, 0, nH, cH,
+                                              cc.nR, lane);
+                            emit_rect<kToHot>(RA, cur, nxt, core, Hp, rows, cols, nH, rc.nR, 0,
+                                              cc.nR, lane);
+                            emit_rect<kToWarmA>(RA, cur, nxt, core, Hp, rows, cols, 0, nW, cc.nR,
+                                                cc.m, lane);
+                            emit_rect<kToWarmB>(RA, cur, nxt, core, Hp, rows, cols, rc.nR, rc.m,
+                                                0, cW, lane);
+                            emit_rect<kToRecord>(RA, cur, nxt, core, Hp, rows, cols, nW, rc.nR,
+                                                 cc.nR, cc.m, lane);
+                            emit_rect<kToRecord>(RA, cur, nxt, core, Hp, rows, cols, rc.nR, rc.m,
+                                                 cW, cc.m, lane);
+                            sorted_terms += (unsigned long long)rc.m * (unsigned long long)cc.m;
+                        }
+                    }
+                }
+            }
+        }
+    }
     FlatState fs;
     fs.k = fs.a0 = fs.b0 = 0;
     fs.left = fs.na = fs.nb = fs.abase = fs.bbase = 0;
     fs.mr = fs.mc = fs.q = 0;
     fs.inv_mc = 0;
-    fs.done = false;
-    while (fl_advance(fs, A, lane, rows, cols)) {
+    fs.done = sorted;   // the general walk: every case the sorted one does not take
+    while (!fs.done && fl_advance(fs, A, lane, rows, cols)) {
         const int32_t t = fs.q + lane;
         const int32_t nt = fs.mr * fs.mc;
         fs.q += 32;
@@ -358,6 +502,7 @@ __global__ void __launch_bounds__(kRouteThreads, 1) k_route(RouteArgs RA) {
     unsigned long long warp_terms = my_terms;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) warp_terms += __shfl_down_sync(kFull, warp_terms, d);
+    warp_terms += sorted_terms;   // (the same in every lane: lane 0 adds it)
     if (lane == 0 && warp_terms) atomicAdd(&A.tv.dc->terms, warp_terms);
 }
 
