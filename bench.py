@@ -885,6 +885,16 @@ def main():
     # (a few GB on the device); per term they grow with the table-to-L2 ratio, so
     # they are not scaled to this size (profiles/k_route_k_apply_c2_m500k.md)
     traffic = None
+    # The atomic roofline: the accumulate's terms per second against the rate
+    # of random 32-bit atomic adds (no return) into an L2-resident 16 MB region,
+    # measured here with the library's probe kernel. Every term outside the
+    # shared-memory core costs at least one L2 atomic or store, so this rate
+    # bounds the accumulate from above as the copy bandwidth does.
+    l2_atomics = crp.probe_update_rate(16 << 20, 1 << 28, 0)
+    atomic_roofline = {"terms_per_s": terms_step / (acc / 1e3), "peak_atomics_per_s": l2_atomics,
+                       "frac": terms_step / (acc / 1e3) / l2_atomics,
+                       "peak_source": "crp_probe_update_rate: 2^28 random 32-bit atomic adds "
+                                      "into a 16 MB region, timed in this run"}
 
     # ---- end to end through the C ABI from pinned host buffers ----
     # Every step copies its input from pinned host memory and reads its top-k
@@ -990,6 +1000,7 @@ def main():
                          "bytes_model": f"{BYTES_PER_TERM_UPDATE:g} B/term + input + "
                                         f"{SLOT_BYTES:g} B/entry",
                          "peak_source": f"{peak_src} hbm_gbs"},
+            "atomic_roofline": atomic_roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),
