@@ -46,7 +46,9 @@ __global__ void k_sel_hist(const uint32_t *key, int64_t n, int pass, unsigned in
 // wanted count drops by the keys of the larger digits. Clears the histogram
 // for the next pass. One CTA of 256 threads.
 __global__ void k_sel_pick(unsigned int *scratch, int pass, uint32_t K) {
-    __shared__ uint32_t digit;
+    __shared__ unsigned int h[256];
+    h[threadIdx.x] = scratch[threadIdx.x];   // one parallel read of the histogram
+    __syncthreads();
     if (threadIdx.x == 0) {
         const int shift = 24 - 8 * pass;
         uint32_t need = pass ? scratch[kSelNeed] : K;
@@ -54,16 +56,14 @@ __global__ void k_sel_pick(unsigned int *scratch, int pass, uint32_t K) {
         uint64_t cum = 0;
         int d = 255;
         for (; d > 0; --d) {
-            if (cum + scratch[d] >= need) break;
-            cum += scratch[d];
+            if (cum + h[d] >= need) break;
+            cum += h[d];
         }
         need -= (uint32_t)cum;
-        digit = (uint32_t)d;
         scratch[kSelNeed] = need;
         scratch[kSelPrefix] = prefix | ((uint32_t)d << shift);
     }
-    __syncthreads();
-    scratch[threadIdx.x] = 0;
+    scratch[threadIdx.x] = 0;   // (every thread read its bin before the barrier)
 }
 
 __global__ void k_sel_emit(const uint32_t *key, int64_t n, const unsigned int *scratch,
