@@ -683,7 +683,8 @@ def run_c5(args, np, torch, crp, ci, stream):
                                       sample_probs=256, stream=stream)
     tune_s = time.time() - t0
     batch = crp.Batch([(x, x) for x in dev], kw["P"], ci.SEED_A, ci.SEED_B,
-                      tile_vectors=kw["tile_vectors"], stream=stream)
+                      tile_vectors=kw["tile_vectors"], hot_items=kw.get("hot_items", 0),
+                      stream=stream)
     info = batch.info()
 
     def step():

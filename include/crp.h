@@ -423,6 +423,12 @@ crp_status crp_outer_product_noalloc(const crp_plan_desc *desc, const crp_sparse
  * table reset + the persistent kernel into one CUDA graph on a private
  * stream.  All problems' work items (problem, tile of outer products) form a
  * single queue drained by that kernel.
+ * desc->hot_items = R > 0 (at most 255; ignored with ready flags) adds a
+ * dense tier per problem: each run counts the items of the problem's first
+ * max(4096, K/64) outer products per side, takes the R most frequent of each
+ * side, counts pairs of two of them in an R x R block instead of the tables,
+ * and adds the block into the tables after the persistent kernel (results
+ * unchanged; the graph holds these kernels too).
  * wait_timeout_ns > 0 enables per-problem ready flags (crp_batch_set_ready;
  * all start ready): a CTA that meets a problem whose flag is cleared waits at
  * most wait_timeout_ns, then skips it and crp_batch_sync returns
@@ -500,9 +506,10 @@ crp_status crp_autotune(const crp_plan_desc *base, const crp_sparse *A, const cr
 /* Autotuner of batched products (crp_batch_create): times the persistent
  * launch of a sample of the problems -- every (nprob / sample_probs)-th
  * problem, sample_probs <= 0 meaning all -- for P in {64, 256, 1024, 4096}
- * and tile_vectors in {16, 32, 64, 128}, and writes into *best a copy of
- * *base with the fastest P and tile_vectors (*best_terms_per_s, nullable:
- * its rate on the sample).  The paper leaves the number of hash buckets and
+ * and tile_vectors in {16, 32, 64, 128}, then hot_items in {64, 128} on the
+ * fastest of those, and writes into *best a copy of *base with the fastest
+ * P, tile_vectors and hot_items (*best_terms_per_s, nullable: its rate on
+ * the sample).  The paper leaves the number of hash buckets and
  * the work per processor to tuning (Section 4, "Parameters"); this is that
  * choice made by measurement.  A, B: host arrays of nprob descriptors as for
  * crp_batch_create.  cache_path as for crp_autotune (key: device, sample

@@ -394,12 +394,14 @@ class Batch:
     (A, B) DeviceSparse pairs."""
 
     def __init__(self, problems, P: int, seed_a: int, seed_b: int, mode: int = CRP_FULL,
-                 tile_vectors: int = 0, wait_timeout_ns: int = 0, stream=None):
+                 tile_vectors: int = 0, wait_timeout_ns: int = 0, hot_items: int = 0,
+                 stream=None):
         self._lib = lib()
         d = crp_plan_desc()
         d.n_rows = d.n_cols = 1
         d.P, d.seed_a, d.seed_b = P, seed_a & (2**64 - 1), seed_b & (2**64 - 1)
         d.value_type, d.mode, d.tile_vectors = CRP_I32, mode, tile_vectors
+        d.hot_items = hot_items
         n = len(problems)
         self._keep = problems
         A = (crp_sparse * n)(*[a.c_struct() for a, _ in problems])
@@ -577,7 +579,7 @@ def autotune(A: DeviceSparse, B: DeviceSparse, n_rows: int, n_cols: int, seed_a:
 
 def autotune_batch(problems, seed_a: int, seed_b: int, mode: int = CRP_FULL,
                    sample_probs: int = 256, cache_path: str | None = None, stream=None):
-    """Fastest (P, tile_vectors) of the batched launch for these problems
+    """Fastest (P, tile_vectors, hot_items) of the batched launch for these problems
     (crp_autotune_batch): returns (dict of Batch keyword arguments, terms/s on
     the sample)."""
     d = crp_plan_desc()
@@ -593,4 +595,4 @@ def autotune_batch(problems, seed_a: int, seed_b: int, mode: int = CRP_FULL,
                                     sample_probs, cache_path.encode() if cache_path else None,
                                     ctypes.byref(best), ctypes.byref(tps),
                                     _stream_handle(stream)), "crp_autotune_batch")
-    return dict(P=best.P, tile_vectors=best.tile_vectors), tps.value
+    return dict(P=best.P, tile_vectors=best.tile_vectors, hot_items=best.hot_items), tps.value

@@ -254,6 +254,31 @@ extern "C" crp_status crp_autotune_batch(const crp_plan_desc *base, int32_t npro
             }
         }
     }
+    // then the dense tier on the best (P, tile): hot blocks of 64 or 128 items
+    // per problem and side
+    if (best_tps > 0) {
+        const crp_plan_desc base_best = *best;
+        for (uint32_t R : {64u, 128u}) {
+            crp_plan_desc d = base_best;
+            d.hot_items = R;
+            crp_batch *b = nullptr;
+            if (crp_batch_create(&b, &d, ns, SA.data(), SB.data(), 0, stream) != CRP_OK) continue;
+            double ms_best = 1e30;
+            bool ok = true;
+            for (int rep = 0; rep < 3 && ok; ++rep) {
+                double ms = 0;
+                ok = crp_batch_run(b) == CRP_OK && crp_batch_sync(b, &ms, nullptr) == CRP_OK;
+                if (ok && rep > 0 && ms > 0) ms_best = std::min(ms_best, ms);
+            }
+            crp_batch_destroy(b);
+            if (!ok || ms_best >= 1e29) continue;
+            const double tps = (double)terms / (ms_best * 1e-3);
+            if (tps > best_tps) {
+                best_tps = tps;
+                *best = d;
+            }
+        }
+    }
     if (best_tps < 0) {
         set_last_error("crp_autotune_batch: no candidate configuration ran");
         return CRP_ECUDA;

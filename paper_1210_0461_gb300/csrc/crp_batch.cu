@@ -29,6 +29,14 @@ struct BatchProb {
     const int32_t *b_idx;
     int64_t K;
     int32_t n_rows, n_cols;
+    // dense tier (hot_R > 0): the problem's hot items per side (rank of an
+    // item in its side's hot list, 0xFF when cold), their counts on the
+    // sample, the lists themselves and the hot block of R x R counters; for
+    // A and B the same arrays the B side shares the A side's
+    uint8_t *rank_a, *rank_b;
+    unsigned int *cnt_a, *cnt_b;
+    int32_t *items_a, *items_b;
+    unsigned int *hot;
 };
 
 struct BatchArgs {
@@ -38,6 +46,7 @@ struct BatchArgs {
     uint32_t P, tile;
     int mode;
     uint32_t sample_parts;                  // > 0: keep only terms with h < sample_parts
+    uint32_t hot_R;                         // > 0: pairs of two hot items count in the hot block
     const unsigned int *ready;              // nullable
     unsigned long long wait_ns;
     HashPair hp;
@@ -132,8 +141,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchArgs B) {
             if (valid) {
                 const unsigned peers = __match_any_sync(act, key);
                 if (lane == __ffs(peers) - 1) {
-                    table_update(A.tv, p, key, __popc(peers));
-                    ++flushed;
+                    bool dense = false;
+                    if (B.hot_R) {
+                        const uint32_t ra = pr.rank_a[oi], rb = pr.rank_b[j];
+                        if (ra < B.hot_R && rb < B.hot_R) {
+                            atomicAdd(&pr.hot[ra * B.hot_R + rb], (unsigned)__popc(peers));
+                            dense = true;
+                        }
+                    }
+                    if (!dense) {
+                        table_update(A.tv, p, key, __popc(peers));
+                        ++flushed;
+                    }
                 }
             }
         }
@@ -161,6 +180,110 @@ __global__ void k_batch_terms(const BatchProb *probs, int32_t nprob, unsigned lo
         for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(kFull, acc, d);
         if ((threadIdx.x & 31) == 0 && acc) atomicAdd(&out[q], acc);
     }
+}
+
+// Dense tier of a batch, per problem (one CTA per problem): item counts over
+// the first outer products (the same sample as a plan's: max(4096, K / 64)
+// of them), then the hot_R most frequent items of each side (an MSD radix
+// select on the counts, ties at the threshold in any order, never an item of
+// count 0): their list and their rank; after the persistent kernel, the hot
+// block's nonzero counters into the problem's tables.
+__global__ void k_batch_item_counts(const BatchProb *probs, int32_t nprob) {
+    for (int32_t q = blockIdx.x; q < nprob; q += gridDim.x) {
+        const BatchProb pr = probs[q];
+        if (pr.K <= 0) continue;
+        const int64_t S = min(pr.K, max((int64_t)4096, pr.K / 64));
+        for (int side = 0; side < 2; ++side) {
+            if (side == 1 && pr.cnt_b == pr.cnt_a) break;
+            const int64_t *ptr = side ? pr.b_ptr : pr.a_ptr;
+            const int32_t *idx = side ? pr.b_idx : pr.a_idx;
+            const int32_t n = side ? pr.n_cols : pr.n_rows;
+            unsigned int *cnt = side ? pr.cnt_b : pr.cnt_a;
+            const int64_t e = ptr[S];
+            for (int64_t x = ptr[0] + threadIdx.x; x < e; x += blockDim.x) {
+                const int32_t v = idx[x];
+                if (v >= 0 && v < n) atomicAdd(&cnt[v], 1u);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_batch_select_hot(const BatchProb *probs, int32_t nprob,
+                                                          uint32_t R) {
+    __shared__ unsigned int hist[256];
+    __shared__ unsigned int sh_prefix, sh_need, n_taken, n_tie;
+    for (int32_t q = blockIdx.x; q < nprob; q += gridDim.x) {
+        const BatchProb pr = probs[q];
+        for (int side = 0; side < 2; ++side) {
+            if (side == 1 && pr.cnt_b == pr.cnt_a) break;
+            const unsigned int *cnt = side ? pr.cnt_b : pr.cnt_a;
+            const int32_t n = side ? pr.n_cols : pr.n_rows;
+            int32_t *items = side ? pr.items_b : pr.items_a;
+            uint8_t *rank = side ? pr.rank_b : pr.rank_a;
+            uint32_t prefix = 0, pmask = 0, need = R;
+            for (int pass = 0; pass < 4; ++pass) {
+                const int shift = 24 - 8 * pass;
+                for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
+                __syncthreads();
+                for (int32_t x = threadIdx.x; x < n; x += blockDim.x) {
+                    const uint32_t c = cnt[x];
+                    if ((c & pmask) == prefix) atomicAdd(&hist[(c >> shift) & 255u], 1u);
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    uint32_t cum = 0;
+                    int d = 255;
+                    for (; d > 0; --d) {
+                        if (cum + hist[d] >= need) break;
+                        cum += hist[d];
+                    }
+                    sh_need = need - cum;
+                    sh_prefix = prefix | ((uint32_t)d << shift);
+                }
+                __syncthreads();
+                need = sh_need;
+                prefix = sh_prefix;
+                pmask |= 255u << shift;
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) n_taken = n_tie = 0;
+            __syncthreads();
+            for (int32_t x = threadIdx.x; x < n; x += blockDim.x) {
+                const uint32_t c = cnt[x];
+                if (c == 0) continue;
+                bool take = c > prefix;
+                if (c == prefix) take = atomicAdd(&n_tie, 1u) < need;
+                if (take) {
+                    const unsigned int pos = atomicAdd(&n_taken, 1u);   // < R by the select
+                    items[pos] = x;
+                    rank[x] = (uint8_t)pos;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void k_batch_hot_flush(BatchArgs B) {
+    const uint32_t R = B.hot_R, RR = R * R;
+    unsigned long long flushed = 0;
+    for (int32_t q = blockIdx.x; q < B.nprob; q += gridDim.x) {
+        const BatchProb pr = B.probs[q];
+        TableView tv = B.tv;
+        tv.part_off = B.tv.part_off + (size_t)q * B.P;
+        tv.part_mask = B.tv.part_mask + (size_t)q * B.P;
+        tv.part_full = B.tv.part_full + (size_t)q * B.P;
+        for (uint32_t c = threadIdx.x; c < RR; c += blockDim.x) {
+            const unsigned int v = pr.hot[c];
+            if (!v) continue;
+            const uint32_t i = (uint32_t)pr.items_a[c / R], j = (uint32_t)pr.items_b[c % R];
+            table_update(tv, partition_hash(B.hp, i, j), make_key(i, j), v);
+            ++flushed;
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) flushed += __shfl_down_sync(kFull, flushed, d);
+    if ((threadIdx.x & 31) == 0 && flushed) atomicAdd(&B.tv.dc->flushed, flushed);
 }
 
 // Largest live-entry count over the sampled partitions of each problem.
@@ -212,6 +335,12 @@ struct crp_batch {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     uint64_t launches = 0;
     unsigned long long total_terms = 0;
+    // dense tier: hot items per problem and side (R = 0: none)
+    uint32_t R = 0;
+    uint8_t *d_rank = nullptr;
+    unsigned int *d_cnt = nullptr, *d_hot = nullptr;
+    int32_t *d_items = nullptr;
+    size_t rank_n = 0, items_n = 0, hot_n = 0;   // (counts: rank_n words)
 };
 
 static crp_status bfail(crp_status st, const std::string &m) {
@@ -244,6 +373,7 @@ static uint64_t bpow2(uint64_t x) {
 static BatchArgs batch_args(crp_batch *b, Slot *slots, const unsigned long long *off,
                             const unsigned long long *mask, uint32_t sample_parts) {
     BatchArgs a;
+    a.hot_R = sample_parts ? 0u : b->R;   // (the sizing launch counts every entry in the tables)
     a.probs = b->d_probs;
     a.tile_prefix = b->d_tile_prefix;
     a.nprob = b->nprob;
@@ -276,7 +406,20 @@ static cudaError_t enqueue_run(crp_batch *b, Slot *slots, const unsigned long lo
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(b->dc, 0, sizeof(DevCounters), b->stream);
     if (e != cudaSuccess) return e;
-    k_batch<<<b->grid, kThreads, 0, b->stream>>>(batch_args(b, slots, off, mask, sample_parts));
+    const BatchArgs args = batch_args(b, slots, off, mask, sample_parts);
+    const int pgrid = std::min(b->nprob, 65535);
+    if (args.hot_R) {
+        e = cudaMemsetAsync(b->d_rank, 0xFF, b->rank_n, b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_cnt, 0, b->rank_n * 4, b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_hot, 0, b->hot_n * 4, b->stream);
+        if (e != cudaSuccess) return e;
+        k_batch_item_counts<<<pgrid, 256, 0, b->stream>>>(b->d_probs, b->nprob);
+        k_batch_select_hot<<<pgrid, 256, 0, b->stream>>>(b->d_probs, b->nprob, b->R);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    k_batch<<<b->grid, kThreads, 0, b->stream>>>(args);
+    if (args.hot_R) k_batch_hot_flush<<<pgrid, 256, 0, b->stream>>>(args);
     return cudaGetLastError();
 }
 
@@ -292,6 +435,10 @@ extern "C" void crp_batch_destroy(crp_batch *b) {
     cudaFree(b->d_full);
     cudaFree(b->d_ready);
     cudaFree(b->dc);
+    cudaFree(b->d_rank);
+    cudaFree(b->d_cnt);
+    cudaFree(b->d_hot);
+    cudaFree(b->d_items);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     delete b;
@@ -322,8 +469,22 @@ extern "C" crp_status crp_batch_create(crp_batch **out, const crp_plan_desc *des
             return bfail(CRP_EINVAL, "problem " + std::to_string(q) + ": bad descriptor");
         }
         probs[q] = {A[q].ptr, A[q].idx, Bm[q].ptr, Bm[q].idx, A[q].n_major, A[q].n_minor,
-                    Bm[q].n_minor};
+                    Bm[q].n_minor, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
         tiles[q + 1] = tiles[q] + (A[q].n_major + b->tile - 1) / b->tile;
+    }
+    // the dense tier (not with ready flags: it reads the inputs before the
+    // persistent kernel waits for them)
+    b->R = wait_timeout_ns ? 0u : std::min<uint32_t>(d.hot_items, 255u);
+    std::vector<size_t> rank_at(nprob + 1, 0);
+    if (b->R) {
+        for (int32_t q = 0; q < nprob; ++q) {
+            const bool same = A[q].ptr == Bm[q].ptr && A[q].idx == Bm[q].idx &&
+                              A[q].n_minor == Bm[q].n_minor;
+            rank_at[q + 1] = rank_at[q] + (size_t)A[q].n_minor + (same ? 0 : (size_t)Bm[q].n_minor);
+            b->items_n += (size_t)b->R * (same ? 1 : 2);
+        }
+        b->rank_n = rank_at[nprob];
+        b->hot_n = (size_t)nprob * b->R * b->R;
     }
     crp_status st = CRP_OK;
     auto ok = [&](cudaError_t e, const char *what) {
@@ -353,6 +514,32 @@ extern "C" crp_status crp_batch_create(crp_batch **out, const crp_plan_desc *des
         ok(cudaMalloc(&b->d_full, NP * 4), "malloc") && ok(cudaMalloc(&b->d_ready, nprob * 4), "malloc") &&
         ok(cudaMalloc(&b->dc, sizeof(DevCounters)), "malloc") && ok(cudaEventCreate(&b->ev0), "ev") &&
         ok(cudaEventCreate(&b->ev1), "ev")) {
+        if (b->R && ok(cudaMalloc(&b->d_rank, b->rank_n), "malloc ranks") &&
+            ok(cudaMalloc(&b->d_cnt, b->rank_n * 4), "malloc counts") &&
+            ok(cudaMalloc(&b->d_items, b->items_n * 4), "malloc items") &&
+            ok(cudaMalloc(&b->d_hot, b->hot_n * 4), "malloc hot")) {
+            size_t it = 0;
+            for (int32_t q = 0; q < nprob; ++q) {
+                BatchProb &pr = probs[q];
+                const size_t r0 = rank_at[q];
+                const bool same = rank_at[q + 1] - r0 == (size_t)A[q].n_minor;
+                pr.rank_a = b->d_rank + r0;
+                pr.cnt_a = b->d_cnt + r0;
+                pr.items_a = b->d_items + it;
+                it += b->R;
+                if (same) {
+                    pr.rank_b = pr.rank_a;
+                    pr.cnt_b = pr.cnt_a;
+                    pr.items_b = pr.items_a;
+                } else {
+                    pr.rank_b = b->d_rank + r0 + A[q].n_minor;
+                    pr.cnt_b = b->d_cnt + r0 + A[q].n_minor;
+                    pr.items_b = b->d_items + it;
+                    it += b->R;
+                }
+                pr.hot = b->d_hot + (size_t)q * b->R * b->R;
+            }
+        }
         ok(cudaMemcpyAsync(b->d_probs, probs.data(), nprob * sizeof(BatchProb),
                            cudaMemcpyHostToDevice, b->stream), "h2d");
         ok(cudaMemcpyAsync(b->d_tile_prefix, tiles.data(), (nprob + 1) * 8, cudaMemcpyHostToDevice,
@@ -470,7 +657,8 @@ extern "C" crp_status crp_batch_run(crp_batch *b) {
     B_CUDA(cudaEventRecord(b->ev0, b->stream));
     B_CUDA(cudaGraphLaunch(b->exec, b->stream));
     B_CUDA(cudaEventRecord(b->ev1, b->stream));
-    b->launches += 2;  // table reset + persistent kernel
+    // table reset + persistent kernel (+ item counts, hot selection, hot flush)
+    b->launches += b->R ? 5 : 2;
     return CRP_OK;
 }
 

@@ -97,7 +97,8 @@ def test_withheld_problem_times_out_then_completes(crp, problems):
 
 
 def test_batch_autotuned_choice_is_bit_exact(crp, problems, tmp_path):
-    """crp_autotune_batch picks P and tile_vectors on a sample of the problems;
+    """crp_autotune_batch picks P, tile_vectors and the per-problem hot block on
+    a sample of the problems;
     the batch built with its choice is bit-exact on every problem, and a
     second call with the same cache file returns the cached choice."""
     dev = [crp.to_device(T) for T in problems]
@@ -105,12 +106,53 @@ def test_batch_autotuned_choice_is_bit_exact(crp, problems, tmp_path):
     cache = str(tmp_path / "tune.txt")
     kw, tps = crp.autotune_batch(pairs, ci.SEED_A, ci.SEED_B, sample_probs=16, cache_path=cache)
     assert kw["P"] in (64, 256, 1024, 4096) and kw["tile_vectors"] in (16, 32, 64, 128)
+    assert kw["hot_items"] in (0, 64, 128)
     assert tps > 0
     kw2, tps2 = crp.autotune_batch(pairs, ci.SEED_A, ci.SEED_B, sample_probs=16, cache_path=cache)
     assert kw2 == kw and tps2 == tps
-    batch = crp.Batch(pairs, kw["P"], ci.SEED_A, ci.SEED_B, tile_vectors=kw["tile_vectors"])
+    batch = crp.Batch(pairs, kw["P"], ci.SEED_A, ci.SEED_B, tile_vectors=kw["tile_vectors"],
+                      hot_items=kw["hot_items"])
     batch.run()
     batch.sync()
     for q, T in enumerate(problems):
         _check(batch, q, _exact(T, O.FULL))
+    batch.close()
+
+
+@pytest.mark.parametrize("mode,R", [(O.FULL, 64), (O.UPPER, 64), (O.FULL, 255), (O.FULL, 7)])
+def test_batch_hot_tier_bit_exact(crp, problems, mode, R):
+    """Per-problem dense tier: pairs of two of a problem's R most frequent
+    items (on its first outer products) count in the problem's hot block and
+    are added into its tables after the persistent kernel; every problem stays
+    bit-exact, run after run (the graph recounts, reselects and clears)."""
+    dev = [crp.to_device(T) for T in problems]
+    batch = crp.Batch([(d, d) for d in dev], 64, ci.SEED_A, ci.SEED_B, mode=mode, tile_vectors=16,
+                      hot_items=R)
+    refs = [_exact(T, mode) for T in problems]
+    for rep in range(2):
+        batch.run()
+        ms, terms = batch.sync()
+        assert terms == sum(r.terms for r in refs)
+        for q, ref in enumerate(refs):
+            _check(batch, q, ref)
+    batch.close()
+
+
+def test_batch_hot_tier_two_sides(crp, problems):
+    """A and B different arrays (same number of outer products): each side
+    selects its own hot items; every problem bit-exact against the oracle's
+    A^T B."""
+    import dataclasses
+    ws = ci.c5_params(40, m_range=(100, 4000), n_range=(100, 3000))[:12]
+    others = [dataclasses.replace(w, seed=w.seed + 7).generate() for w in ws]
+    pairs, refs = [], []
+    for T, U in zip(problems[:12], others):
+        assert T.n_major == U.n_major
+        pairs.append((crp.to_device(T), crp.to_device(U)))
+        refs.append(O.exact_product(O.Compressed.of(T), O.Compressed.of(U), O.FULL))
+    batch = crp.Batch(pairs, 64, ci.SEED_A, ci.SEED_B, tile_vectors=16, hot_items=32)
+    batch.run()
+    batch.sync()
+    for q, ref in enumerate(refs):
+        _check(batch, q, ref)
     batch.close()
