@@ -8,15 +8,44 @@
 
 namespace crp {
 
-// nnz_at, when given, holds the count on the device (an entry of a ptr array)
-__global__ void k_item_counts(const int32_t *idx, int64_t nnz, const int64_t *nnz_at,
-                              int32_t n_items, unsigned int *cnt) {
+// Item counts with on-chip combining: each CTA counts into a shared-memory
+// table of kCountSlots items (open addressing, a few probes; an item that
+// finds no slot is counted straight in global memory) and adds the table into
+// cnt at the end, so a frequent item costs one global atomic per CTA rather
+// than one per occurrence.  nnz_at, when given, holds the count on the device
+// (an entry of a ptr array).
+constexpr int kCountSlots = 2048;
+constexpr int kCountProbes = 8;
+__global__ void __launch_bounds__(256) k_item_counts(const int32_t *idx, int64_t nnz,
+                                                     const int64_t *nnz_at, int32_t n_items,
+                                                     unsigned int *cnt) {
+    __shared__ unsigned int key[kCountSlots], val[kCountSlots];
+    for (int t = threadIdx.x; t < kCountSlots; t += blockDim.x) {
+        key[t] = 0xFFFFFFFFu;
+        val[t] = 0u;
+    }
+    __syncthreads();
     if (nnz_at) nnz = *nnz_at;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nnz;
          x += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = idx[x];
-        if (v >= 0 && v < n_items) atomicAdd(&cnt[v], 1u);
+        if (v < 0 || v >= n_items) continue;
+        uint32_t h = ((uint32_t)v * 2654435761u) >> 21;   // 11 bits: kCountSlots
+        bool done = false;
+        for (int pr = 0; pr < kCountProbes; ++pr, h = (h + 1) & (kCountSlots - 1)) {
+            unsigned int k = key[h];
+            if (k == 0xFFFFFFFFu) k = atomicCAS(&key[h], 0xFFFFFFFFu, (unsigned int)v);
+            if (k == 0xFFFFFFFFu || k == (unsigned int)v) {
+                atomicAdd(&val[h], 1u);
+                done = true;
+                break;
+            }
+        }
+        if (!done) atomicAdd(&cnt[v], 1u);
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kCountSlots; t += blockDim.x)
+        if (val[t]) atomicAdd(&cnt[key[t]], val[t]);
 }
 
 // Selection state kept on the device between passes (no host round trip):
@@ -76,6 +105,14 @@ __global__ void k_sel_emit(const uint32_t *key, int64_t n, const unsigned int *s
         if (k == tau) take = atomicAdd(tie, 1u) < need_at_tau;
         if (take) out[atomicAdd(cnt, 1u)] = x;
     }
+}
+
+// CTAs of the counting kernel: enough for the input, at most 512 (each adds
+// its shared-memory table into the counts at the end, so more CTAs would
+// only repeat the frequent items' global atomics).
+static int count_grid_for(int64_t n) {
+    const int64_t g = (n + 4095) / 4096;
+    return (int)(g < 512 ? (g > 0 ? g : 1) : 512);
 }
 
 int select_grid_for(int64_t n) {
@@ -139,7 +176,7 @@ cudaError_t order_by_count(int64_t *items, const unsigned int *cnt, uint32_t R, 
 cudaError_t launch_item_counts(const int32_t *idx, int64_t nnz, int32_t n_items, unsigned int *cnt,
                                cudaStream_t s) {
     if (nnz <= 0) return cudaSuccess;
-    k_item_counts<<<select_grid_for(nnz), 256, 0, s>>>(idx, nnz, nullptr, n_items, cnt);
+    k_item_counts<<<count_grid_for(nnz), 256, 0, s>>>(idx, nnz, nullptr, n_items, cnt);
     return cudaGetLastError();
 }
 
@@ -147,7 +184,7 @@ cudaError_t launch_item_counts(const int32_t *idx, int64_t nnz, int32_t n_items,
 // round trip); nnz_hint sizes the grid only.
 cudaError_t launch_item_counts_at(const int32_t *idx, const int64_t *nnz_at, int64_t nnz_hint,
                                   int32_t n_items, unsigned int *cnt, cudaStream_t s) {
-    k_item_counts<<<select_grid_for(nnz_hint), 256, 0, s>>>(idx, 0, nnz_at, n_items, cnt);
+    k_item_counts<<<count_grid_for(nnz_hint), 256, 0, s>>>(idx, 0, nnz_at, n_items, cnt);
     return cudaGetLastError();
 }
 
