@@ -7,7 +7,10 @@
 // L2-resident region run several times faster than into HBM.  So:
 //
 //  1. k_route enumerates every term once (blocks of up to 32 x 32 terms of
-//     a_k b_k staged in shared memory, 32 terms per warp step).  Terms of hot and warm items go to the dense
+//     a_k b_k staged in shared memory, 32 terms per warp step; for integer
+//     counts of every pair each side of a block is ordered by dense-tier
+//     class, so that a warp step has one destination).  Terms of hot and
+//     warm items go to the dense
 //     counters; every other term becomes a record appended to the bin of its
 //     partition group b = h(i,j) >> shift.  (Pairs of the most frequent
 //     items count first in per-CTA shared-memory counters, added into the
@@ -17,9 +20,10 @@
 //     one shared-memory 64-bit atomic returns (chunk, position) together, the
 //     lane that receives position kChunkRecs installs the next chunk, and no
 //     CTA-wide barrier is needed while enumerating.
-//  2. k_apply walks the chunks sorted by bin, all warps on one bin at a
-//     time, adding each record into its partition table; a group's table
-//     region stays in L2 while it is updated.
+//  2. k_apply_bulk (k_apply for real values) walks the chunks sorted by bin,
+//     all warps on a few bins at a time, adding each record into its
+//     partition table; a group's table region stays in L2 while it is
+//     updated.
 //
 // An append that arrives while its chunk is being replaced backs off and
 // retries; one that still finds no slot, or finds the pool exhausted, goes to
@@ -153,8 +157,8 @@ __device__ __forceinline__ uint32_t ld_idx(const int32_t *p) {
 // ranks and values, is staged in the warp's shared memory, and the lanes take
 // the block's mr x mc terms in order, 32 per step (term t: row t / mc, column
 // t mod mc), so every lane has a term in every step but a block's last --
-// where one row per lane left a lane idle for every row short of 32 (c2's
-// vectors hold ~20 entries).  The warp takes tiles of outer products from a
+// where one row per lane left a lane idle for every row short of 32 (Poisson(20)
+// transactions hold ~20 items).  The warp takes tiles of outer products from a
 // global counter, so warps never wait on each other for work.
 // Shared memory of a route CTA: per bin its open chunk (u64) and spare (u32),
 // the core counters, then (flattened enumeration) 64 staged entries per warp.
