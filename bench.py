@@ -993,7 +993,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
                          "kernel": {"direct": "k_accumulate", "smem": "k_accumulate",
-                                    "routed": "k_route+k_apply"}[args.mode]
+                                    "routed": "k_route+k_apply_bulk"}[args.mode]
                                    + ("+k_hot_flush" if args.hot else "")
                                    + ("+k_warm_flush" if args.warm else ""),
                          "kernel_ms": acc,
