@@ -506,7 +506,7 @@ crp_status crp_autotune(const crp_plan_desc *base, const crp_sparse *A, const cr
 /* Autotuner of batched products (crp_batch_create): times the persistent
  * launch of a sample of the problems -- every (nprob / sample_probs)-th
  * problem, sample_probs <= 0 meaning all -- for P in {64, 256, 1024, 4096}
- * and tile_vectors in {16, 32, 64, 128}, then hot_items in {64, 128} on the
+ * and tile_vectors in {16, 32, 64, 128}, then hot_items in {64, 128, 255} on the
  * fastest of those, and writes into *best a copy of *base with the fastest
  * P, tile_vectors and hot_items (*best_terms_per_s, nullable: its rate on
  * the sample).  The paper leaves the number of hash buckets and

@@ -254,11 +254,11 @@ extern "C" crp_status crp_autotune_batch(const crp_plan_desc *base, int32_t npro
             }
         }
     }
-    // then the dense tier on the best (P, tile): hot blocks of 64 or 128 items
+    // then the dense tier on the best (P, tile): hot blocks of 64, 128 or 255 items
     // per problem and side
     if (best_tps > 0) {
         const crp_plan_desc base_best = *best;
-        for (uint32_t R : {64u, 128u}) {
+        for (uint32_t R : {64u, 128u, 255u}) {
             crp_plan_desc d = base_best;
             d.hot_items = R;
             crp_batch *b = nullptr;
