@@ -58,12 +58,25 @@ def test_batched_full_size():
     Ts = [w.generate() for w in ws]
     dev = [crp.to_device(T) for T in Ts]
     Pb = 256
-    batch = crp.Batch([(x, x) for x in dev], Pb, ci.SEED_A, ci.SEED_B, tile_vectors=32)
+    # the configuration bench.py times: 64 outer products per work item and
+    # per-problem hot blocks of 128 items
+    batch = crp.Batch([(x, x) for x in dev], Pb, ci.SEED_A, ci.SEED_B, tile_vectors=64,
+                      hot_items=128)
     batch.run()
     _, terms = batch.sync()
     per = [int((T.lengths().astype(np.int64) ** 2).sum()) for T in Ts]
     assert terms == sum(per)
     rng = np.random.default_rng(5)
+    # 64 of the problems under 1e6 terms, every entry against the oracle
+    small = [q for q in range(len(Ts)) if per[q] < 1_000_000]
+    for q in rng.choice(small, 64, replace=False).tolist():
+        Tc = O.Compressed.of(Ts[q])
+        ref = O.exact_product(Tc, Tc, O.FULL)
+        i, j, w = batch.export(q)
+        o = np.lexsort((j, i))
+        assert np.array_equal(i[o], ref.i) and np.array_equal(j[o], ref.j), q
+        assert np.array_equal(w[o], ref.w), q
+    # 12 larger ones: every term stored once, the diagonal, sampled entries
     for q in rng.choice(len(Ts), 12, replace=False).tolist():
         T = Ts[q]
         i, j, w = batch.export(q)
