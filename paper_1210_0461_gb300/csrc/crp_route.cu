@@ -328,6 +328,12 @@ __device__ __forceinline__ SortedCounts stage_sorted(const AccumulateArgs &A, co
 
 enum { kToCore = 0, kToHot, kToWarmA, kToWarmB, kToRecord };
 
+// +1 into a dense-tier counter, the line marked to stay in L2 (the tiers are
+// tens of MB, the records that stream past them many GB)
+__device__ __forceinline__ void red_keep(unsigned int *a, unsigned long long pol) {
+    asm volatile("red.global.add.L2::cache_hint.u32 [%0], 1, %1;" ::"l"(a), "l"(pol) : "memory");
+}
+
 // The terms rows [r0, r1) x cols [c0, c1) of a staged block, all bound for
 // destination DST.
 template <int DST>
@@ -340,6 +346,9 @@ __device__ __forceinline__ void emit_rect(const RouteArgs &RA, unsigned long lon
     const AccumulateArgs &A = RA.acc;
     const int n = nr * nc;
     const uint32_t inv = (65536u + (uint32_t)nc - 1u) / (uint32_t)nc;   // t / nc for t < 1024
+    unsigned long long keep = 0;
+    if constexpr (DST == kToHot || DST == kToWarmA || DST == kToWarmB)
+        asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
     for (int q = 0; q < n; q += 32) {
         const int t = q + lane;
         if (t >= n) break;
@@ -349,11 +358,11 @@ __device__ __forceinline__ void emit_rect(const RouteArgs &RA, unsigned long lon
         if constexpr (DST == kToCore) {
             atomicAdd(&core[rd.ranks * Hp + cd.ranks], 1u);
         } else if constexpr (DST == kToHot) {
-            atomicAdd(&A.hot_block[rd.ranks * A.hot_R + cd.ranks], 1u);
+            red_keep(&A.hot_block[rd.ranks * A.hot_R + cd.ranks], keep);
         } else if constexpr (DST == kToWarmA) {
-            atomicAdd(&A.warm_a[(size_t)rd.ranks * A.n_cols + cd.j], 1u);
+            red_keep(&A.warm_a[(size_t)rd.ranks * A.n_cols + cd.j], keep);
         } else if constexpr (DST == kToWarmB) {
-            atomicAdd(&A.warm_b[(size_t)cd.ranks * A.n_rows + rd.i], 1u);
+            red_keep(&A.warm_b[(size_t)cd.ranks * A.n_rows + rd.i], keep);
         } else {
             const uint32_t p = (rd.ha + cd.hb) & A.hp.ha.mask;
             bin_append(RA, cur, nxt, p >> RA.B_shift, (unsigned long long)make_key(rd.i, cd.j));
