@@ -81,7 +81,14 @@ __device__ __forceinline__ void apply_record(const RouteArgs &RA, const R &r) {
     table_update(RA.acc.tv, partition_hash(RA.acc.hp, i, j), key, rec_val(r));
 }
 
-__device__ __forceinline__ void store_rec(unsigned long long *p, unsigned long long v) { *p = v; }
+// (8-byte records are stored marked evict-first in L2: many GB stream past the
+// dense tiers and the open chunks' lines)
+__device__ __forceinline__ void store_rec(unsigned long long *p, unsigned long long v) {
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" ::"l"(p), "l"(v), "l"(pol)
+                 : "memory");
+}
 __device__ __forceinline__ void store_rec(Rec16 *p, const Rec16 &v) {
     *(ulonglong2 *)p = *(const ulonglong2 *)&v;
 }
@@ -145,10 +152,14 @@ __device__ __forceinline__ void bin_append(const RouteArgs &RA, unsigned long lo
 }
 
 // An input index read that does not allocate in L1 (L1 keeps the rank
-// arrays of the dense tiers; the index arrays stream through once).
+// arrays of the dense tiers; the index arrays stream through once) and is
+// marked evict-first in L2.
 __device__ __forceinline__ uint32_t ld_idx(const int32_t *p) {
     uint32_t v;
-    asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;"
+                 : "=r"(v) : "l"(p), "l"(pol));
     return v;
 }
 
