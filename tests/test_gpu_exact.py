@@ -418,3 +418,22 @@ def test_distinct_count_estimate_against_the_oracle(crp, w, P, tol):
     assert est > 0
     assert abs(est - len(ref.i)) <= tol * len(ref.i), (est, len(ref.i))
     plan.close()
+
+
+@pytest.mark.parametrize("hot,warm", [(512, 200), (300, 128), (129, 129), (2048, 64)],
+                         ids=["warm-above-core", "warm-equal-core", "hot-just-above-core",
+                              "hot2048-warm64"])
+def test_routed_class_sorted_walk_tier_orders(crp, hot, warm):
+    """The routed walk orders each staged side by dense-tier class; the
+    rectangles it walks depend on whether the warm width is below, at or
+    above the 128-item shared-memory core.  Every order gives the oracle's
+    product exactly (Zipf(1.1) transactions over 1,000 items, so the tiers hold
+    most items)."""
+    T = ci.C1.scaled(m=20_000).generate()
+    Tc = O.Compressed.of(T)
+    ref = O.exact_product(Tc, Tc, O.FULL)
+    plan = _run(crp, T, T, T.n_minor, T.n_minor, 64,
+                flags=crp.CRP_PLAN_ROUTED | crp.CRP_PLAN_DEBUG_CHECKS, groups=0,
+                hot_items=hot, warm_items=warm)
+    _check_exact(crp, plan, ref, 64)
+    plan.close()
